@@ -1,0 +1,181 @@
+"""Seeded synthetic seed-extension workloads.
+
+The paper's BSW measurements use pairs intercepted from BWA-MEM on real reads
+(Section VI, Table V).  Neither those reads nor the reference ship here, so the
+workloads are synthetic stand-ins drawn by ``bswgen.c`` (splitmix64 streams,
+one per read or pair).  This module only produces inputs: sequences as codes
+0..3 (A, C, G, T), offsets, lengths and the seed score h0.  It holds none of
+the extension arithmetic; the CUDA path and the CPU oracle both take their
+inputs from here.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bswgen.c")
+_SO = os.path.join(_HERE, "_bswgen.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the generator into an in-tree shared object."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, i32, u64, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p
+            lib.bswgen_num_units.argtypes = [ctypes.c_int, i64]
+            lib.bswgen_num_units.restype = i64
+            lib.bswgen_lengths.argtypes = [ctypes.c_int, u64, i64, i32, vp, vp]
+            lib.bswgen_lengths.restype = ctypes.c_int
+            lib.bswgen_fill.argtypes = [ctypes.c_int, u64, i64, i32, vp, vp, vp, vp, vp, ctypes.c_int]
+            lib.bswgen_fill.restype = ctypes.c_int
+            lib.bswgen_random_codes.argtypes = [u64, i64, vp]
+            lib.bswgen_random_codes.restype = None
+            _lib = lib
+    return _lib
+
+
+@dataclasses.dataclass(frozen=True)
+class Scoring:
+    """Match score a > 0; mismatch, gap-open and gap-extension penalties > 0.
+
+    A gap of k bases costs o + k*e (Eq. 3 writes the boundary as
+    H[0,0] - (g_o + g_e*i))."""
+    match: int = 1
+    mismatch: int = 4
+    o_del: int = 6
+    e_del: int = 1
+    o_ins: int = 6
+    e_ins: int = 1
+
+
+@dataclasses.dataclass(frozen=True)
+class Params:
+    scoring: Scoring = Scoring()
+    w: int = 100
+    zdrop: int = 100
+    end_bonus: int = 5
+
+
+@dataclasses.dataclass
+class Workload:
+    """A batch of extension pairs.  Sequence k of q is q[q_off[k] : q_off[k] + q_len[k]]."""
+    name: str
+    params: Params
+    q: np.ndarray       # uint8 codes 0..3
+    q_off: np.ndarray   # int64, in bases
+    q_len: np.ndarray   # int32
+    t: np.ndarray
+    t_off: np.ndarray
+    t_len: np.ndarray
+    h0: np.ndarray      # int32
+
+    @property
+    def n_pairs(self) -> int:
+        return int(self.q_len.shape[0])
+
+    def subset(self, idx) -> "Workload":
+        """Pairs idx (an index array), re-laid out compactly."""
+        idx = np.asarray(idx, dtype=np.int64)
+        ql, tl = self.q_len[idx], self.t_len[idx]
+        qo, qt = layout(ql)
+        to, tt = layout(tl)
+        q = np.zeros(qt, np.uint8)
+        t = np.zeros(tt, np.uint8)
+        for k, p in enumerate(idx):
+            q[qo[k]:qo[k] + ql[k]] = self.q[self.q_off[p]:self.q_off[p] + ql[k]]
+            t[to[k]:to[k] + tl[k]] = self.t[self.t_off[p]:self.t_off[p] + tl[k]]
+        return Workload(self.name + "[subset]", self.params, q, qo, ql.copy(), t, to, tl.copy(),
+                        self.h0[idx].copy())
+
+
+def layout(lengths: np.ndarray, align: int = 16):
+    """Offsets (multiples of `align` bases) for sequences of the given lengths, and the total."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    padded = (lengths + align - 1) // align * align
+    off = np.zeros(lengths.shape[0], np.int64)
+    if lengths.shape[0] > 1:
+        np.cumsum(padded[:-1], out=off[1:])
+    total = int(padded.sum()) + align
+    return off, total
+
+
+# The five workloads: id, pairs, seed, band w, z-drop.  Scoring is the same for
+# all: match 1, mismatch 4, gap open 6, gap extend 1, end bonus 5.
+CONFIGS = {
+    "plain10k": dict(gen=0, n_pairs=10_000, seed=0, w=100, zdrop=100),
+    "read151": dict(gen=1, n_pairs=2_000_000, seed=1, w=100, zdrop=100),
+    "read250": dict(gen=2, n_pairs=4_000_000, seed=2, w=100, zdrop=100),
+    "long10k": dict(gen=3, n_pairs=20_000, seed=3, w=500, zdrop=400),
+}
+
+
+def make(config: str, n_pairs: int | None = None, seed: int | None = None, align: int = 16,
+         nthreads: int | None = None) -> Workload:
+    """Generate workload `config` (a CONFIGS key); n_pairs/seed override the defaults."""
+    c = CONFIGS[config]
+    n = c["n_pairs"] if n_pairs is None else int(n_pairs)
+    s = c["seed"] if seed is None else int(seed)
+    params = Params(Scoring(), w=c["w"], zdrop=c["zdrop"], end_bonus=5)
+    lib = _load()
+    q_len = np.zeros(n, np.int32)
+    t_len = np.zeros(n, np.int32)
+    rc = lib.bswgen_lengths(c["gen"], s, n, params.scoring.match, q_len.ctypes.data, t_len.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("bswgen_lengths failed: %d" % rc)
+    q_off, qt = layout(q_len, align)
+    t_off, tt = layout(t_len, align)
+    q = np.zeros(qt, np.uint8)
+    t = np.zeros(tt, np.uint8)
+    h0 = np.zeros(n, np.int32)
+    nth = nthreads or min(32, os.cpu_count() or 1)
+    rc = lib.bswgen_fill(c["gen"], s, n, params.scoring.match, q_off.ctypes.data, t_off.ctypes.data,
+                         q.ctypes.data, t.ctypes.data, h0.ctypes.data, nth)
+    if rc != 0:
+        raise RuntimeError("bswgen_fill failed: %d" % rc)
+    return Workload(config, params, q, q_off, q_len, t, t_off, t_len, h0)
+
+
+def random_codes(seed: int, n: int) -> np.ndarray:
+    out = np.zeros(n, np.uint8)
+    _load().bswgen_random_codes(seed, n, out.ctypes.data)
+    return out
+
+
+def from_lists(queries, targets, h0s, params: Params | None = None, align: int = 16,
+               name: str = "custom") -> Workload:
+    """Build a workload from explicit code sequences (lists/arrays of 0..3)."""
+    ql = np.array([len(x) for x in queries], np.int32)
+    tl = np.array([len(x) for x in targets], np.int32)
+    qo, qt = layout(ql, align)
+    to, tt = layout(tl, align)
+    q = np.zeros(qt, np.uint8)
+    t = np.zeros(tt, np.uint8)
+    for k, x in enumerate(queries):
+        q[qo[k]:qo[k] + len(x)] = np.asarray(x, np.uint8)
+    for k, x in enumerate(targets):
+        t[to[k]:to[k] + len(x)] = np.asarray(x, np.uint8)
+    return Workload(name, params or Params(), q, qo, ql, t, to, tl, np.asarray(h0s, np.int32))
+
+
+def encode(s: str) -> np.ndarray:
+    """ACGT string -> codes 0..3."""
+    lut = {"A": 0, "C": 1, "G": 2, "T": 3}
+    return np.array([lut[ch] for ch in s.upper()], np.uint8)
