@@ -6,7 +6,7 @@ in place (Section V-A, last paragraph), this module fills explicit matrices
 H, E, F over every cell, with the boundaries written out as the functions of
 Eq. 3, so the index bookkeeping of the one-row form is not shared.
 
-It implements:
+``extend_full`` implements:
   * Eq. 2 with the readings R2 (zero diagonal -> M = 0) and R3 (E and F open
     from M with cost o + e) of the oracle's header;
   * Eq. 3 boundaries: H[-1,-1] = h0, first row max(0, h0 - o_ins - (j+1) e_ins),
@@ -15,8 +15,9 @@ It implements:
     with cells outside it absent (H = E = 0, F restarts inside the band);
   * the all-zero-row abort (rule b, first half) and optionally z-drop (R5);
   * best / global-score bookkeeping with the tie rules R4.
-It does NOT implement the band adjustment after each row (rule c): that is the
-heuristic the comparisons are about.
+It does not adjust the band after each row (rule c).  ``extend_trimmed`` adds
+rule c, restated over the same explicit matrices with a per-column record of
+the row that last wrote each slot (see its docstring).
 
 The DP runs over a batch of equally-shaped pairs at once (numpy vectors over
 the batch); the loops over cells are plain Python.
@@ -132,6 +133,143 @@ def extend_full(params, Q: np.ndarray, T: np.ndarray, H0: np.ndarray, band: bool
             alive = alive & ~(cand & (drop > params.zdrop))
         if not alive.any():
             break
+    out[:, 0] = best
+    out[:, 1] = bj + 1
+    out[:, 2] = bi + 1
+    out[:, 3] = gi + 1
+    out[:, 4] = gbest
+    out[:, 5] = moff
+    return out
+
+
+def extend_trimmed(params, Q: np.ndarray, T: np.ndarray, H0: np.ndarray, zdrop: bool = True,
+                   w: int | None = None):
+    """The full heuristic (rules a, b and c), restated over explicit matrices.
+
+    The one-row form of Section V-A keeps a slot per column; between rows,
+    slot c holds the H of column c-1 and the E entering column c, as written
+    by the last row whose band covered c.  Here that is spelled out: every
+    computed cell is kept in full matrices, and for each column the row that
+    last wrote its slot is recorded.  A cell's diagonal and incoming E are then
+    read from that row -- the previous row when the band is unchanged, an
+    earlier row (or the first row of Eq. 3) when the band regrows (R6).  The
+    slot of the band's first column holds that row's first-column boundary
+    (Eq. 3, 0 once the band has left column 0); the slot just past its last
+    column holds the last H and an E of 0.
+
+    Band adjustment (rule c): the next row starts at the first non-empty slot
+    and ends two past the last non-empty slot, a slot being empty when its H
+    and E are both 0.  Returns int64 [B, 6] like extend_full.
+    """
+    s = params.scoring
+    Q = np.asarray(Q, np.int64)
+    T = np.asarray(T, np.int64)
+    H0 = np.asarray(H0, np.int64)
+    B, n = Q.shape
+    m = T.shape[1]
+    out = np.zeros((B, 6), np.int64)
+    if n == 0:
+        out[:, 0] = H0
+        out[:, 4] = H0
+        return out
+    oe_d, oe_i = s.o_del + s.e_del, s.o_ins + s.e_ins
+    wb = band_clip(n, params.w if w is None else w, s.match, params.end_bonus,
+                   s.o_ins, s.e_ins, s.o_del, s.e_del)
+    ar = np.arange(B)
+
+    def left(i):
+        return np.maximum(0, H0 - s.o_del - (np.asarray(i) + 1) * s.e_del)
+
+    def top_slot(j):  # the first row of Eq. 3 as the slot of column j
+        return H0.copy() if j == 0 else np.maximum(0, H0 - s.o_ins - j * s.e_ins)
+
+    H = np.zeros((max(m, 1), n, B), np.int64)      # H(i, j)
+    Eo = np.zeros((max(m, 1), n, B), np.int64)     # E(i+1, j)
+    LO = np.zeros((max(m, 1), B), np.int64)
+    HI = np.zeros((max(m, 1), B), np.int64)
+    lw = np.full((n + 1, B), -1, np.int64)         # last row that wrote slot j
+
+    def slot(r, j):
+        """(H, E) held by slot j after row r (r >= 0 per pair, j in [LO[r], HI[r]])."""
+        lo_r, hi_r = LO[r, ar], HI[r, ar]
+        first = np.where(lo_r == 0, left(r), 0)
+        hprev = H[r, max(j - 1, 0), ar] if j > 0 else np.zeros(B, np.int64)
+        hv = np.where(j == lo_r, first, hprev)
+        ev = np.where(j >= hi_r, 0, Eo[r, min(j, n - 1), ar])
+        return hv, ev
+
+    best = H0.copy()
+    bi = np.full(B, -1, np.int64)
+    bj = np.full(B, -1, np.int64)
+    gbest = np.full(B, -1, np.int64)
+    gi = np.full(B, -1, np.int64)
+    moff = np.zeros(B, np.int64)
+    alive = np.ones(B, bool)
+    lo = np.zeros(B, np.int64)
+    hi = np.full(B, n, np.int64)
+
+    for i in range(m):
+        lo = np.maximum(lo, i - wb)
+        hi = np.minimum(np.minimum(hi, i + wb + 1), n)
+        LO[i], HI[i] = lo, hi
+        F = np.zeros(B, np.int64)
+        rm = np.zeros(B, np.int64)
+        rj = np.full(B, -1, np.int64)
+        for j in range(n):
+            inb = alive & (lo <= j) & (j < hi)
+            if not inb.any():
+                continue
+            r = lw[j]
+            never = r < 0
+            rr = np.where(never, 0, r)
+            hv, ev = slot(rr, j)
+            d = np.where(never, top_slot(j), hv)
+            e = np.where(never, 0, ev)
+            sc = np.where(Q[:, j] == T[:, i], s.match, -s.mismatch)
+            M = np.where(d > 0, d + sc, 0)
+            h = np.maximum(M, np.maximum(e, F))
+            H[i, j] = np.where(inb, h, 0)
+            Eo[i, j] = np.where(inb, np.maximum(np.maximum(e - s.e_del, M - oe_d), 0), 0)
+            F = np.where(inb, np.maximum(np.maximum(F - s.e_ins, M - oe_i), 0), 0)
+            ge = inb & (h >= rm)
+            rj = np.where(ge, j, rj)
+            rm = np.where(inb, np.maximum(rm, h), rm)
+        # slots [lo, hi] now belong to row i
+        for j in range(n + 1):
+            cov = alive & (lo <= j) & (j <= hi)
+            lw[j] = np.where(cov, i, lw[j])
+        reach = np.maximum(lo, hi) == n
+        hend = np.where(hi > lo, H[i, np.clip(hi - 1, 0, n - 1), ar], np.where(lo == 0, left(i), 0))
+        upd = alive & reach
+        gi = np.where(upd & (hend >= gbest), i, gi)
+        gbest = np.where(upd, np.maximum(gbest, hend), gbest)
+        alive = alive & (rm != 0)
+        newb = alive & (rm > best)
+        moff = np.where(newb, np.maximum(moff, np.abs(rj - i)), moff)
+        bi0, bj0 = bi.copy(), bj.copy()
+        best = np.where(newb, rm, best)
+        bi = np.where(newb, i, bi)
+        bj = np.where(newb, rj, bj)
+        if zdrop and params.zdrop > 0:
+            di, dj = i - bi0, rj - bj0
+            drop = np.where(di > dj, best - rm - (di - dj) * s.e_del, best - rm - (dj - di) * s.e_ins)
+            alive = alive & ~(~newb & (drop > params.zdrop))
+        if not alive.any():
+            break
+        # rule c
+        nz = np.zeros((n + 1, B), bool)
+        for j in range(n + 1):
+            cov = (lo <= j) & (j <= hi)
+            if cov.any():
+                hv, ev = slot(np.full(B, i), j)
+                nz[j] = cov & ((hv != 0) | (ev != 0))
+        idx = np.arange(n + 1)[:, None]
+        cand_lo = np.where(nz & (idx < hi), idx, n + 1).min(axis=0)
+        new_lo = np.where(cand_lo <= n, np.minimum(cand_lo, hi), hi)
+        cand_hi = np.where(nz & (idx >= new_lo), idx, -1).max(axis=0)
+        last = np.where(cand_hi >= 0, cand_hi, new_lo - 1)
+        lo = np.where(alive, new_lo, lo)
+        hi = np.where(alive, np.minimum(last + 2, n), hi)
     out[:, 0] = best
     out[:, 1] = bj + 1
     out[:, 2] = bi + 1

@@ -221,6 +221,67 @@ def test_trim_never_raises_score():
     assert (got[:, 0] == ref[:, 0]).mean() > 0.9
 
 
+def _readlike(rng, B, n, m, flip_p=0.2):
+    Q = rng.integers(0, 4, (B, n))
+    T = rng.integers(0, 4, (B, m))
+    k = min(n, m)
+    T[: B // 2, :k] = Q[: B // 2, :k]
+    flip = rng.random((B // 2, k)) < flip_p
+    T[: B // 2, :k] = np.where(flip, (T[: B // 2, :k] + 1) % 4, T[: B // 2, :k])
+    return Q, T
+
+
+TRIM_PARAMS = [
+    W.Params(W.Scoring(), w=100, zdrop=100, end_bonus=5),
+    W.Params(W.Scoring(1, 4, 2, 1, 2, 1), w=3, zdrop=3, end_bonus=5),
+    W.Params(W.Scoring(1, 6, 1, 1, 1, 1), w=100, zdrop=5, end_bonus=0),
+    W.Params(W.Scoring(2, 3, 3, 2, 1, 1), w=2, zdrop=0, end_bonus=1),
+]
+
+
+def test_trimmed_exhaustive_4x4():
+    """The full heuristic on every pair of 4-base sequences equals the
+    explicit-matrix restatement with band adjustment (rule c)."""
+    allseq = np.array(list(itertools.product(range(4), repeat=4)), np.uint8)
+    Q = np.repeat(allseq, len(allseq), axis=0)
+    T = np.tile(allseq, (len(allseq), 1))
+    for params in TRIM_PARAMS[:2]:
+        for h0 in (2, 9):
+            H0 = np.full(len(Q), h0, np.int32)
+            got, _, _ = _oracle_grid(Q, T, H0, 0, params)
+            np.testing.assert_array_equal(got, brute.extend_trimmed(params, Q, T, H0))
+
+
+@pytest.mark.parametrize("pi", range(len(TRIM_PARAMS)))
+@pytest.mark.parametrize("n,m", [(1, 5), (5, 1), (8, 8), (12, 16), (24, 30), (40, 20)])
+def test_trimmed_random(pi, n, m):
+    """As above on random read-like pairs, including pairs where the band
+    regrows over slots written by earlier rows (R6)."""
+    params = TRIM_PARAMS[pi]
+    rng = np.random.default_rng(1000 * pi + 10 * n + m)
+    B = 3000
+    Q, T = _readlike(rng, B, n, m, 0.25)
+    H0 = rng.integers(0, 20, B)
+    got, _, stale = _oracle_grid(Q, T, H0, 0, params)
+    np.testing.assert_array_equal(got, brute.extend_trimmed(params, Q, T, H0))
+    got2, _, _ = _oracle_grid(Q, T, H0, oracle.NO_ZDROP, params)
+    np.testing.assert_array_equal(got2, brute.extend_trimmed(params, Q, T, H0, zdrop=False))
+
+
+def test_stale_reads_occur_and_match():
+    """R6 is exercised: a narrow band over noisy pairs makes the band regrow
+    over slots from earlier rows with non-zero values, and the results still
+    equal the explicit-matrix restatement."""
+    params = W.Params(W.Scoring(1, 4, 2, 1, 2, 1), w=3, zdrop=0, end_bonus=5)
+    rng = np.random.default_rng(11)
+    B = 6000
+    Q, T = _readlike(rng, B, 24, 24, 0.3)
+    H0 = rng.integers(0, 20, B)
+    got, _, stale = _oracle_grid(Q, T, H0, 0, params)
+    assert (stale > 0).sum() >= 20
+    np.testing.assert_array_equal(got, brute.extend_trimmed(params, Q, T, H0))
+
+
 def test_gap_reading_differs():
     """R3: with gaps opening from M an insertion cannot directly follow a
     deletion; opening from H (Eq. 2 as printed) allows it.  The two readings
@@ -235,6 +296,10 @@ def test_gap_reading_differs():
     a, _, _ = _oracle_grid(Q, T, H0, 0, params)
     b, _, _ = _oracle_grid(Q, T, H0, oracle.GAP_FROM_H, params)
     assert (a != b).any(axis=1).sum() > 0
+    # the default reading is the one the brute force states (gaps open from M)
+    full, _, _ = _oracle_grid(Q, T, H0, oracle.NO_BAND | oracle.NO_TRIM | oracle.NO_ZDROP, params)
+    np.testing.assert_array_equal(full, brute.extend_full(params, Q, T, H0))
+    np.testing.assert_array_equal(a, brute.extend_trimmed(params, Q, T, H0, zdrop=False))
     same = np.tile(np.arange(8) % 4, (50, 1))
     a2, _, _ = _oracle_grid(same, same, np.full(50, 10), 0, params)
     b2, _, _ = _oracle_grid(same, same, np.full(50, 10), oracle.GAP_FROM_H, params)
