@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""BSW seed-extension benchmark: GCUPS on one GB300 (batched vs plain kernel).
+
+A step is one pass of the whole extension path over one batch: length
+bucketing, the per-class extension kernels and the exact 32-bit re-run, for
+every pair of the 151 bp short-read workload (2,000,000 pairs, inputs resident
+in HBM).  GCUPS counts the DP cells the scalar algorithm computes (the oracle's
+count, which the library reproduces exactly).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--config read151] [--pairs N] [--serve]
+
+--impl reference times the CPU oracle on the host cores, on a bounded sample of
+the same workload.  --serve runs the serving sweep (Poisson arrivals of
+mixed-size requests, p50/p99 latency per offered load) instead of the batch
+benchmark.  Under torchrun each rank runs its own batch (weak scaling, no
+collective on the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Algorithmic integer operations per DP cell of Eq. 2 as BWA-MEM computes it:
+# the diagonal add, the zero-diagonal rule, the 3-way max for H, M - (o + e),
+# the E and F updates (add-max-clamp each), and the row max with its argmax.
+OPS_PER_CELL = 8
+# 32-bit integer lane-operations one SM issues per clock (4 schedulers x 32 lanes).
+LANE_OPS_PER_CLK_PER_SM = 128
+METRIC = "BSW GCUPS on 1 GB300 (batched vs plain kernel, bit-exact); p50/p99 serve latency"
+KERNELS_PER_STEP = 14    # classify, scan, scatter, 8 per-thread classes, 2 warp classes, re-run
+
+WORKLOAD_TEXT = {
+    "read151": "151 bp short-read seed extensions: 2,000,000 left/right pairs from 1,000,000 reads of a 100 Mbp "
+               "random reference (0.1% SNPs, 1% sequencing substitutions), seeds 19-151 bp, query 0-132 bp, "
+               "target = query + 100; match 1, mismatch 4, gap 6+1k, w 100, zdrop 100, end bonus 5",
+    "read250": "250 bp read seed extensions: 4,000,000 pairs, 2% divergence (10% of it 1-10 bp indels), w 100, zdrop 100",
+    "plain10k": "10,000 pairs, queries 1-130 bp with 1% substitutions and 0.1% 1-3 bp indels, w 100, zdrop 100",
+    "long10k": "20,000 long-query pairs, query log-uniform 1-10 kbp, 12% error, w 500, zdrop 400",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="read151")
+    ap.add_argument("--pairs", type=int, default=None)
+    ap.add_argument("--serve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    """Barrier and max-over-ranks for torchrun launches (no data-path collective)."""
+
+    def __init__(self, backend="nccl"):
+        import torch
+        import torch.distributed as td
+        self.world, self.rank, self.local = dist_env()
+        self.td = td
+        self.on = self.world > 1
+        if self.on and not td.is_initialized():
+            td.init_process_group(backend=backend)
+        self.torch = torch
+        self.device = "cuda" if backend == "nccl" else "cpu"
+
+    def barrier(self):
+        if self.on:
+            self.td.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.on:
+            return x
+        t = self.torch.tensor([float(x)], dtype=self.torch.float64, device=self.device)
+        self.td.all_reduce(t, op=self.td.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.on:
+            return x
+        t = self.torch.tensor([float(x)], dtype=self.torch.float64, device=self.device)
+        self.td.all_reduce(t, op=self.td.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.on and self.td.is_initialized():
+            self.td.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def class_of(q_len, t_len, h0, match=1):
+    """Per-thread kernel class of each pair with 8-bit lanes, as the library
+    buckets it (0: 129-256 query bases, 1: 65-128, 2: 33-64, 3: 1-32; -1 other)."""
+    n = np.asarray(q_len, np.int64)
+    bound = np.asarray(h0, np.int64) + match * np.minimum(n, np.asarray(t_len, np.int64))
+    c = np.select([n > 128, n > 64, n > 32, n > 0], [0, 1, 2, 3], -1)
+    return np.where((n > 256) | (bound > 255) | (np.asarray(t_len) <= 0), -1, c)
+
+
+# ------------------------------------------------------------------ arms
+
+def cpu_baseline(wl, pairs: int):
+    import oracle
+    sample = wl.subset(np.arange(min(pairs, wl.n_pairs)))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res, cells, _ = oracle.extend_batch(sample, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return sample, res, cells, dt, cores
+
+
+def run_reference(args):
+    """The CPU oracle, timed on the host cores on a bounded sample per step."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1907_12931_gb300 import workload as W
+    import oracle
+    wl = W.make(args.config, n_pairs=args.pairs)
+    per_step = min(wl.n_pairs, 100_000 if args.config in ("read151", "read250") else 2000)
+    cores = os.cpu_count() or 1
+    steps = max(1, min(args.steps, 20))
+    times, cells_tot = [], 0
+    for s in range(args.warmup + steps):
+        lo = (s * per_step) % max(1, wl.n_pairs - per_step + 1)
+        sub = wl.subset(np.arange(lo, lo + per_step))
+        t0 = time.perf_counter()
+        _, cells, _ = oracle.extend_batch(sub, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            cells_tot += int(cells.sum())
+    total = sum(times)
+    value = cells_tot / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GCUPS", "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.config, "description": WORKLOAD_TEXT.get(args.config, args.config),
+                   "pairs": wl.n_pairs, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                         "sample": "%d consecutive pairs per step of the %d-pair workload" % (per_step, wl.n_pairs)},
+        "e2e": {"value": round(value, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def pinned_host_batch(bsw, hb):
+    """Copy a HostBatch's arrays into pinned host memory (for the end-to-end leg)."""
+    import torch
+    for name in ("q", "t", "q_off", "q_len", "t_off", "t_len", "h0"):
+        a = getattr(hb, name)
+        p = torch.empty(a.shape, dtype={np.uint8: torch.uint8, np.int32: torch.int32,
+                                        np.int64: torch.int64}[a.dtype.type], pin_memory=True)
+        p.numpy()[...] = a
+        setattr(hb, "_pin_" + name, p)
+        setattr(hb, name, p.numpy())
+    return hb
+
+
+def time_device(ctx, db, flags, steps, warmup, stream, dist):
+    import torch
+    for _ in range(warmup):
+        ctx.extend_device(db, flags, stream.cuda_stream)
+    stream.synchronize()
+    ctx.sync(stream.cuda_stream)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.extend_device(db, flags, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.sync(stream.cuda_stream)
+    dist.barrier()
+    return dist.max(ms) / steps
+
+
+def run_gb300(args):
+    import torch
+    from paper_1907_12931_gb300 import bsw, workload as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist("nccl")
+    base = W.CONFIGS[args.config]
+    wl = W.make(args.config, n_pairs=args.pairs, seed=base["seed"] + rank)
+    ctx = bsw.Context(wl.params, mem_budget_bytes=40 << 30)
+    hb = bsw.HostBatch(wl)
+    db = bsw.DeviceBatch(hb)
+    stream = torch.cuda.Stream()
+    in_bytes = hb.nbytes()
+
+    # batched path, timed with clocks sampled
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_device(ctx, db, 0, args.steps, args.warmup, stream, dist)
+    clk = clocks.stop()
+    cells = int(db.cells.item())
+    total_cells = dist.sum(cells)
+    gcups = total_cells / (ms * 1e-3) / 1e9
+    out_batched = db.out.cpu().numpy().copy()
+
+    # plain one-pair-per-warp kernel on the same inputs
+    p_steps = max(3, args.steps // 10)
+    ms_plain = time_device(ctx, db, bsw.BSW_PLAIN_KERNEL, p_steps, max(1, args.warmup // 2), stream, dist)
+    plain_cells = int(db.cells.item())
+    plain_equal = bool(np.array_equal(db.out.cpu().numpy(), out_batched)) and plain_cells == cells
+    gcups_plain = dist.sum(plain_cells) / (ms_plain * 1e-3) / 1e9
+
+    # dominant kernel: the 8-bit class with the most cells, as a batch of its own
+    all_cls = class_of(wl.q_len, wl.t_len, wl.h0, wl.params.scoring.match)
+    est = wl.q_len.astype(np.float64) * wl.t_len
+    dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(4)]))
+    sub = wl.subset(np.nonzero(all_cls == dom)[0])
+    sdb = bsw.DeviceBatch(bsw.HostBatch(sub))
+    ms_dom = time_device(ctx, sdb, 0, max(3, args.steps // 4), 2, stream, dist)
+    dom_cells = int(sdb.cells.item())
+    del sdb
+    nmax = {0: 256, 1: 128, 2: 64, 3: 32}[dom]
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    f_mhz = clk["sm_mhz"] or 1470.0
+    achieved = dom_cells * OPS_PER_CELL / (ms_dom * 1e-3) / 1e12
+    peak = sms * f_mhz * 1e6 * LANE_OPS_PER_CLK_PER_SM / 1e12
+
+    # end to end through the C ABI with pinned host buffers
+    hbp = pinned_host_batch(bsw, bsw.HostBatch(wl))
+    e_steps = max(3, args.steps // 20)
+    for _ in range(2):
+        ctx.extend_host(hbp)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        out_h, cells_h = ctx.extend_host(hbp)
+    t_e2e = dist.max((time.perf_counter() - t0) / e_steps)
+    e2e = dist.sum(cells_h) / t_e2e / 1e9
+    e2e_equal = bool(np.array_equal(out_h, out_batched))
+    n = wl.n_pairs
+    qb = int((wl.q_off[-1] + wl.q_len[-1] + 3) // 4) if n else 0
+    tb = int((wl.t_off[-1] + wl.t_len[-1] + 3) // 4) if n else 0
+    h2d = qb + tb + n * (8 + 4 + 8 + 4 + 4)
+    d2h = n * 24 + 8 + 4
+
+    # CPU baseline (rank 0): the oracle on a bounded sample, also a parity spot check
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu:
+        sample, res, scells, dt, cores = cpu_baseline(wl, 400_000)
+        cpu = {"value": round(int(scells.sum()) / dt / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+               "sample": "first %d of %d pairs (%.2f s on %d threads)" % (sample.n_pairs, n, dt, cores)}
+        mism = int((res != out_batched[: sample.n_pairs]).any(axis=1).sum())
+        parity = {"pairs_checked": sample.n_pairs, "fields": 6, "mismatches": mism}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": args.config, "description": WORKLOAD_TEXT.get(args.config, args.config),
+                       "pairs_per_gpu": n, "cells_per_step": cells,
+                       "l2": "inputs larger than L2 (%.0f MB resident packed inputs + %.0f MB results)"
+                             % (in_bytes / 1e6, n * 24 / 1e6),
+                       "parallelism": "replicas x%d (pairs sharded by rank, no collective)" % world},
+            "plain": {"value": round(gcups_plain, 3), "unit": "GCUPS", "ms_per_step": round(ms_plain, 4),
+                      "kernel": "one pair per warp, input order", "bit_exact_vs_batched": plain_equal},
+            "speedup_vs_plain": round(gcups / gcups_plain, 3) if gcups_plain else None,
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "k_inter<%d,u8> (batch of its own class: %d pairs, %d cells)"
+                                   % (nmax, sub.n_pairs, dom_cells),
+                         "ops_per_cell": OPS_PER_CELL,
+                         "peak_basis": "%d SMs x %.0f MHz (median under load) x %d lane-ops/clk"
+                                       % (sms, f_mhz, LANE_OPS_PER_CLK_PER_SM)},
+            "cpu_baseline": cpu,
+            "parity_sample": parity,
+            "e2e": {"value": round(e2e, 3), "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": round(t_e2e * 1e3, 3), "bit_exact_vs_device": e2e_equal},
+            "gpu_launches": KERNELS_PER_STEP * (args.steps),
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"]},
+            "peaks_file": {k: measured_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.serve:
+        from paper_1907_12931_gb300 import serve_bench
+        return serve_bench.main(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

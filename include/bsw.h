@@ -1,0 +1,190 @@
+/*
+ * bsw.h - C ABI of the GB300 banded Smith-Waterman seed-extension library.
+ *
+ * The operation is BWA-MEM's seed extension as described in Section V-A of
+ * "Efficient Architecture-Aware Acceleration of BWA-MEM for Multicore Systems"
+ * (Vasimuddin, Misra, Li, Aluru, IPDPS 2019): starting from a seed with score
+ * h0 = H[0,0], fill the DP matrix of Eq. 2 row by row with the boundary of
+ * Eq. 3, restricted to a band around the diagonal (rule a), stopping when a
+ * row is all zero or drops too far below the best (rule b, z-drop), and
+ * shrinking the band past zero cells at both ends after each row (rule c).
+ * Rows walk the target (deletions are vertical moves), columns walk the query
+ * (insertions are horizontal moves).  The result fields are the ones BWA-MEM's
+ * extension returns (Section V-D, items (a) and (b)):
+ *   score   best H over the computed rows, or h0 if no cell exceeds it
+ *   qle,tle query / target length of the best cell (column+1, row+1; 0 = seed)
+ *   gtle    target length at the best score reaching the query end (0 = none)
+ *   gscore  best H in the query's last column (-1 if the band never reached it)
+ *   max_off largest |column - row| of a cell that raised the best score
+ * Every field is exact integer arithmetic; the library's kernels and a plain
+ * CPU restatement agree bit for bit.
+ *
+ * Conventions
+ *   - Bases are 2-bit codes A=0 C=1 G=2 T=3, packed four per byte, base k of a
+ *     sequence in bits 2*(k%4)..2*(k%4)+1 of byte k/4 (bsw_pack_2bit).
+ *     Offsets are in bases and must be multiples of 4, so every sequence starts
+ *     on a byte.  Ambiguous bases (N) are not representable.
+ *   - Extension runs rightward from the seed.  A left extension is the caller's
+ *     job: pass the reversed query prefix and the reversed reference window.
+ *   - An empty query returns {h0, 0, 0, 0, h0, 0}; an empty target returns
+ *     {h0, 0, 0, 0, -1, 0}.
+ *   - Scores must satisfy h0 + match * min(qlen, tlen) < 2^30.
+ *
+ * Threading: a context is not thread-safe, except that bsw_stream_submit and
+ * bsw_stream_poll may be called from one client thread while the context's
+ * own server thread runs.
+ *
+ * Every function returns BSW_OK (0), BSW_PENDING (> 0, poll only) or a
+ * negative BSW_E* code; nothing else crosses the ABI.  After any error except
+ * BSW_ECUDA the context stays usable.  After BSW_ECUDA from a sticky device
+ * error (the CUDA context is lost) only bsw_destroy is valid.
+ */
+#ifndef BSW_H
+#define BSW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSW_OK        0
+#define BSW_PENDING   1
+#define BSW_EINVAL   (-1)   /* bad argument or input value                    */
+#define BSW_ENOMEM   (-2)   /* host or device allocation failed               */
+#define BSW_EBUDGET  (-3)   /* the batch cannot fit the device-memory budget  */
+#define BSW_ECUDA    (-4)   /* a CUDA call failed                             */
+#define BSW_ETIMEOUT (-5)   /* a bounded wait ran out                         */
+#define BSW_ENOTFOUND (-6)  /* unknown or already collected ticket            */
+#define BSW_ESTATE   (-7)   /* the context cannot accept the call             */
+
+/* bsw_batch_t.flags */
+#define BSW_DEVICE_PTRS   0x01u  /* every batch pointer and `out` are device pointers      */
+#define BSW_FORCE_I8      0x02u  /* 8-bit lanes for every pair up to 256 query bases,
+                                    without the score-bound check; pairs whose scores
+                                    leave 0..255 are re-run exactly with 32-bit lanes   */
+#define BSW_FORCE_I16     0x04u  /* 16-bit lanes (same re-run rule above 32767)            */
+#define BSW_FORCE_I32     0x08u  /* 32-bit warp-per-pair kernel for every pair             */
+#define BSW_PLAIN_KERNEL  0x10u  /* baseline: one pair per warp, no bucketing, input order */
+#define BSW_NO_GRAPH      0x20u  /* device-pointer path: launch directly, no CUDA graph    */
+#define BSW_COPY_INPUTS   0x40u  /* submit: copy host inputs at submit time                */
+
+typedef struct bsw_ctx bsw_ctx_t;
+
+/* match > 0; mismatch, o_*, e_* > 0 are penalties (a gap of k costs o + k*e).
+ * match <= 127 and mismatch <= 128. */
+typedef struct {
+    int32_t match, mismatch, o_del, e_del, o_ins, e_ins;
+} bsw_scoring_t;
+
+typedef struct {
+    int32_t score, qle, tle, gtle, gscore, max_off;
+} bsw_result_t;
+
+typedef struct {
+    int64_t n_pairs;
+    const uint8_t *q;          /* packed queries                                  */
+    const int64_t *q_off;      /* [n_pairs] query start, in bases, multiple of 4  */
+    const int32_t *q_len;      /* [n_pairs] >= 0                                  */
+    const uint8_t *t;          /* packed targets                                  */
+    const int64_t *t_off;      /* [n_pairs]                                       */
+    const int32_t *t_len;      /* [n_pairs] >= 0                                  */
+    const int32_t *h0;         /* [n_pairs] seed score, >= 0                      */
+    const int32_t *w_override; /* [n_pairs] per-pair band, or NULL for the ctx w  */
+    uint32_t flags;            /* BSW_* flags above                               */
+} bsw_batch_t;
+
+/*
+ * Create a context.  sc: scoring (copied); w >= 0: band half-width before the
+ * gap-limit clip; zdrop: z-drop threshold, <= 0 disables it; end_bonus >= 0:
+ * used only in the band clip (the largest gap worth opening is
+ * trunc((qlen*match + end_bonus - o)/e + 1)).  mem_budget_bytes > 0 caps the
+ * device memory the context allocates (work buffers, staging and the serving
+ * loop's slots).  On success *out owns a CUDA-side context on the current
+ * device; release it with bsw_destroy.
+ * Errors: BSW_EINVAL (bad scoring/arguments), BSW_ENOMEM, BSW_ECUDA.
+ */
+int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonus,
+             int64_t mem_budget_bytes, bsw_ctx_t **out);
+
+/*
+ * Extend every pair of a batch (Section V-A for each pair; the batch is the
+ * inter-task unit of Section V-C).  out[k] receives pair k's result.
+ *
+ * Host pointers (default): inputs and out are host memory owned by the caller;
+ * they may be released on return.  The call stages inputs to the device,
+ * runs the kernels on cuda_stream (a cudaStream_t, or NULL for the context's
+ * own stream), copies results back and returns when they are in out.
+ *
+ * BSW_DEVICE_PTRS: every pointer, including out and cells_out, is device
+ * memory on the context's device.  The call only enqueues work on cuda_stream
+ * and returns; results are valid once the stream reaches that point.  Input
+ * errors found by the kernels are reported by bsw_sync.
+ *
+ * cells_out (nullable): receives the number of DP cells computed, the same
+ * count the CPU restatement makes (cells inside each row's band, over the rows
+ * run).  In device mode it is a device int64 that the call overwrites.
+ *
+ * Errors: BSW_EINVAL (n_pairs < 0, null pointer, negative length or h0,
+ * offset not a multiple of 4, score bound too large, bad flags), BSW_EBUDGET,
+ * BSW_ENOMEM, BSW_ECUDA.
+ */
+int bsw_extend_batch(bsw_ctx_t *ctx, const bsw_batch_t *batch, bsw_result_t *out,
+                     int64_t *cells_out, void *cuda_stream);
+
+/*
+ * Wait for cuda_stream (NULL: the context's stream) and report input errors
+ * the kernels flagged since the last call (BSW_EINVAL), or BSW_ECUDA.
+ */
+int bsw_sync(bsw_ctx_t *ctx, void *cuda_stream);
+
+/*
+ * Serving: queue a batch (host pointers; device pointers with
+ * BSW_DEVICE_PTRS) and return at once with a ticket.  A server thread admits
+ * queued batches as stream slots and device memory within the budget free up,
+ * merges small ones into one launch, and overlaps launches on several streams
+ * (continuous batching).  Inputs and out must stay valid until poll returns
+ * BSW_OK for the ticket, unless BSW_COPY_INPUTS is set (inputs are copied
+ * before submit returns; out must still stay valid).
+ * Errors: BSW_EINVAL, BSW_EBUDGET (the batch alone exceeds the budget),
+ * BSW_ENOMEM, BSW_ESTATE (context shutting down).
+ */
+int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *batch, bsw_result_t *out,
+                      uint64_t *ticket);
+
+/*
+ * Wait up to timeout_us microseconds (0: just check; < 0: wait without limit)
+ * for a ticket.  BSW_OK: out is filled and the ticket is released.
+ * BSW_PENDING: not yet.  A negative code: the request failed (the ticket is
+ * released) or the ticket is unknown (BSW_ENOTFOUND).
+ */
+int bsw_stream_poll(bsw_ctx_t *ctx, uint64_t ticket, int32_t timeout_us);
+
+/* Static English description of a return code. */
+const char *bsw_strerror(int code);
+
+/* Stop the server thread, wait for queued work, free everything.  NULL is a no-op. */
+void bsw_destroy(bsw_ctx_t *ctx);
+
+/*
+ * Pack n bases into out[(n + 3) / 4] (layout above).  Input bytes are codes
+ * 0..3 or the letters ACGT/acgt.  Returns BSW_OK, or BSW_EINVAL on any other
+ * byte (out is then unspecified).
+ */
+int bsw_pack_2bit(const uint8_t *in, int64_t n, uint8_t *out);
+
+/*
+ * The band half-width after the gap-limit clip for a query of qlen bases:
+ * min(w, trunc((qlen*match + end_bonus - o)/e + 1) for both gap kinds), each
+ * limit at least 1.  Returns -1 on bad arguments.
+ */
+int32_t bsw_band_width(const bsw_ctx_t *ctx, int32_t qlen, int32_t w);
+
+/* Library version string. */
+const char *bsw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSW_H */

@@ -1,0 +1,257 @@
+"""Python binding of the BSW C ABI (include/bsw.h): argument marshalling only.
+
+Every function named like the C ABI calls it directly through ctypes; every
+step of the extension runs in the library's CUDA kernels.  The library must
+have been built (``paper_1907_12931_gb300.build.build()``); there is no
+fallback of any kind, and a missing library raises at load time.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB
+
+BSW_OK = 0
+BSW_PENDING = 1
+BSW_EINVAL = -1
+BSW_ENOMEM = -2
+BSW_EBUDGET = -3
+BSW_ECUDA = -4
+BSW_ETIMEOUT = -5
+BSW_ENOTFOUND = -6
+BSW_ESTATE = -7
+
+BSW_DEVICE_PTRS = 0x01
+BSW_FORCE_I8 = 0x02
+BSW_FORCE_I16 = 0x04
+BSW_FORCE_I32 = 0x08
+BSW_PLAIN_KERNEL = 0x10
+BSW_NO_GRAPH = 0x20
+BSW_COPY_INPUTS = 0x40
+
+FIELDS = ("score", "qle", "tle", "gtle", "gscore", "max_off")
+
+
+class BswError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__("%s: %s (%d)" % (where, bsw_strerror(code), code))
+        self.code = code
+
+
+class bsw_scoring_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("match", "mismatch", "o_del", "e_del", "o_ins", "e_ins")]
+
+
+class bsw_result_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in FIELDS]
+
+
+class bsw_batch_t(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64),
+                ("q", ctypes.c_void_p), ("q_off", ctypes.c_void_p), ("q_len", ctypes.c_void_p),
+                ("t", ctypes.c_void_p), ("t_off", ctypes.c_void_p), ("t_len", ctypes.c_void_p),
+                ("h0", ctypes.c_void_p), ("w_override", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libbsw.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError("libbsw.so is not built (%s); run paper_1907_12931_gb300.build.build()" % LIB)
+            L = ctypes.CDLL(LIB)
+            vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+            L.bsw_init.argtypes = [ctypes.POINTER(bsw_scoring_t), i32, i32, i32, i64, ctypes.POINTER(vp)]
+            L.bsw_init.restype = ctypes.c_int
+            L.bsw_extend_batch.argtypes = [vp, ctypes.POINTER(bsw_batch_t), vp, vp, vp]
+            L.bsw_extend_batch.restype = ctypes.c_int
+            L.bsw_sync.argtypes = [vp, vp]
+            L.bsw_sync.restype = ctypes.c_int
+            L.bsw_stream_submit.argtypes = [vp, ctypes.POINTER(bsw_batch_t), vp, ctypes.POINTER(u64)]
+            L.bsw_stream_submit.restype = ctypes.c_int
+            L.bsw_stream_poll.argtypes = [vp, u64, i32]
+            L.bsw_stream_poll.restype = ctypes.c_int
+            L.bsw_strerror.argtypes = [ctypes.c_int]
+            L.bsw_strerror.restype = ctypes.c_char_p
+            L.bsw_destroy.argtypes = [vp]
+            L.bsw_destroy.restype = None
+            L.bsw_pack_2bit.argtypes = [vp, i64, vp]
+            L.bsw_pack_2bit.restype = ctypes.c_int
+            L.bsw_band_width.argtypes = [vp, i32, i32]
+            L.bsw_band_width.restype = i32
+            L.bsw_version.argtypes = []
+            L.bsw_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------ C ABI, by name
+
+def bsw_strerror(code: int) -> str:
+    return lib().bsw_strerror(int(code)).decode()
+
+
+def bsw_version() -> str:
+    return lib().bsw_version().decode()
+
+
+def bsw_init(scoring, w: int, zdrop: int, end_bonus: int, mem_budget_bytes: int) -> int:
+    """Returns the context handle (an integer pointer)."""
+    sc = bsw_scoring_t(scoring.match, scoring.mismatch, scoring.o_del, scoring.e_del, scoring.o_ins, scoring.e_ins)
+    h = ctypes.c_void_p()
+    rc = lib().bsw_init(ctypes.byref(sc), int(w), int(zdrop), int(end_bonus), int(mem_budget_bytes), ctypes.byref(h))
+    if rc != BSW_OK:
+        raise BswError(rc, "bsw_init")
+    return h.value
+
+
+def bsw_destroy(ctx: int) -> None:
+    lib().bsw_destroy(ctx)
+
+
+def bsw_extend_batch(ctx: int, batch: bsw_batch_t, out_ptr: int, cells_ptr: int | None, stream: int | None) -> int:
+    return lib().bsw_extend_batch(ctx, ctypes.byref(batch), out_ptr, cells_ptr, stream)
+
+
+def bsw_sync(ctx: int, stream: int | None = None) -> int:
+    return lib().bsw_sync(ctx, stream)
+
+
+def bsw_stream_submit(ctx: int, batch: bsw_batch_t, out_ptr: int) -> tuple[int, int]:
+    t = ctypes.c_uint64()
+    rc = lib().bsw_stream_submit(ctx, ctypes.byref(batch), out_ptr, ctypes.byref(t))
+    return rc, t.value
+
+
+def bsw_stream_poll(ctx: int, ticket: int, timeout_us: int) -> int:
+    return lib().bsw_stream_poll(ctx, int(ticket), int(timeout_us))
+
+
+def bsw_pack_2bit(codes: np.ndarray) -> np.ndarray:
+    codes = np.ascontiguousarray(codes, np.uint8)
+    out = np.zeros((codes.shape[0] + 3) // 4, np.uint8)
+    rc = lib().bsw_pack_2bit(codes.ctypes.data, codes.shape[0], out.ctypes.data)
+    if rc != BSW_OK:
+        raise BswError(rc, "bsw_pack_2bit")
+    return out
+
+
+def bsw_band_width(ctx: int, qlen: int, w: int) -> int:
+    return int(lib().bsw_band_width(ctx, int(qlen), int(w)))
+
+
+# --------------------------------------------------------------- marshalling
+
+class HostBatch:
+    """Packed, host-resident inputs of a workload (numpy arrays kept alive)."""
+
+    def __init__(self, wl, w_override=None, flags: int = 0):
+        self.q = bsw_pack_2bit(wl.q)
+        self.t = bsw_pack_2bit(wl.t)
+        self.q_off = np.ascontiguousarray(wl.q_off, np.int64)
+        self.q_len = np.ascontiguousarray(wl.q_len, np.int32)
+        self.t_off = np.ascontiguousarray(wl.t_off, np.int64)
+        self.t_len = np.ascontiguousarray(wl.t_len, np.int32)
+        self.h0 = np.ascontiguousarray(wl.h0, np.int32)
+        self.w = None if w_override is None else np.ascontiguousarray(w_override, np.int32)
+        self.n = int(self.q_len.shape[0])
+        self.flags = flags
+
+    def struct(self, flags: int | None = None) -> bsw_batch_t:
+        f = self.flags if flags is None else flags
+        return bsw_batch_t(self.n, self.q.ctypes.data, self.q_off.ctypes.data, self.q_len.ctypes.data,
+                           self.t.ctypes.data, self.t_off.ctypes.data, self.t_len.ctypes.data,
+                           self.h0.ctypes.data, None if self.w is None else self.w.ctypes.data, f)
+
+    def nbytes(self) -> int:
+        return sum(a.nbytes for a in (self.q, self.t, self.q_off, self.q_len, self.t_off, self.t_len, self.h0))
+
+
+class DeviceBatch:
+    """The same inputs as torch CUDA tensors, plus device result buffers."""
+
+    def __init__(self, hb: HostBatch, device="cuda"):
+        import torch
+        self.n = hb.n
+        self.q = torch.from_numpy(hb.q).to(device)
+        self.t = torch.from_numpy(hb.t).to(device)
+        self.q_off = torch.from_numpy(hb.q_off).to(device)
+        self.q_len = torch.from_numpy(hb.q_len).to(device)
+        self.t_off = torch.from_numpy(hb.t_off).to(device)
+        self.t_len = torch.from_numpy(hb.t_len).to(device)
+        self.h0 = torch.from_numpy(hb.h0).to(device)
+        self.w = None if hb.w is None else torch.from_numpy(hb.w).to(device)
+        self.out = torch.zeros((self.n, 6), dtype=torch.int32, device=device)
+        self.cells = torch.zeros(1, dtype=torch.int64, device=device)
+
+    def struct(self, flags: int = 0) -> bsw_batch_t:
+        return bsw_batch_t(self.n, self.q.data_ptr(), self.q_off.data_ptr(), self.q_len.data_ptr(),
+                           self.t.data_ptr(), self.t_off.data_ptr(), self.t_len.data_ptr(), self.h0.data_ptr(),
+                           None if self.w is None else self.w.data_ptr(), flags | BSW_DEVICE_PTRS)
+
+
+class Context:
+    """Owns a bsw_ctx_t."""
+
+    def __init__(self, params, mem_budget_bytes: int = 8 << 30):
+        self.params = params
+        self.handle = bsw_init(params.scoring, params.w, params.zdrop, params.end_bonus, mem_budget_bytes)
+
+    def close(self):
+        if self.handle:
+            bsw_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def extend_host(self, hb: HostBatch, flags: int = 0, stream: int | None = None):
+        """Host inputs -> (results int32 [N, 6], cells)."""
+        out = np.zeros((hb.n, 6), np.int32)
+        cells = ctypes.c_int64()
+        rc = bsw_extend_batch(self.handle, hb.struct(hb.flags | flags), out.ctypes.data,
+                              ctypes.addressof(cells), stream)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_extend_batch")
+        return out, cells.value
+
+    def extend_device(self, db: DeviceBatch, flags: int = 0, stream: int | None = None):
+        """Device inputs; enqueues on `stream` (a cudaStream_t as int) and returns."""
+        rc = bsw_extend_batch(self.handle, db.struct(flags), db.out.data_ptr(), db.cells.data_ptr(), stream)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_extend_batch")
+
+    def sync(self, stream: int | None = None):
+        rc = bsw_sync(self.handle, stream)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_sync")
+
+    def submit(self, hb: HostBatch, out: np.ndarray, flags: int = 0) -> int:
+        rc, ticket = bsw_stream_submit(self.handle, hb.struct(hb.flags | flags), out.ctypes.data)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_stream_submit")
+        return ticket
+
+    def poll(self, ticket: int, timeout_us: int = -1) -> int:
+        return bsw_stream_poll(self.handle, ticket, timeout_us)
+
+    def band_width(self, qlen: int, w: int | None = None) -> int:
+        return bsw_band_width(self.handle, qlen, self.params.w if w is None else w)

@@ -1,0 +1,808 @@
+// bsw_api.cu - C ABI and host runtime of the BSW library (see include/bsw.h).
+//
+// Host side of the batched extension: argument checks, a device-memory arena
+// held within the context's budget, staging of host inputs, CUDA-graph replay
+// for device-pointer calls, and the serving loop (bsw_stream_submit/poll):
+// a server thread that admits queued batches into a few execution lanes (one
+// stream set and buffer set each), merges small batches into one launch and
+// overlaps lanes on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bsw.h"
+#include "bsw_device.cuh"
+#include "bsw_launch.h"
+
+using namespace bsw;
+
+namespace {
+
+constexpr uint32_t kKnownFlags = BSW_DEVICE_PTRS | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32 |
+                                 BSW_PLAIN_KERNEL | BSW_NO_GRAPH | BSW_COPY_INPUTS;
+constexpr int kServeLanes = 3;
+constexpr int64_t kMergePairs = 1 << 20;   // the serving loop merges queued batches up to this size
+constexpr int kGraphCache = 8;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Budget {
+    int64_t cap = 0;
+    std::atomic<int64_t> used{0};
+};
+
+// One growable device allocation, charged to the context's budget.
+struct DevBuf {
+    uint8_t *p = nullptr;
+    size_t cap = 0;
+
+    int reserve(size_t bytes, Budget &B, bool *moved = nullptr)
+    {
+        if (bytes <= cap) return BSW_OK;
+        size_t want = align_up(std::max(bytes, cap + cap / 4), 1 << 20);
+        if (B.used.load() - (int64_t)cap + (int64_t)want > B.cap) want = align_up(bytes, 256);
+        if (B.used.load() - (int64_t)cap + (int64_t)want > B.cap) return BSW_EBUDGET;
+        release(B);
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return BSW_ENOMEM;
+        }
+        cap = want;
+        B.used += (int64_t)want;
+        if (moved) *moved = true;
+        return BSW_OK;
+    }
+    void release(Budget &B)
+    {
+        if (p) {
+            cudaFree(p);
+            B.used -= (int64_t)cap;
+        }
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// Byte offsets of the work buffers inside one allocation.
+struct WorkLayout {
+    size_t key, order, rerun, hist, cursor, cls_start, cls_count, cls_next, cells, status, slots, total;
+    int64_t slot_bytes;
+};
+
+WorkLayout work_layout(int64_t n, int64_t slot_bytes, int nwarps)
+{
+    WorkLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    L.key = take(4 * (size_t)n);
+    L.order = take(4 * (size_t)n);
+    L.rerun = take(4 * (size_t)n);
+    L.hist = take(4 * kNumBins);
+    L.cursor = take(4 * kNumBins);
+    L.cls_start = take(4 * (kNumClass + 1));
+    L.cls_count = take(4 * (kNumClass + 1));
+    L.cls_next = take(4 * (kNumClass + 1));
+    L.cells = take(8);
+    L.status = take(4);
+    L.slots = take((size_t)slot_bytes * (size_t)nwarps);
+    L.total = o;
+    L.slot_bytes = slot_bytes;
+    return L;
+}
+
+Work make_work(uint8_t *base, const WorkLayout &L)
+{
+    Work W;
+    W.key = (int32_t *)(base + L.key);
+    W.order = (int32_t *)(base + L.order);
+    W.rerun = (int32_t *)(base + L.rerun);
+    W.hist = (uint32_t *)(base + L.hist);
+    W.cursor = (uint32_t *)(base + L.cursor);
+    W.cls_start = (int32_t *)(base + L.cls_start);
+    W.cls_count = (int32_t *)(base + L.cls_count);
+    W.cls_next = (uint32_t *)(base + L.cls_next);
+    W.cells = (unsigned long long *)(base + L.cells);
+    W.status = (uint32_t *)(base + L.status);
+    W.slots = base + L.slots;
+    W.slot_bytes_per_warp = L.slot_bytes;
+    return W;
+}
+
+int64_t slot_bytes_for(int maxn) { return (int64_t)align_up((size_t)(maxn + 1 + 32 * 8) * 8, 256); }
+
+// One execution lane: a stream set, work buffers and staging buffers.
+struct Lane {
+    Streams S{};
+    cudaEvent_t done = nullptr;
+    DevBuf work, io;
+    WorkLayout wl{};
+    bool work_dirty = true;     // histogram must be zeroed before the next launch
+    uint8_t *pinned = nullptr;  // host staging (serving lanes)
+    size_t pinned_cap = 0;
+
+    int create()
+    {
+        if (cudaStreamCreateWithFlags(&S.main, cudaStreamNonBlocking) != cudaSuccess) return BSW_ECUDA;
+        for (int k = 0; k < 3; ++k) {
+            if (cudaStreamCreateWithFlags(&S.side[k], cudaStreamNonBlocking) != cudaSuccess) return BSW_ECUDA;
+            if (cudaEventCreateWithFlags(&S.join[k], cudaEventDisableTiming) != cudaSuccess) return BSW_ECUDA;
+        }
+        if (cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess) return BSW_ECUDA;
+        if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) return BSW_ECUDA;
+        return BSW_OK;
+    }
+    void destroy(Budget &B)
+    {
+        if (S.main) cudaStreamSynchronize(S.main);
+        for (int k = 0; k < 3; ++k) {
+            if (S.side[k]) { cudaStreamSynchronize(S.side[k]); cudaStreamDestroy(S.side[k]); }
+            if (S.join[k]) cudaEventDestroy(S.join[k]);
+        }
+        if (S.fork) cudaEventDestroy(S.fork);
+        if (done) cudaEventDestroy(done);
+        if (S.main) cudaStreamDestroy(S.main);
+        work.release(B);
+        io.release(B);
+        if (pinned) cudaFreeHost(pinned);
+        pinned = nullptr;
+    }
+    // Work buffers for n pairs and queries up to maxn; sets *moved on reallocation.
+    int ensure_work(int64_t n, int maxn, int sms, Budget &B, bool *moved)
+    {
+        const int64_t sb = slot_bytes_for(maxn);
+        const bool fits = wl.total && n <= (int64_t)(wl.order - wl.key) / 4 && sb <= wl.slot_bytes;
+        if (fits && work.p) return BSW_OK;
+        const int64_t n_cap = std::max<int64_t>(n, (int64_t)((wl.order - wl.key) / 4));
+        const int64_t sb_cap = std::max<int64_t>(sb, wl.slot_bytes);
+        WorkLayout L = work_layout(n_cap, sb_cap, warp_slots_needed(sms));
+        bool m2 = false;
+        int rc = work.reserve(L.total, B, &m2);
+        if (rc != BSW_OK) return rc;
+        wl = L;
+        work_dirty = true;
+        if (moved) *moved = true;
+        return BSW_OK;
+    }
+    int ensure_pinned(size_t bytes)
+    {
+        if (bytes <= pinned_cap) return BSW_OK;
+        if (pinned) cudaFreeHost(pinned);
+        pinned = nullptr;
+        pinned_cap = 0;
+        size_t want = align_up(bytes + bytes / 4, 1 << 20);
+        if (cudaMallocHost(&pinned, want) != cudaSuccess) {
+            cudaGetLastError();
+            pinned = nullptr;
+            return BSW_ENOMEM;
+        }
+        pinned_cap = want;
+        return BSW_OK;
+    }
+};
+
+// Host-side check of one batch; fills the packed-byte extents and max query length.
+struct Extents {
+    int64_t q_lo = INT64_MAX, q_hi = 0, t_lo = INT64_MAX, t_hi = 0;
+    int maxn = 0;
+};
+
+int check_host_batch(const bsw_batch_t *b, const Params &P, Extents *x)
+{
+    const int64_t N = b->n_pairs;
+    for (int64_t k = 0; k < N; ++k) {
+        const int32_t n = b->q_len[k], m = b->t_len[k], h0 = b->h0[k];
+        const int64_t qo = b->q_off[k], to = b->t_off[k];
+        const int32_t w = b->w_override ? b->w_override[k] : P.w;
+        if (n < 0 || m < 0 || h0 < 0 || w < 0 || qo < 0 || to < 0 || (qo & 3) || (to & 3)) return BSW_EINVAL;
+        if (n > 0 && m > 0) {
+            if ((int64_t)h0 + (int64_t)P.a * std::min(n, m) >= (1ll << 30)) return BSW_EINVAL;
+            if (n > kLongMax) return BSW_EINVAL;
+            x->q_lo = std::min(x->q_lo, qo / 4);
+            x->q_hi = std::max(x->q_hi, (qo + n + 3) / 4);
+            x->t_lo = std::min(x->t_lo, to / 4);
+            x->t_hi = std::max(x->t_hi, (to + m + 3) / 4);
+            x->maxn = std::max(x->maxn, n);
+        }
+    }
+    if (x->q_lo > x->q_hi) x->q_lo = x->q_hi = 0;
+    if (x->t_lo > x->t_hi) x->t_lo = x->t_hi = 0;
+    return BSW_OK;
+}
+
+// Device layout of a staged batch.
+struct IoLayout {
+    size_t q, t, q_off, q_len, t_off, t_len, h0, w, out, cells, status, in_end, total;
+};
+
+IoLayout io_layout(int64_t N, int64_t qbytes, int64_t tbytes)
+{
+    IoLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    L.q = take((size_t)qbytes);
+    L.t = take((size_t)tbytes);
+    L.q_off = take(8 * (size_t)N);
+    L.q_len = take(4 * (size_t)N);
+    L.t_off = take(8 * (size_t)N);
+    L.t_len = take(4 * (size_t)N);
+    L.h0 = take(4 * (size_t)N);
+    L.w = take(4 * (size_t)N);
+    L.in_end = o;
+    L.out = take(sizeof(bsw_result_t) * (size_t)N);
+    L.cells = take(8);
+    L.status = take(4);
+    L.total = o;
+    return L;
+}
+
+int status_to_rc(uint32_t st) { return st ? BSW_EINVAL : BSW_OK; }
+
+int cuda_rc(cudaError_t e)
+{
+    if (e == cudaSuccess) return BSW_OK;
+    cudaGetLastError();
+    return BSW_ECUDA;
+}
+
+// ---------------------------------------------------------------- serving
+
+struct Request {
+    uint64_t ticket = 0;
+    bsw_batch_t b{};
+    bsw_result_t *out = nullptr;
+    Extents ext;
+    std::vector<uint8_t> own;   // owned input copies (BSW_COPY_INPUTS)
+    int status = BSW_PENDING;
+    int64_t out_pos = 0;        // position of this request's pairs in the merged launch
+};
+
+}  // namespace
+
+struct bsw_ctx {
+    Params P{};
+    int device = 0;
+    int sms = 0;
+    Budget budget;
+    Lane sync;
+    uint32_t *h_status = nullptr;     // pinned
+    unsigned long long *h_cells = nullptr;
+
+    struct GEntry {
+        bsw_batch_t b;
+        void *out, *cells;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GEntry> graphs;
+
+    // serving
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> tickets;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    bool server_started = false;
+    std::thread server;
+    Lane serve_lane[kServeLanes];
+    bool lane_created[kServeLanes] = {false, false, false};
+    std::vector<Request *> lane_reqs[kServeLanes];
+    int64_t lane_pairs[kServeLanes] = {0, 0, 0};
+    size_t lane_out_off[kServeLanes] = {0, 0, 0};
+    IoLayout lane_io[kServeLanes];
+    bool lane_busy[kServeLanes] = {false, false, false};
+};
+
+namespace {
+
+void clear_graphs(bsw_ctx *c)
+{
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+bool same_batch(const bsw_batch_t &a, const bsw_batch_t &b)
+{
+    return a.n_pairs == b.n_pairs && a.q == b.q && a.q_off == b.q_off && a.q_len == b.q_len && a.t == b.t &&
+           a.t_off == b.t_off && a.t_len == b.t_len && a.h0 == b.h0 && a.w_override == b.w_override &&
+           a.flags == b.flags;
+}
+
+// Enqueue one launch of a device-resident batch on the lane's streams (S.main
+// may be replaced by the caller's stream).  Zeroes cells/status first.
+cudaError_t enqueue_launch(bsw_ctx *c, Lane &lane, const Streams &S, const Batch &B, Work W, bool plain,
+                           bool reset_status)
+{
+    cudaError_t e;
+    if (lane.work_dirty) {
+        if ((e = cudaMemsetAsync(W.hist, 0, 4 * kNumBins, S.main)) != cudaSuccess) return e;
+        lane.work_dirty = false;
+    }
+    if ((e = cudaMemsetAsync(W.cells, 0, 8, S.main)) != cudaSuccess) return e;
+    if (reset_status && (e = cudaMemsetAsync(W.status, 0, 4, S.main)) != cudaSuccess) return e;
+    return plain ? launch_plain(B, c->P, W, S.main, c->sms) : launch_batched(B, c->P, W, S, c->sms);
+}
+
+int extend_host(bsw_ctx *c, const bsw_batch_t *b, bsw_result_t *out, int64_t *cells_out, cudaStream_t user)
+{
+    Extents x;
+    int rc = check_host_batch(b, c->P, &x);
+    if (rc != BSW_OK) return rc;
+    const int64_t N = b->n_pairs;
+    // Only the packed bytes the pairs use are staged; the device base pointers
+    // are shifted back by the first used byte so the caller's offsets stay valid.
+    const int64_t qbytes = x.q_hi - x.q_lo, tbytes = x.t_hi - x.t_lo;
+    IoLayout L = io_layout(N, qbytes, tbytes);
+    Lane &lane = c->sync;
+    bool moved = false;
+    if ((rc = lane.io.reserve(L.total, c->budget, &moved)) != BSW_OK) return rc;
+    if ((rc = lane.ensure_work(N, std::max(x.maxn, kShortMax), c->sms, c->budget, &moved)) != BSW_OK) return rc;
+    if (moved) clear_graphs(c);
+    uint8_t *d = lane.io.p;
+    cudaStream_t st = lane.S.main;
+    cudaError_t e;
+    if (user) {
+        if ((e = cudaEventRecord(lane.done, user)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaStreamWaitEvent(st, lane.done, 0)) != cudaSuccess) return cuda_rc(e);
+    }
+    struct Cp { size_t off; const void *src; size_t bytes; } cps[] = {
+        {L.q, b->q + x.q_lo, (size_t)qbytes}, {L.t, b->t + x.t_lo, (size_t)tbytes},
+        {L.q_off, b->q_off, 8 * (size_t)N}, {L.q_len, b->q_len, 4 * (size_t)N},
+        {L.t_off, b->t_off, 8 * (size_t)N}, {L.t_len, b->t_len, 4 * (size_t)N},
+        {L.h0, b->h0, 4 * (size_t)N}, {L.w, b->w_override, b->w_override ? 4 * (size_t)N : 0}};
+    for (const Cp &cp : cps)
+        if (cp.bytes && (e = cudaMemcpyAsync(d + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+    Batch B{N, d + L.q - x.q_lo, (const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len), d + L.t - x.t_lo,
+            (const int64_t *)(d + L.t_off), (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
+            b->w_override ? (const int32_t *)(d + L.w) : nullptr, (bsw_result_t *)(d + L.out)};
+    Work W = make_work(lane.work.p, lane.wl);
+    if ((e = enqueue_launch(c, lane, lane.S, B, W, (b->flags & BSW_PLAIN_KERNEL) != 0, true)) != cudaSuccess) {
+        lane.work_dirty = true;
+        return cuda_rc(e);
+    }
+    if ((e = cudaMemcpyAsync(out, d + L.out, sizeof(bsw_result_t) * (size_t)N, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaMemcpyAsync(c->h_cells, W.cells, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaMemcpyAsync(c->h_status, W.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { lane.work_dirty = true; return cuda_rc(e); }
+    if (cells_out) *cells_out = (int64_t)*c->h_cells;
+    return status_to_rc(*c->h_status);
+}
+
+int extend_device(bsw_ctx *c, const bsw_batch_t *b, bsw_result_t *out, int64_t *cells_out, cudaStream_t user)
+{
+    const int64_t N = b->n_pairs;
+    Lane &lane = c->sync;
+    bool moved = false;
+    int rc = lane.ensure_work(N, kLongMax, c->sms, c->budget, &moved);
+    if (rc != BSW_OK) return rc;
+    if (moved) clear_graphs(c);
+    cudaStream_t st = user ? user : lane.S.main;
+    Batch B{N, b->q, b->q_off, b->q_len, b->t, b->t_off, b->t_len, b->h0, b->w_override, out};
+    Work W = make_work(lane.work.p, lane.wl);
+    if (cells_out) W.cells = (unsigned long long *)cells_out;
+    const bool plain = (b->flags & BSW_PLAIN_KERNEL) != 0;
+    cudaError_t e;
+    if (b->flags & BSW_NO_GRAPH) {
+        Streams S = lane.S;
+        S.main = st;
+        if ((e = enqueue_launch(c, lane, S, B, W, plain, false)) != cudaSuccess) {
+            lane.work_dirty = true;
+            return cuda_rc(e);
+        }
+        return BSW_OK;
+    }
+    for (auto &g : c->graphs)
+        if (same_batch(g.b, *b) && g.out == (void *)out && g.cells == (void *)cells_out)
+            return cuda_rc(cudaGraphLaunch(g.exec, st));
+    if (lane.work_dirty) {   // make the zeroing part of the stream order, not of the graph
+        if ((e = cudaMemsetAsync(W.hist, 0, 4 * kNumBins, st)) != cudaSuccess) return cuda_rc(e);
+        lane.work_dirty = false;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if ((e = cudaStreamBeginCapture(lane.S.main, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_rc(e);
+    cudaError_t le = enqueue_launch(c, lane, lane.S, B, W, plain, false);
+    e = cudaStreamEndCapture(lane.S.main, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        lane.work_dirty = true;
+        return cuda_rc(le != cudaSuccess ? le : e);
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if ((int)c->graphs.size() >= kGraphCache) {
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back({*b, (void *)out, (void *)cells_out, exec});
+    return cuda_rc(cudaGraphLaunch(exec, st));
+}
+
+// ------------------------------------------------------------ serving loop
+
+// Stage the lane's requests into pinned memory, copy to the device, launch,
+// copy results back.  Called by the server thread without the lock.
+int serve_launch(bsw_ctx *c, int li)
+{
+    Lane &lane = c->serve_lane[li];
+    std::vector<Request *> &reqs = c->lane_reqs[li];
+    int64_t N = 0, qb = 0, tb = 0;
+    int maxn = 0;
+    for (Request *r : reqs) {
+        r->out_pos = N;
+        N += r->b.n_pairs;
+        qb += r->ext.q_hi - r->ext.q_lo;
+        tb += r->ext.t_hi - r->ext.t_lo;
+        maxn = std::max(maxn, r->ext.maxn);
+    }
+    IoLayout L = io_layout(N, qb, tb);
+    int rc;
+    if ((rc = lane.io.reserve(L.total, c->budget)) != BSW_OK) return rc;
+    if ((rc = lane.ensure_work(N, std::max(maxn, kShortMax), c->sms, c->budget, nullptr)) != BSW_OK) return rc;
+    if ((rc = lane.ensure_pinned(L.total)) != BSW_OK) return rc;
+    uint8_t *h = lane.pinned;
+    int64_t qpos = 0, tpos = 0, k0 = 0;
+    for (Request *r : reqs) {
+        const bsw_batch_t &b = r->b;
+        const int64_t n = b.n_pairs;
+        std::memcpy(h + L.q + qpos, b.q + r->ext.q_lo, (size_t)(r->ext.q_hi - r->ext.q_lo));
+        std::memcpy(h + L.t + tpos, b.t + r->ext.t_lo, (size_t)(r->ext.t_hi - r->ext.t_lo));
+        int64_t *qo = (int64_t *)(h + L.q_off) + k0, *to = (int64_t *)(h + L.t_off) + k0;
+        const int64_t dq = 4 * (qpos - r->ext.q_lo), dt = 4 * (tpos - r->ext.t_lo);
+        for (int64_t k = 0; k < n; ++k) {
+            // pairs that are never read (empty sides) keep a valid offset of 0
+            const bool used = b.q_len[k] > 0 && b.t_len[k] > 0;
+            qo[k] = used ? b.q_off[k] + dq : 0;
+            to[k] = used ? b.t_off[k] + dt : 0;
+        }
+        std::memcpy((int32_t *)(h + L.q_len) + k0, b.q_len, 4 * (size_t)n);
+        std::memcpy((int32_t *)(h + L.t_len) + k0, b.t_len, 4 * (size_t)n);
+        std::memcpy((int32_t *)(h + L.h0) + k0, b.h0, 4 * (size_t)n);
+        int32_t *wv = (int32_t *)(h + L.w) + k0;
+        if (b.w_override) std::memcpy(wv, b.w_override, 4 * (size_t)n);
+        else for (int64_t k = 0; k < n; ++k) wv[k] = c->P.w;
+        qpos += r->ext.q_hi - r->ext.q_lo;
+        tpos += r->ext.t_hi - r->ext.t_lo;
+        k0 += n;
+    }
+    cudaStream_t st = lane.S.main;
+    uint8_t *d = lane.io.p;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d, h, L.in_end, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_rc(e);
+    Batch B{N, d + L.q, (const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len), d + L.t,
+            (const int64_t *)(d + L.t_off), (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
+            (const int32_t *)(d + L.w), (bsw_result_t *)(d + L.out)};
+    Work W = make_work(lane.work.p, lane.wl);
+    if ((e = enqueue_launch(c, lane, lane.S, B, W, false, true)) != cudaSuccess) {
+        lane.work_dirty = true;
+        return cuda_rc(e);
+    }
+    if ((e = cudaMemcpyAsync(h + L.out, d + L.out, sizeof(bsw_result_t) * (size_t)N, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaMemcpyAsync(h + L.status, W.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaEventRecord(lane.done, st)) != cudaSuccess) return cuda_rc(e);
+    c->lane_io[li] = L;
+    c->lane_pairs[li] = N;
+    return BSW_OK;
+}
+
+void finish_lane(bsw_ctx *c, int li, int rc)
+{
+    Lane &lane = c->serve_lane[li];
+    const IoLayout &L = c->lane_io[li];
+    if (rc == BSW_OK) rc = status_to_rc(*(uint32_t *)(lane.pinned + L.status));
+    for (Request *r : c->lane_reqs[li]) {
+        if (rc == BSW_OK)
+            std::memcpy(r->out, lane.pinned + L.out + sizeof(bsw_result_t) * (size_t)r->out_pos,
+                        sizeof(bsw_result_t) * (size_t)r->b.n_pairs);
+        r->status = rc;
+    }
+    c->lane_reqs[li].clear();
+    c->lane_busy[li] = false;
+}
+
+void server_main(bsw_ctx *c)
+{
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(c->mu);
+    for (;;) {
+        bool progressed = false;
+        // completions
+        for (int li = 0; li < kServeLanes; ++li) {
+            if (!c->lane_busy[li]) continue;
+            cudaError_t q = cudaEventQuery(c->serve_lane[li].done);
+            if (q == cudaErrorNotReady) continue;
+            finish_lane(c, li, q == cudaSuccess ? BSW_OK : cuda_rc(q));
+            progressed = true;
+        }
+        if (progressed) c->cv_done.notify_all();
+        // admissions: continuous batching into free lanes
+        for (int li = 0; li < kServeLanes && !c->queue.empty(); ++li) {
+            if (c->lane_busy[li]) continue;
+            if (!c->lane_created[li]) {
+                if (c->serve_lane[li].create() != BSW_OK) continue;
+                c->lane_created[li] = true;
+            }
+            std::vector<Request *> &reqs = c->lane_reqs[li];
+            int64_t pairs = 0;
+            while (!c->queue.empty() && (reqs.empty() || pairs + c->queue.front()->b.n_pairs <= kMergePairs)) {
+                pairs += c->queue.front()->b.n_pairs;
+                reqs.push_back(c->queue.front());
+                c->queue.pop_front();
+            }
+            c->lane_busy[li] = true;
+            lk.unlock();
+            int rc = serve_launch(c, li);
+            lk.lock();
+            if (rc == BSW_EBUDGET) {
+                bool others = false;
+                for (int k = 0; k < kServeLanes; ++k) others |= (k != li && c->lane_busy[k]);
+                if (others) {   // wait for memory held by other lanes
+                    for (auto it = reqs.rbegin(); it != reqs.rend(); ++it) c->queue.push_front(*it);
+                    reqs.clear();
+                    c->lane_busy[li] = false;
+                    c->serve_lane[li].io.release(c->budget);
+                    break;
+                }
+            }
+            if (rc != BSW_OK) {
+                finish_lane(c, li, rc);
+                c->cv_done.notify_all();
+            }
+            progressed = true;
+        }
+        bool busy = false;
+        for (int li = 0; li < kServeLanes; ++li) busy |= c->lane_busy[li];
+        if (c->stop && !busy && c->queue.empty()) break;
+        if (!progressed) {
+            if (busy) c->cv_work.wait_for(lk, std::chrono::microseconds(50));
+            else c->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char *bsw_version(void) { return "bsw-gb300 1.0 (sm_103a)"; }
+
+const char *bsw_strerror(int code)
+{
+    switch (code) {
+    case BSW_OK: return "ok";
+    case BSW_PENDING: return "pending";
+    case BSW_EINVAL: return "invalid argument or input value";
+    case BSW_ENOMEM: return "out of memory";
+    case BSW_EBUDGET: return "batch exceeds the device-memory budget";
+    case BSW_ECUDA: return "CUDA error";
+    case BSW_ETIMEOUT: return "timed out";
+    case BSW_ENOTFOUND: return "unknown ticket";
+    case BSW_ESTATE: return "context cannot accept the call";
+    default: return "unknown error code";
+    }
+}
+
+int bsw_pack_2bit(const uint8_t *in, int64_t n, uint8_t *out)
+{
+    if (n < 0 || (n > 0 && (!in || !out))) return BSW_EINVAL;
+    for (int64_t k = 0; k < (n + 3) / 4; ++k) out[k] = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int v;
+        switch (in[k]) {
+        case 0: case 'A': case 'a': v = 0; break;
+        case 1: case 'C': case 'c': v = 1; break;
+        case 2: case 'G': case 'g': v = 2; break;
+        case 3: case 'T': case 't': v = 3; break;
+        default: return BSW_EINVAL;
+        }
+        out[k >> 2] |= (uint8_t)(v << (2 * (k & 3)));
+    }
+    return BSW_OK;
+}
+
+int32_t bsw_band_width(const bsw_ctx_t *ctx, int32_t qlen, int32_t w)
+{
+    if (!ctx || qlen < 0 || w < 0) return -1;
+    const Params &P = ctx->P;
+    auto cap = [&](int o, int e) {
+        long long x = (long long)qlen * P.a + P.end_bonus - o + e;
+        long long k = x / e;
+        return (int32_t)(k > 1 ? k : 1);
+    };
+    return std::min(w, std::min(cap(P.o_ins, P.e_ins), cap(P.o_del, P.e_del)));
+}
+
+int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonus, int64_t mem_budget_bytes,
+             bsw_ctx_t **out)
+{
+    if (!sc || !out || w < 0 || end_bonus < 0 || mem_budget_bytes <= 0) return BSW_EINVAL;
+    if (sc->match <= 0 || sc->match > 127 || sc->mismatch <= 0 || sc->mismatch > 128 || sc->o_del < 0 ||
+        sc->o_ins < 0 || sc->e_del <= 0 || sc->e_ins <= 0 || sc->o_del > (1 << 20) || sc->o_ins > (1 << 20) ||
+        sc->e_del > (1 << 20) || sc->e_ins > (1 << 20) || end_bonus > (1 << 20))
+        return BSW_EINVAL;
+    *out = nullptr;
+    bsw_ctx *c = new (std::nothrow) bsw_ctx();
+    if (!c) return BSW_ENOMEM;
+    c->P = Params{sc->match, sc->mismatch, sc->o_del, sc->e_del, sc->o_ins, sc->e_ins, w, zdrop, end_bonus, 0u};
+    c->budget.cap = mem_budget_bytes;
+    int rc = BSW_OK;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        rc = BSW_ECUDA;
+    }
+    if (rc == BSW_OK) rc = c->sync.create();
+    if (rc == BSW_OK && prepare_kernels(c->sms) != cudaSuccess) rc = BSW_ECUDA;
+    if (rc == BSW_OK && (cudaMallocHost(&c->h_status, 4) != cudaSuccess ||
+                         cudaMallocHost(&c->h_cells, 8) != cudaSuccess))
+        rc = BSW_ENOMEM;
+    if (rc != BSW_OK) {
+        cudaGetLastError();
+        bsw_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return BSW_OK;
+}
+
+int bsw_extend_batch(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, int64_t *cells_out, void *stream)
+{
+    if (!ctx || !b) return BSW_EINVAL;
+    if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~kKnownFlags)) return BSW_EINVAL;
+    const uint32_t forced = b->flags & (BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32);
+    if (forced & (forced - 1)) return BSW_EINVAL;
+    const bool dev = (b->flags & BSW_DEVICE_PTRS) != 0;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+    if (b->n_pairs == 0) {
+        if (cells_out) {
+            if (dev) return cuda_rc(cudaMemsetAsync(cells_out, 0, 8, (cudaStream_t)stream));
+            *cells_out = 0;
+        }
+        return BSW_OK;
+    }
+    if (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out) return BSW_EINVAL;
+    if (dev) return extend_device(ctx, b, out, cells_out, (cudaStream_t)stream);
+    return extend_host(ctx, b, out, cells_out, (cudaStream_t)stream);
+}
+
+int bsw_sync(bsw_ctx_t *ctx, void *stream)
+{
+    if (!ctx) return BSW_EINVAL;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->sync.S.main;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if (!ctx->sync.work.p) return BSW_OK;
+    Work W = make_work(ctx->sync.work.p, ctx->sync.wl);
+    if ((e = cudaMemcpy(ctx->h_status, W.status, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaMemset(W.status, 0, 4)) != cudaSuccess) return cuda_rc(e);
+    return status_to_rc(*ctx->h_status);
+}
+
+int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, uint64_t *ticket)
+{
+    if (!ctx || !b || !ticket) return BSW_EINVAL;
+    if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~kKnownFlags)) return BSW_EINVAL;
+    if (b->flags & (BSW_DEVICE_PTRS | BSW_PLAIN_KERNEL | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32))
+        return BSW_EINVAL;   // the serving loop runs the default batched path on host inputs
+    if (b->n_pairs > 0 && (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out))
+        return BSW_EINVAL;
+    Request *r = new (std::nothrow) Request();
+    if (!r) return BSW_ENOMEM;
+    r->b = *b;
+    r->out = out;
+    int rc = check_host_batch(b, ctx->P, &r->ext);
+    if (rc == BSW_OK) {
+        const int64_t N = b->n_pairs;
+        IoLayout L = io_layout(N, r->ext.q_hi - r->ext.q_lo, r->ext.t_hi - r->ext.t_lo);
+        WorkLayout W = work_layout(N, slot_bytes_for(std::max(r->ext.maxn, kShortMax)), warp_slots_needed(ctx->sms));
+        if ((int64_t)(L.total + W.total) > ctx->budget.cap) rc = BSW_EBUDGET;
+    }
+    if (rc == BSW_OK && (b->flags & BSW_COPY_INPUTS) && b->n_pairs > 0) {
+        const int64_t N = b->n_pairs;
+        const size_t qb = (size_t)(r->ext.q_hi - r->ext.q_lo), tb = (size_t)(r->ext.t_hi - r->ext.t_lo);
+        const size_t total = qb + tb + 8 * (size_t)N * 2 + 4 * (size_t)N * (b->w_override ? 4 : 3);
+        try {
+            r->own.resize(total);
+        } catch (...) {
+            rc = BSW_ENOMEM;
+        }
+        if (rc == BSW_OK) {
+            uint8_t *p = r->own.data();
+            std::memcpy(p, b->q + r->ext.q_lo, qb);
+            r->b.q = p - r->ext.q_lo;   // keep the caller's offsets valid
+            p += qb;
+            std::memcpy(p, b->t + r->ext.t_lo, tb);
+            r->b.t = p - r->ext.t_lo;
+            p += tb;
+            auto dup = [&](const void *src, size_t bytes) { std::memcpy(p, src, bytes); void *d = p; p += bytes; return d; };
+            r->b.q_off = (const int64_t *)dup(b->q_off, 8 * (size_t)N);
+            r->b.t_off = (const int64_t *)dup(b->t_off, 8 * (size_t)N);
+            r->b.q_len = (const int32_t *)dup(b->q_len, 4 * (size_t)N);
+            r->b.t_len = (const int32_t *)dup(b->t_len, 4 * (size_t)N);
+            r->b.h0 = (const int32_t *)dup(b->h0, 4 * (size_t)N);
+            if (b->w_override) r->b.w_override = (const int32_t *)dup(b->w_override, 4 * (size_t)N);
+        }
+    }
+    if (rc != BSW_OK) {
+        delete r;
+        return rc;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->stop) {
+        delete r;
+        return BSW_ESTATE;
+    }
+    r->ticket = ctx->next_ticket++;
+    *ticket = r->ticket;
+    ctx->tickets[r->ticket] = r;
+    if (b->n_pairs == 0) {
+        r->status = BSW_OK;
+        return BSW_OK;
+    }
+    ctx->queue.push_back(r);
+    if (!ctx->server_started) {
+        ctx->server = std::thread(server_main, ctx);
+        ctx->server_started = true;
+    }
+    ctx->cv_work.notify_one();
+    return BSW_OK;
+}
+
+int bsw_stream_poll(bsw_ctx_t *ctx, uint64_t ticket, int32_t timeout_us)
+{
+    if (!ctx) return BSW_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return BSW_ENOTFOUND;
+    Request *r = it->second;
+    auto ready = [&] { return r->status != BSW_PENDING; };
+    if (!ready()) {
+        if (timeout_us < 0) ctx->cv_done.wait(lk, ready);
+        else if (timeout_us > 0) ctx->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+    }
+    if (!ready()) return BSW_PENDING;
+    const int rc = r->status;
+    ctx->tickets.erase(ticket);
+    delete r;
+    return rc;
+}
+
+void bsw_destroy(bsw_ctx_t *ctx)
+{
+    if (!ctx) return;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->stop = true;
+    }
+    ctx->cv_work.notify_all();
+    if (ctx->server_started) ctx->server.join();
+    cudaSetDevice(ctx->device);
+    clear_graphs(ctx);
+    for (int li = 0; li < kServeLanes; ++li)
+        if (ctx->lane_created[li]) ctx->serve_lane[li].destroy(ctx->budget);
+    ctx->sync.destroy(ctx->budget);
+    for (auto &kv : ctx->tickets) delete kv.second;
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->h_cells) cudaFreeHost(ctx->h_cells);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// bsw_device.cuh - device-side types shared by the BSW kernels and their launcher.
+#pragma once
+
+#include <cstdint>
+#include "bsw.h"
+
+namespace bsw {
+
+// Query lengths up to kShortMax run in the per-thread (inter-task) kernels;
+// longer ones, and every pair of the 32-bit re-run, in the warp-per-pair kernel.
+constexpr int kShortMax = 256;
+// Longest query the warp-per-pair kernel's slot scratch is sized for.
+constexpr int kLongMax = 32768;
+
+// Pair classes.  Classes 0-3: 8-bit lanes for query lengths (128,256], (64,128],
+// (32,64], [1,32]; 4-7: the same with 16-bit lanes; 8: warp per pair with 16-bit
+// slots; 9: warp per pair with 32-bit slots; 10: the re-run list (32-bit).
+constexpr int kNumClass = 10;
+constexpr int kRerun = 10;
+
+// Counting-sort bins.  Within a class the bins run from long to short queries,
+// so the persistent kernels take the longest work first.
+constexpr int kBinU8 = 0, kBinI16 = 256, kBinW16 = 512, kBinW32 = 1152, kNumBins = 1792;
+
+// Status bits written by the kernels.
+constexpr uint32_t kStInval = 1u;      // an input value is out of range
+constexpr uint32_t kStTooLong = 2u;    // a query exceeds the slot scratch
+
+struct Params {
+    int32_t a, b, o_del, e_del, o_ins, e_ins, w, zdrop, end_bonus;
+    uint32_t flags;
+};
+
+struct Batch {
+    int64_t n;
+    const uint8_t *q;
+    const int64_t *q_off;
+    const int32_t *q_len;
+    const uint8_t *t;
+    const int64_t *t_off;
+    const int32_t *t_len;
+    const int32_t *h0;
+    const int32_t *w_override;
+    bsw_result_t *out;
+};
+
+// Device scratch for one batch launch (allocated and owned by the host runtime).
+struct Work {
+    int32_t *key;              // [n] counting-sort bin, -1 = done or invalid
+    int32_t *order;            // [n] pair ids grouped by bin
+    uint32_t *hist;            // [kNumBins], zero between launches
+    uint32_t *cursor;          // [kNumBins]
+    int32_t *cls_start;        // [kNumClass + 1]
+    int32_t *cls_count;        // [kNumClass + 1]
+    uint32_t *cls_next;        // [kNumClass + 1] work counters of the persistent kernels
+    int32_t *rerun;            // [n] pairs to redo with 32-bit lanes
+    unsigned long long *cells; // DP cells computed
+    uint32_t *status;          // kSt* bits
+    uint8_t *slots;            // warp-per-pair slot scratch
+    int64_t slot_bytes_per_warp;
+};
+
+}  // namespace bsw

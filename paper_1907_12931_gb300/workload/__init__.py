@@ -97,13 +97,21 @@ class Workload:
         ql, tl = self.q_len[idx], self.t_len[idx]
         qo, qt = layout(ql)
         to, tt = layout(tl)
-        q = np.zeros(qt, np.uint8)
-        t = np.zeros(tt, np.uint8)
-        for k, p in enumerate(idx):
-            q[qo[k]:qo[k] + ql[k]] = self.q[self.q_off[p]:self.q_off[p] + ql[k]]
-            t[to[k]:to[k] + tl[k]] = self.t[self.t_off[p]:self.t_off[p] + tl[k]]
-        return Workload(self.name + "[subset]", self.params, q, qo, ql.copy(), t, to, tl.copy(),
+        return Workload(self.name + "[subset]", self.params, _gather(self.q, self.q_off[idx], ql, qo, qt), qo,
+                        ql.copy(), _gather(self.t, self.t_off[idx], tl, to, tt), to, tl.copy(),
                         self.h0[idx].copy())
+
+
+def _gather(seq, src_off, lengths, dst_off, total):
+    """Copy sequences [src_off, src_off + len) of seq to dst_off in a new array of `total` bases."""
+    out = np.zeros(total, np.uint8)
+    lengths = np.asarray(lengths, np.int64)
+    n = int(lengths.sum())
+    if n:
+        starts = np.repeat(np.cumsum(lengths) - lengths, lengths)
+        within = np.arange(n, dtype=np.int64) - starts
+        out[np.repeat(dst_off, lengths) + within] = seq[np.repeat(src_off, lengths) + within]
+    return out
 
 
 def layout(lengths: np.ndarray, align: int = 16):
