@@ -157,12 +157,13 @@ class HostBatch:
     def __init__(self, wl, w_override=None, flags: int = 0):
         self.q = bsw_pack_2bit(wl.q)
         self.t = bsw_pack_2bit(wl.t)
-        self.q_off = np.ascontiguousarray(wl.q_off, np.int64)
-        self.q_len = np.ascontiguousarray(wl.q_len, np.int32)
-        self.t_off = np.ascontiguousarray(wl.t_off, np.int64)
-        self.t_len = np.ascontiguousarray(wl.t_len, np.int32)
-        self.h0 = np.ascontiguousarray(wl.h0, np.int32)
-        self.w = None if w_override is None else np.ascontiguousarray(w_override, np.int32)
+        # own copies: the caller's arrays are never aliased
+        self.q_off = np.array(wl.q_off, np.int64, copy=True, order="C")
+        self.q_len = np.array(wl.q_len, np.int32, copy=True, order="C")
+        self.t_off = np.array(wl.t_off, np.int64, copy=True, order="C")
+        self.t_len = np.array(wl.t_len, np.int32, copy=True, order="C")
+        self.h0 = np.array(wl.h0, np.int32, copy=True, order="C")
+        self.w = None if w_override is None else np.array(w_override, np.int32, copy=True, order="C")
         self.n = int(self.q_len.shape[0])
         self.flags = flags
 
