@@ -150,21 +150,34 @@ __global__ void __launch_bounds__(1024) k_scan(Work W)
     if (t <= kNumClass) W.cls_next[t] = 0;
 }
 
-// Place every pair in its bin (warp-aggregated atomics on the cursors).
-__global__ void __launch_bounds__(512) k_scatter(int64_t n, Work W)
+// Place every pair in its bin.  Each block takes tiles of kScatterTile pairs:
+// ranks within the tile come from shared-memory atomics, and one global atomic
+// per non-empty bin reserves the tile's range in that bin.
+constexpr int kScatterThreads = 512, kScatterPer = 8, kScatterTile = kScatterThreads * kScatterPer;
+
+__global__ void __launch_bounds__(kScatterThreads) k_scatter(int64_t n, Work W)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t p = base + threadIdx.x;
-        const int key = p < n ? W.key[p] : -1;
-        const unsigned peers = __match_any_sync(kFull, key);
-        const int leader = __ffs(peers) - 1;
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        uint32_t pos = 0;
-        if (lane == leader && key >= 0) pos = atomicAdd(&W.cursor[key], (uint32_t)__popc(peers));
-        pos = __shfl_sync(kFull, pos, leader);
-        if (key >= 0) W.order[pos + rank] = (int32_t)p;
+    __shared__ uint32_t cnt[kNumBins];
+    __shared__ uint32_t base[kNumBins];
+    for (int64_t tile = (int64_t)blockIdx.x * kScatterTile; tile < n; tile += (int64_t)gridDim.x * kScatterTile) {
+        for (int k = threadIdx.x; k < kNumBins; k += kScatterThreads) cnt[k] = 0;
+        __syncthreads();
+        int key[kScatterPer];
+        uint32_t rank[kScatterPer];
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u) {
+            const int64_t p = tile + u * kScatterThreads + threadIdx.x;
+            key[u] = p < n ? W.key[p] : -1;
+            rank[u] = key[u] >= 0 ? atomicAdd(&cnt[key[u]], 1u) : 0u;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kNumBins; k += kScatterThreads)
+            if (cnt[k]) base[k] = atomicAdd(&W.cursor[k], cnt[k]);
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u)
+            if (key[u] >= 0) W.order[base[key[u]] + rank[u]] = (int32_t)(tile + u * kScatterThreads + threadIdx.x);
+        __syncthreads();
     }
 }
 
@@ -632,7 +645,8 @@ cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const
     const int cblocks = (int)((B.n + 511) / 512 < (int64_t)sms * 4 ? (B.n + 511) / 512 : (int64_t)sms * 4);
     k_classify<<<cblocks, 512, 0, S.main>>>(B, P, W);
     k_scan<<<1, 1024, 0, S.main>>>(W);
-    k_scatter<<<cblocks, 512, 0, S.main>>>(B.n, W);
+    const int sblocks = (int)((B.n + kScatterTile - 1) / kScatterTile < (int64_t)sms * 2 ? (B.n + kScatterTile - 1) / kScatterTile : (int64_t)sms * 2);
+    k_scatter<<<sblocks, kScatterThreads, 0, S.main>>>(B.n, W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Fork: classes run concurrently on the side streams so that one class's
     // tail overlaps the next class's start.
