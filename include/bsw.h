@@ -139,8 +139,8 @@ int bsw_extend_batch(bsw_ctx_t *ctx, const bsw_batch_t *batch, bsw_result_t *out
 int bsw_sync(bsw_ctx_t *ctx, void *cuda_stream);
 
 /*
- * Serving: queue a batch (host pointers; device pointers with
- * BSW_DEVICE_PTRS) and return at once with a ticket.  A server thread admits
+ * Serving: queue a batch of host inputs and return at once with a ticket
+ * (flags: 0 or BSW_COPY_INPUTS; the other flags are rejected).  A server thread admits
  * queued batches as stream slots and device memory within the budget free up,
  * merges small ones into one launch, and overlaps launches on several streams
  * (continuous batching).  Inputs and out must stay valid until poll returns

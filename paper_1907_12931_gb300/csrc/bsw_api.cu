@@ -322,17 +322,20 @@ bool same_batch(const bsw_batch_t &a, const bsw_batch_t &b)
 
 // Enqueue one launch of a device-resident batch on the lane's streams (S.main
 // may be replaced by the caller's stream).  Zeroes cells/status first.
-cudaError_t enqueue_launch(bsw_ctx *c, Lane &lane, const Streams &S, const Batch &B, Work W, bool plain,
+cudaError_t enqueue_launch(bsw_ctx *c, Lane &lane, const Streams &S, const Batch &B, Work W, uint32_t flags,
                            bool reset_status)
 {
     cudaError_t e;
+    Params P = c->P;
+    P.flags = flags;
+    const bool plain = (flags & BSW_PLAIN_KERNEL) != 0;
     if (lane.work_dirty) {
         if ((e = cudaMemsetAsync(W.hist, 0, 4 * kNumBins, S.main)) != cudaSuccess) return e;
         lane.work_dirty = false;
     }
     if ((e = cudaMemsetAsync(W.cells, 0, 8, S.main)) != cudaSuccess) return e;
     if (reset_status && (e = cudaMemsetAsync(W.status, 0, 4, S.main)) != cudaSuccess) return e;
-    return plain ? launch_plain(B, c->P, W, S.main, c->sms) : launch_batched(B, c->P, W, S, c->sms);
+    return plain ? launch_plain(B, P, W, S.main, c->sms) : launch_batched(B, P, W, S, c->sms);
 }
 
 int extend_host(bsw_ctx *c, const bsw_batch_t *b, bsw_result_t *out, int64_t *cells_out, cudaStream_t user)
@@ -369,7 +372,7 @@ int extend_host(bsw_ctx *c, const bsw_batch_t *b, bsw_result_t *out, int64_t *ce
             (const int64_t *)(d + L.t_off), (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
             b->w_override ? (const int32_t *)(d + L.w) : nullptr, (bsw_result_t *)(d + L.out)};
     Work W = make_work(lane.work.p, lane.wl);
-    if ((e = enqueue_launch(c, lane, lane.S, B, W, (b->flags & BSW_PLAIN_KERNEL) != 0, true)) != cudaSuccess) {
+    if ((e = enqueue_launch(c, lane, lane.S, B, W, b->flags, true)) != cudaSuccess) {
         lane.work_dirty = true;
         return cuda_rc(e);
     }
@@ -394,12 +397,11 @@ int extend_device(bsw_ctx *c, const bsw_batch_t *b, bsw_result_t *out, int64_t *
     Batch B{N, b->q, b->q_off, b->q_len, b->t, b->t_off, b->t_len, b->h0, b->w_override, out};
     Work W = make_work(lane.work.p, lane.wl);
     if (cells_out) W.cells = (unsigned long long *)cells_out;
-    const bool plain = (b->flags & BSW_PLAIN_KERNEL) != 0;
     cudaError_t e;
     if (b->flags & BSW_NO_GRAPH) {
         Streams S = lane.S;
         S.main = st;
-        if ((e = enqueue_launch(c, lane, S, B, W, plain, false)) != cudaSuccess) {
+        if ((e = enqueue_launch(c, lane, S, B, W, b->flags, false)) != cudaSuccess) {
             lane.work_dirty = true;
             return cuda_rc(e);
         }
@@ -415,7 +417,7 @@ int extend_device(bsw_ctx *c, const bsw_batch_t *b, bsw_result_t *out, int64_t *
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     if ((e = cudaStreamBeginCapture(lane.S.main, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_rc(e);
-    cudaError_t le = enqueue_launch(c, lane, lane.S, B, W, plain, false);
+    cudaError_t le = enqueue_launch(c, lane, lane.S, B, W, b->flags, false);
     e = cudaStreamEndCapture(lane.S.main, &graph);
     if (le != cudaSuccess || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -488,7 +490,7 @@ int serve_launch(bsw_ctx *c, int li)
             (const int64_t *)(d + L.t_off), (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
             (const int32_t *)(d + L.w), (bsw_result_t *)(d + L.out)};
     Work W = make_work(lane.work.p, lane.wl);
-    if ((e = enqueue_launch(c, lane, lane.S, B, W, false, true)) != cudaSuccess) {
+    if ((e = enqueue_launch(c, lane, lane.S, B, W, 0u, true)) != cudaSuccess) {
         lane.work_dirty = true;
         return cuda_rc(e);
     }
@@ -641,7 +643,7 @@ int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonu
     *out = nullptr;
     bsw_ctx *c = new (std::nothrow) bsw_ctx();
     if (!c) return BSW_ENOMEM;
-    c->P = Params{sc->match, sc->mismatch, sc->o_del, sc->e_del, sc->o_ins, sc->e_ins, w, zdrop, end_bonus, 0u};
+    c->P = Params{sc->match, sc->mismatch, sc->o_del, sc->e_del, sc->o_ins, sc->e_ins, w, zdrop, end_bonus, 0u, kLongMax};
     c->budget.cap = mem_budget_bytes;
     int rc = BSW_OK;
     if (cudaGetDevice(&c->device) != cudaSuccess ||

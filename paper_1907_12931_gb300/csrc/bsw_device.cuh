@@ -29,6 +29,7 @@ constexpr uint32_t kStTooLong = 2u;    // a query exceeds the slot scratch
 struct Params {
     int32_t a, b, o_del, e_del, o_ins, e_ins, w, zdrop, end_bonus;
     uint32_t flags;
+    int32_t max_qlen;   // longer queries are rejected (kStTooLong)
 };
 
 struct Batch {

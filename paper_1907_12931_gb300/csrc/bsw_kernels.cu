@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
         } else {
             const long long bound = (long long)h0 + (long long)P.a * min(n, m);
             if (bound >= (1ll << 30)) atomicOr(W.status, kStInval);
-            else if (n > kLongMax) atomicOr(W.status, kStTooLong);
+            else if (n > P.max_qlen) atomicOr(W.status, kStTooLong);
             else key = pick_bin(n, bound, P.flags);
         }
         W.key[p] = key;
@@ -670,6 +670,30 @@ cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const
     }
     // Section V-D1: pairs whose scores left their lane range, exactly, in 32 bits.
     return launch_warp<4, false>(B, P, W, kRerun, S.main, wblocks);
+}
+
+cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms,
+                                  int warp_blocks)
+{
+    cudaError_t e;
+    if (B.n <= 0) return cudaSuccess;
+    const int cblocks = (int)((B.n + 511) / 512 < (int64_t)sms * 4 ? (B.n + 511) / 512 : (int64_t)sms * 4);
+    k_classify<<<cblocks, 512, 0, st>>>(B, P, W);
+    k_scan<<<1, 1024, 0, st>>>(W);
+    const int sblocks = (int)((B.n + kScatterTile - 1) / kScatterTile < (int64_t)sms * 2 ? (B.n + kScatterTile - 1) / kScatterTile : (int64_t)sms * 2);
+    k_scatter<<<sblocks, kScatterThreads, 0, st>>>(B.n, W);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_inter<256, true>(B, P, W, 0, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<128, true>(B, P, W, 1, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<64, true>(B, P, W, 2, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<32, true>(B, P, W, 3, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<256, false>(B, P, W, 4, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<128, false>(B, P, W, 5, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<64, false>(B, P, W, 6, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<32, false>(B, P, W, 7, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_warp<4, true>(B, P, W, 8, st, warp_blocks)) != cudaSuccess) return e;
+    if ((e = launch_warp<4, false>(B, P, W, 9, st, warp_blocks)) != cudaSuccess) return e;
+    return launch_warp<4, false>(B, P, W, kRerun, st, warp_blocks);
 }
 
 cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms)

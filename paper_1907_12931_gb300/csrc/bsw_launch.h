@@ -30,6 +30,11 @@ int warp_slots_needed(int sms);
 // accumulate.
 cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const Streams &S, int sms);
 
+// The same path on one stream (no side streams, no events); the warp-per-pair
+// kernels use warp_blocks blocks of kWarpKernelThreads threads.
+cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms,
+                                  int warp_blocks);
+
 // Baseline: one pair per warp in input order.
 cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms);
 
