@@ -180,6 +180,45 @@ int bsw_pack_2bit(const uint8_t *in, int64_t n, uint8_t *out);
  */
 int32_t bsw_band_width(const bsw_ctx_t *ctx, int32_t qlen, int32_t w);
 
+/*
+ * bsw_extend_batch_noalloc: the batched extension for callers that cannot
+ * allocate device memory.  The paper has no counterpart; it exists for code
+ * that may not call cudaMalloc where it extends seeds (a memory pool that owns
+ * the whole device, an allocator that forbids allocation at that point, or a
+ * library inside a process whose device memory is managed by someone else).
+ *
+ * It computes exactly what bsw_extend_batch computes for the same scoring and
+ * parameters, and allocates nothing: no context, no cudaMalloc/cudaFree, no
+ * streams or events.  Its work buffers live in one file-scope device array of
+ * BSW_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads this library holds
+ * until the process exits.
+ *
+ *   sc, w, zdrop, end_bonus  as for bsw_init
+ *   batch    device pointers only (flags must include BSW_DEVICE_PTRS; the
+ *            BSW_FORCE_* flags are honoured, others are rejected)
+ *   out      device array of n_pairs results
+ *   cells_out  nullable device int64, overwritten with the cell count
+ *   cuda_stream  the stream to run on (NULL: the legacy default stream)
+ *
+ * Limits: n_pairs <= BSW_NOALLOC_MAX_PAIRS, every query <= BSW_NOALLOC_MAX_QLEN
+ * bases.  A larger n_pairs returns BSW_EINVAL before any work; a longer query
+ * is found by the kernels and the call returns BSW_EINVAL (out is then
+ * unspecified for that batch).  The call enqueues the work, waits for the
+ * stream and returns the status (BSW_OK, BSW_EINVAL for bad inputs, BSW_ECUDA).
+ *
+ * The first call on a device looks up the array's device address for that
+ * device and sets kernel attributes; make that first call before any stream
+ * capture on the device.  All calls share the one array: two calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * it and give wrong results; serialize them.
+ */
+#define BSW_NOALLOC_MAX_PAIRS 262144
+#define BSW_NOALLOC_MAX_QLEN 256
+#define BSW_NOALLOC_SCRATCH_BYTES (16u << 20)
+int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonus,
+                             const bsw_batch_t *batch, bsw_result_t *out, int64_t *cells_out,
+                             void *cuda_stream);
+
 /* Library version string. */
 const char *bsw_version(void);
 

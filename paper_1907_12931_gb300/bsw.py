@@ -88,6 +88,9 @@ def lib():
             L.bsw_pack_2bit.restype = ctypes.c_int
             L.bsw_band_width.argtypes = [vp, i32, i32]
             L.bsw_band_width.restype = i32
+            L.bsw_extend_batch_noalloc.argtypes = [ctypes.POINTER(bsw_scoring_t), i32, i32, i32,
+                                                   ctypes.POINTER(bsw_batch_t), vp, vp, vp]
+            L.bsw_extend_batch_noalloc.restype = ctypes.c_int
             L.bsw_version.argtypes = []
             L.bsw_version.restype = ctypes.c_char_p
             _lib = L
@@ -120,6 +123,18 @@ def bsw_destroy(ctx: int) -> None:
 
 def bsw_extend_batch(ctx: int, batch: bsw_batch_t, out_ptr: int, cells_ptr: int | None, stream: int | None) -> int:
     return lib().bsw_extend_batch(ctx, ctypes.byref(batch), out_ptr, cells_ptr, stream)
+
+
+def bsw_extend_batch_noalloc(scoring, w: int, zdrop: int, end_bonus: int, batch: bsw_batch_t, out_ptr: int,
+                             cells_ptr: int | None, stream: int | None) -> int:
+    """The allocation-free variant (device pointers only); returns the C return code."""
+    sc = bsw_scoring_t(scoring.match, scoring.mismatch, scoring.o_del, scoring.e_del, scoring.o_ins, scoring.e_ins)
+    return lib().bsw_extend_batch_noalloc(ctypes.byref(sc), int(w), int(zdrop), int(end_bonus), ctypes.byref(batch),
+                                          out_ptr, cells_ptr, stream)
+
+
+BSW_NOALLOC_MAX_PAIRS = 262144
+BSW_NOALLOC_MAX_QLEN = 256
 
 
 def bsw_sync(ctx: int, stream: int | None = None) -> int:
