@@ -173,12 +173,21 @@ def measured_peaks():
 
 
 def class_of(q_len, t_len, h0, match=1):
-    """Per-thread kernel class of each pair with 8-bit lanes, as the library
-    buckets it (0: 129-256 query bases, 1: 65-128, 2: 33-64, 3: 1-32; -1 other)."""
+    """Kernel class of each pair, as the library buckets it: 0-3 8-bit lanes for
+    129-256 / 65-128 / 33-64 / 1-32 query bases, 4-7 the same with 16-bit lanes,
+    8 warp per pair with 16-bit slots, 9 warp per pair with 32-bit slots, -1 empty."""
     n = np.asarray(q_len, np.int64)
-    bound = np.asarray(h0, np.int64) + match * np.minimum(n, np.asarray(t_len, np.int64))
-    c = np.select([n > 128, n > 64, n > 32, n > 0], [0, 1, 2, 3], -1)
-    return np.where((n > 256) | (bound > 255) | (np.asarray(t_len) <= 0), -1, c)
+    m = np.asarray(t_len, np.int64)
+    bound = np.asarray(h0, np.int64) + match * np.minimum(n, m)
+    sub = np.select([n > 128, n > 64, n > 32], [0, 1, 2], 3)
+    c = np.where(n > 256, np.where(bound <= 32767, 8, 9),
+                 np.where(bound <= 255 - match, sub, np.where(bound <= 32767, 4 + sub, 9)))
+    return np.where((n <= 0) | (m <= 0), -1, c)
+
+
+CLASS_KERNEL = {0: "k_inter<256,u8>", 1: "k_inter<128,u8>", 2: "k_inter<64,u8>", 3: "k_inter<32,u8>",
+                4: "k_inter<256,i16>", 5: "k_inter<128,i16>", 6: "k_inter<64,i16>", 7: "k_inter<32,i16>",
+                8: "k_warp<4,s16>", 9: "k_warp<4,s32>"}
 
 
 # ------------------------------------------------------------------ arms
@@ -296,16 +305,21 @@ def run_gb300(args):
     plain_equal = bool(np.array_equal(db.out.cpu().numpy(), out_batched)) and plain_cells == cells
     gcups_plain = dist.sum(plain_cells) / (ms_plain * 1e-3) / 1e9
 
+    # the same batched path with two pairs per thread (packed 16-bit lanes) in the 8-bit classes
+    s_steps = max(3, args.steps // 10)
+    ms_packed = time_device(ctx, db, bsw.BSW_PACKED_PAIRS, s_steps, max(1, args.warmup // 2), stream, dist)
+    packed_equal = bool(np.array_equal(db.out.cpu().numpy(), out_batched))
+    gcups_packed = total_cells / (ms_packed * 1e-3) / 1e9
+
     # dominant kernel: the 8-bit class with the most cells, as a batch of its own
     all_cls = class_of(wl.q_len, wl.t_len, wl.h0, wl.params.scoring.match)
-    est = wl.q_len.astype(np.float64) * wl.t_len
-    dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(4)]))
+    est = wl.q_len.astype(np.float64) * np.minimum(wl.t_len, 2 * wl.params.w + 1)
+    dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(10)]))
     sub = wl.subset(np.nonzero(all_cls == dom)[0])
     sdb = bsw.DeviceBatch(bsw.HostBatch(sub))
     ms_dom = time_device(ctx, sdb, 0, max(3, args.steps // 4), 2, stream, dist)
     dom_cells = int(sdb.cells.item())
     del sdb
-    nmax = {0: 256, 1: 128, 2: 64, 3: 32}[dom]
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     f_mhz = clk["sm_mhz"] or 1470.0
     achieved = dom_cells * OPS_PER_CELL / (ms_dom * 1e-3) / 1e12
@@ -343,7 +357,7 @@ def run_gb300(args):
         line = {
             "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "vs_baseline": None, "dtype": "u8" if args.config != "long10k" else "int16", "data": "synthetic",
             "config": {"workload": args.config, "description": WORKLOAD_TEXT.get(args.config, args.config),
                        "pairs_per_gpu": n, "cells_per_step": cells,
                        "l2": "inputs larger than L2 (%.0f MB resident packed inputs + %.0f MB results)"
@@ -352,10 +366,12 @@ def run_gb300(args):
             "plain": {"value": round(gcups_plain, 3), "unit": "GCUPS", "ms_per_step": round(ms_plain, 4),
                       "kernel": "one pair per warp, input order", "bit_exact_vs_batched": plain_equal},
             "speedup_vs_plain": round(gcups / gcups_plain, 3) if gcups_plain else None,
+            "two_pairs_per_thread": {"value": round(gcups_packed, 3), "unit": "GCUPS", "ms_per_step": round(ms_packed, 4),
+                                     "bit_exact_vs_batched": packed_equal},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
-                         "kernel": "k_inter<%d,u8> (batch of its own class: %d pairs, %d cells)"
-                                   % (nmax, sub.n_pairs, dom_cells),
+                         "kernel": "%s (batch of its own class: %d pairs, %d cells)"
+                                   % (CLASS_KERNEL[dom], sub.n_pairs, dom_cells),
                          "ops_per_cell": OPS_PER_CELL,
                          "peak_basis": "%d SMs x %.0f MHz (median under load) x %d lane-ops/clk"
                                        % (sms, f_mhz, LANE_OPS_PER_CLK_PER_SM)},

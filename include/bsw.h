@@ -68,6 +68,8 @@ extern "C" {
 #define BSW_PLAIN_KERNEL  0x10u  /* baseline: one pair per warp, no bucketing, input order */
 #define BSW_NO_GRAPH      0x20u  /* device-pointer path: launch directly, no CUDA graph    */
 #define BSW_COPY_INPUTS   0x40u  /* submit: copy host inputs at submit time                */
+#define BSW_PACKED_PAIRS  0x80u  /* 8-bit classes up to 128 query bases: two pairs per
+                                    thread in packed 16-bit lanes instead of one        */
 
 typedef struct bsw_ctx bsw_ctx_t;
 

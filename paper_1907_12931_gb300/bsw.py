@@ -32,6 +32,7 @@ BSW_FORCE_I32 = 0x08
 BSW_PLAIN_KERNEL = 0x10
 BSW_NO_GRAPH = 0x20
 BSW_COPY_INPUTS = 0x40
+BSW_PACKED_PAIRS = 0x80
 
 FIELDS = ("score", "qle", "tle", "gtle", "gscore", "max_off")
 

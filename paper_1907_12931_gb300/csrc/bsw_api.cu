@@ -31,7 +31,7 @@ using namespace bsw;
 namespace {
 
 constexpr uint32_t kKnownFlags = BSW_DEVICE_PTRS | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32 |
-                                 BSW_PLAIN_KERNEL | BSW_NO_GRAPH | BSW_COPY_INPUTS;
+                                 BSW_PLAIN_KERNEL | BSW_NO_GRAPH | BSW_COPY_INPUTS | BSW_PACKED_PAIRS;
 constexpr int kServeLanes = 3;
 constexpr int64_t kMergePairs = 1 << 20;   // the serving loop merges queued batches up to this size
 constexpr int kGraphCache = 8;

@@ -337,6 +337,308 @@ __global__ void __launch_bounds__(256) k_inter(Batch B, Params P, Work W, int cl
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
 
+// --------------------------------------------- two pairs per thread (s16x2)
+//
+// The paper's inter-task SIMD with 16-bit lanes (Section V-C, V-D1), two pairs
+// per 32-bit register: one warp holds 64 pairs.  Opt-in (BSW_PACKED_PAIRS).
+
+// Packed 16-bit integer SIMD (two lanes per 32-bit register).
+__device__ __forceinline__ uint32_t add2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("add.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t max2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t max2relu(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.s16x2.relu %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t minu2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Scores scaled by 128 in 16-bit lanes: the low 7 bits of H*128 + j carry
+// the column (queries up to 128 bases), so one packed max tracks each pair's
+// row best with ties to the larger column.
+constexpr int kS2 = 7;
+
+// Per-thread state of the two-pair kernel for one row.
+struct Row2 {
+    uint32_t f2, key2, dprev2, hlast2, tbit2;
+};
+
+// Constants of the packed cell update.
+struct Cell2K {
+    uint32_t nK;      // 0x10000 - (match + mismatch)*128: packed negation of the mismatch cost
+    uint32_t noed2;   // -(o_del + e_del)*128 in each lane
+    uint32_t noei2;   // -(o_ins + e_ins)*128
+    uint32_t ned2;    // -e_del*128
+    uint32_t nei2;    // -e_ins*128
+    uint32_t a128;    // match*128
+};
+
+// Cells [j0, j1) of one row for both lanes.  m: lanes whose band covers the
+// range (0xffff per lane); lanes outside it are computed but neither stored
+// nor counted.  Slot words: SD[j*32] = D*128 per lane (D = H + match for
+// H > 0, else 0: the previous row's H at column j-1); SE[j*32] = E*128 per
+// lane in bits 7-14 / 23-30 and the lane's query mismatch mask in bits
+// 0-3 / 16-19.
+template <bool MASKED>
+__device__ __forceinline__ void cells2(uint32_t *SD, uint32_t *SE, int j0, int j1, uint32_t m, Row2 &R,
+                                       const Cell2K &K)
+{
+    const uint32_t keep_e = MASKED ? (m & 0xff80ff80u) : 0xff80ff80u;
+    uint32_t J2 = (uint32_t)j0 * 0x00010001u;
+#pragma unroll 2
+    for (int j = j0; j < j1; ++j) {
+        const uint32_t wd = SD[j * 32], we = SE[j * 32];
+        const uint32_t e2 = we & 0x7f807f80u;                          // E(i, j)*128
+        const uint32_t mm = minu2(we & R.tbit2, 0x00010001u);          // 1 where base != t_i
+        const uint32_t M2 = add2(wd, mm * K.nK);                       // Eq. 2 diagonal term
+        const uint32_t h2 = max2(max2(M2, e2), R.f2);                  // H(i, j)
+        uint32_t hj = add2(h2, J2);
+        if (MASKED) hj &= m;
+        R.key2 = max2(R.key2, hj);
+        const uint32_t en = max2relu(add2(e2, K.ned2), add2(M2, K.noed2));   // E(i+1, j)
+        R.f2 = max2relu(add2(R.f2, K.nei2), add2(M2, K.noei2));              // F(i, j+1)
+        if (MASKED) {
+            SD[j * 32] = (R.dprev2 & m) | (wd & ~m);
+            SE[j * 32] = (en & keep_e) | (we & ~keep_e);
+        } else {
+            SD[j * 32] = R.dprev2;
+            SE[j * 32] = en | (we & 0x000f000fu);
+        }
+        R.dprev2 = minu2(h2, 0x00010001u) * K.a128 + h2;               // D of H(i, j)
+        R.hlast2 = h2;
+        J2 += 0x00010001u;
+    }
+}
+
+// Per-pair bookkeeping of the two-pair kernel.
+struct Pair2 {
+    int p, n, m, h0, wb;
+    int lo, hi, best, bi, bj, gbest, gi, moff;
+    bool live;
+    unsigned long long ncell;
+    const uint8_t *tp;
+};
+
+__device__ __forceinline__ void pair2_open(Pair2 &X, const Batch &B, const Params &P, int p)
+{
+    X.p = p;
+    X.live = p >= 0;
+    if (!X.live) return;
+    X.n = B.q_len[p];
+    X.m = B.t_len[p];
+    X.h0 = B.h0[p];
+    X.wb = clip_band(P, X.n, B.w_override ? B.w_override[p] : P.w);
+    X.lo = 0; X.hi = X.n;
+    X.best = X.h0; X.bi = X.bj = -1; X.gbest = X.gi = -1; X.moff = 0;
+    X.ncell = 0;
+    X.tp = B.t + (B.t_off[p] >> 2);
+}
+
+// Extend pairs pa (low lanes) and pb (high lanes, -1 for none) on one thread.
+// Returns the cells computed; pairs whose scores leave the lane range go to
+// the 32-bit re-run and count nothing here.
+template <int NMAX>
+__device__ unsigned long long inter2_pairs(const Batch &B, const Params &P, const Work &W, int pa, int pb,
+                                           uint32_t *SD, uint32_t *SE)
+{
+    const int a = P.a;
+    const int vmax = 255 - a;
+    Pair2 X[2];
+    pair2_open(X[0], B, P, pa);
+    pair2_open(X[1], B, P, pb);
+    // First row of Eq. 3 and the query masks, per lane.
+    const int nmax = max(X[0].live ? X[0].n : 0, X[1].live ? X[1].n : 0);
+    for (int j = 0; j <= nmax; ++j) { SD[j * 32] = 0u; SE[j * 32] = 0u; }
+    for (int h = 0; h < 2; ++h) {
+        if (!X[h].live) continue;
+        if (X[h].h0 > vmax || X[h].n > NMAX) {
+            W.rerun[atomicAdd(&W.cls_count[kRerun], 1)] = X[h].p;
+            X[h].live = false;
+            continue;
+        }
+        const uint8_t *qp = B.q + (B.q_off[X[h].p] >> 2);
+        const int sh = 16 * h;
+        for (int c = 0; c <= X[h].n; c += 4) {
+            const uint32_t byte = c < X[h].n ? __ldg(qp + (c >> 2)) : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = c + k;
+                if (j <= X[h].n) {
+                    const int hv = j == 0 ? X[h].h0 : max(0, X[h].h0 - P.o_ins - j * P.e_ins);
+                    const uint32_t d = hv > 0 ? (uint32_t)(hv + a) << kS2 : 0u;
+                    const uint32_t q = (~(1u << ((byte >> (2 * k)) & 3)) & 0xfu);
+                    SD[j * 32] |= d << sh;
+                    SE[j * 32] |= q << sh;
+                }
+            }
+        }
+    }
+    const int bm = min(P.b, 255 - a);
+    Cell2K K;
+    const uint32_t kmis = (uint32_t)((a + bm) << kS2);
+    K.nK = 0x10000u - kmis;
+    auto rep = [](int v) { return ((uint32_t)v & 0xffffu) * 0x00010001u; };
+    K.noed2 = rep(-(min(P.o_del + P.e_del, 255) << kS2));
+    K.noei2 = rep(-(min(P.o_ins + P.e_ins, 255) << kS2));
+    K.ned2 = rep(-(min(P.e_del, 255) << kS2));
+    K.nei2 = rep(-(min(P.e_ins, 255) << kS2));
+    K.a128 = (uint32_t)(a << kS2);
+
+    const int oe_del = P.o_del + P.e_del;
+    uint32_t tbyte[2] = {0u, 0u};
+    for (int i = 0; X[0].live || X[1].live; ++i) {
+        int lo[2], hi[2], left[2];
+        bool on[2];
+        Row2 R;
+        R.f2 = 0u; R.key2 = 0u; R.dprev2 = 0u; R.hlast2 = 0u; R.tbit2 = 0u;
+        for (int h = 0; h < 2; ++h) {
+            if (X[h].live && i >= X[h].m) {                 // every target row done
+                store_result(&B.out[X[h].p], X[h].best, X[h].bj + 1, X[h].bi + 1, X[h].gi + 1, X[h].gbest, X[h].moff);
+                X[h].live = false;
+            }
+            on[h] = X[h].live;
+            if (!on[h]) { lo[h] = hi[h] = 0; left[h] = 0; continue; }
+            if ((i & 3) == 0) tbyte[h] = __ldg(X[h].tp + (i >> 2));
+            const int tb = (tbyte[h] >> (2 * (i & 3))) & 3;
+            R.tbit2 |= (1u << tb) << (16 * h);
+            X[h].lo = max(X[h].lo, i - X[h].wb);
+            X[h].hi = min(min(X[h].hi, i + X[h].wb + 1), X[h].n);
+            lo[h] = X[h].lo; hi[h] = X[h].hi;
+            left[h] = lo[h] == 0 ? max(0, X[h].h0 - oe_del - i * P.e_del) : 0;
+        }
+        if (!on[0] && !on[1]) break;
+        const bool band0 = on[0] && lo[0] < hi[0], band1 = on[1] && lo[1] < hi[1];
+        uint32_t hl2 = 0u;                      // H(i, hi-1)*128 per lane (or the left boundary)
+        for (int h = 0; h < 2; ++h)
+            if (on[h]) hl2 |= ((uint32_t)left[h] << kS2) << (16 * h);
+        // Walk the union of the two bands in segments where the active lanes do not change.
+        int j = 1 << 30, jend = 0;
+        if (band0) { j = min(j, lo[0]); jend = max(jend, hi[0]); }
+        if (band1) { j = min(j, lo[1]); jend = max(jend, hi[1]); }
+        while (j < jend) {
+            int nb = jend;
+            uint32_t m = 0u;
+            for (int h = 0; h < 2; ++h) {
+                const bool bh = h ? band1 : band0;
+                if (!bh) continue;
+                if (lo[h] > j) nb = min(nb, lo[h]);
+                if (hi[h] > j) nb = min(nb, hi[h]);
+                if (lo[h] <= j && j < hi[h]) {
+                    m |= 0xffffu << (16 * h);
+                    if (j == lo[h]) {           // lane h enters its band: fresh F, left boundary
+                        const uint32_t lh = (uint32_t)left[h] << kS2;
+                        const uint32_t dl = left[h] > 0 ? lh + ((uint32_t)a << kS2) : 0u;
+                        R.f2 &= ~(0xffffu << (16 * h));
+                        R.dprev2 = (R.dprev2 & ~(0xffffu << (16 * h))) | (dl << (16 * h));
+                    }
+                }
+            }
+            if (m == 0xffffffffu) cells2<false>(SD, SE, j, nb, m, R, K);
+            else if (m) cells2<true>(SD, SE, j, nb, m, R, K);
+            for (int h = 0; h < 2; ++h) {
+                const bool bh = h ? band1 : band0;
+                if (bh && hi[h] == nb && (m >> (16 * h)) & 1u)     // lane h leaves its band
+                    hl2 = (hl2 & ~(0xffffu << (16 * h))) | (R.hlast2 & (0xffffu << (16 * h)));
+            }
+            j = nb;
+        }
+        for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            Pair2 &Y = X[h];
+            const int sh = 16 * h;
+            const int hl = (int)((hl2 >> sh) & 0xffffu) >> kS2;
+            // slot hi: H(i, hi-1) and E = 0 for this lane
+            const uint32_t dl = hl > 0 ? (uint32_t)(hl + a) << kS2 : 0u;
+            SD[Y.hi * 32] = (SD[Y.hi * 32] & ~(0xffffu << sh)) | (dl << sh);
+            SE[Y.hi * 32] &= ~(0xff80u << sh);
+            const int key = (int)((R.key2 >> sh) & 0xffffu);
+            const int rm = key >> kS2, rj = key & ((1 << kS2) - 1);
+            if (rm > vmax) {                                   // Section V-D1: widen and redo
+                W.rerun[atomicAdd(&W.cls_count[kRerun], 1)] = Y.p;
+                Y.live = false;
+                Y.ncell = 0;
+                continue;
+            }
+            if (Y.hi > Y.lo) Y.ncell += (unsigned)(Y.hi - Y.lo);
+            if (max(Y.lo, Y.hi) == Y.n) {
+                if (hl >= Y.gbest) Y.gi = i;
+                Y.gbest = max(Y.gbest, hl);
+            }
+            bool stop = rm == 0;
+            if (!stop) {
+                if (rm > Y.best) {
+                    Y.best = rm; Y.bi = i; Y.bj = rj;
+                    Y.moff = max(Y.moff, abs(rj - i));
+                } else if (P.zdrop > 0) {
+                    const int di = i - Y.bi, dj = rj - Y.bj;
+                    const int drop = di > dj ? Y.best - rm - (di - dj) * P.e_del : Y.best - rm - (dj - di) * P.e_ins;
+                    stop = drop > P.zdrop;
+                }
+            }
+            if (stop) {
+                store_result(&B.out[Y.p], Y.best, Y.bj + 1, Y.bi + 1, Y.gi + 1, Y.gbest, Y.moff);
+                Y.live = false;
+                continue;
+            }
+            const uint32_t mk = 0xffffu << sh, mke = 0xff80u << sh;
+            int k = Y.lo;                                      // rule c
+            while (k < Y.hi && !((SD[k * 32] & mk) | (SE[k * 32] & mke))) ++k;
+            Y.lo = k;
+            k = Y.hi;
+            while (k >= Y.lo && !((SD[k * 32] & mk) | (SE[k * 32] & mke))) --k;
+            Y.hi = min(k + 2, Y.n);
+        }
+    }
+    unsigned long long cells = 0;
+    for (int h = 0; h < 2; ++h) {
+        if (X[h].p < 0) continue;
+        cells += X[h].ncell;
+    }
+    return cells;
+}
+
+// Persistent kernel: each warp takes groups of 64 consecutive pairs of its
+// class (thread L takes entries 2L and 2L+1, pairs of nearly equal length).
+template <int NMAX>
+__global__ void __launch_bounds__(256) k_inter2(Batch B, Params P, Work W, int cls)
+{
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    uint32_t *SD = smem + (threadIdx.x >> 5) * ((NMAX + 1) * 64) + lane;
+    uint32_t *SE = SD + (NMAX + 1) * 32;
+    const int start = W.cls_start[cls], count = W.cls_count[cls];
+    const int ngroups = (count + 63) >> 6;
+    unsigned long long cells = 0;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(&W.cls_next[cls], 1u);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= ngroups) break;
+        const int i0 = (g << 6) + 2 * lane;
+        const int pa = i0 < count ? W.order[start + i0] : -1;
+        const int pb = i0 + 1 < count ? W.order[start + i0 + 1] : -1;
+        if (pa >= 0) cells += inter2_pairs<NMAX>(B, P, W, pa, pb, SD, SE);
+        __syncwarp();
+    }
+    for (int d = 16; d > 0; d >>= 1) cells += __shfl_xor_sync(kFull, cells, d);
+    if (lane == 0 && cells) atomicAdd(W.cells, cells);
+}
+
 // ---------------------------------------------------------- one pair per warp
 
 // Slot storage for the warp kernels: 16-bit (H low half, E high half of a
@@ -613,6 +915,49 @@ cudaError_t launch_inter(const Batch &B, const Params &P, const Work &W, int cls
     return cudaGetLastError();
 }
 
+int g_inter2_blocks[3] = {1, 1, 1};
+
+template <int NMAX> constexpr int inter2_warps() { return NMAX >= 128 ? 2 : NMAX >= 64 ? 4 : 8; }
+template <int NMAX> constexpr size_t inter2_smem() { return (size_t)inter2_warps<NMAX>() * (NMAX + 1) * 64 * 4; }
+template <int NMAX> constexpr int inter2_index() { return NMAX >= 128 ? 0 : NMAX >= 64 ? 1 : 2; }
+
+template <int NMAX>
+cudaError_t prepare_inter2()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_inter2<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)inter2_smem<NMAX>());
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inter2<NMAX>, inter2_warps<NMAX>() * 32,
+                                                      inter2_smem<NMAX>());
+    if (e != cudaSuccess) return e;
+    g_inter2_blocks[inter2_index<NMAX>()] = nb > 0 ? nb : 1;
+    return cudaSuccess;
+}
+
+// The packed kernel holds every intermediate in a signed 16-bit lane only when
+// the mismatch and gap-open costs (clamped where larger ones act the same) fit.
+bool inter2_ok(const Params &P)
+{
+    const int bm = P.b < 255 - P.a ? P.b : 255 - P.a;
+    const int od = P.o_del + P.e_del < 255 ? P.o_del + P.e_del : 255;
+    const int oi = P.o_ins + P.e_ins < 255 ? P.o_ins + P.e_ins : 255;
+    return P.a + bm + od <= 256 && P.a + bm + oi <= 256 && (P.flags & BSW_PACKED_PAIRS);
+}
+
+// 8-bit class with queries up to NMAX: one pair per thread, or two pairs per
+// thread in packed 16-bit lanes when asked for and the scoring allows.
+template <int NMAX>
+cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms)
+{
+    if (NMAX <= 128 && inter2_ok(P)) {
+        const int blocks = sms * g_inter2_blocks[inter2_index<NMAX>()];
+        k_inter2<NMAX><<<blocks, inter2_warps<NMAX>() * 32, inter2_smem<NMAX>(), st>>>(B, P, W, cls);
+        return cudaGetLastError();
+    }
+    return launch_inter<NMAX, true>(B, P, W, cls, st, sms);
+}
+
 template <int C, bool S16>
 cudaError_t launch_warp(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int blocks)
 {
@@ -633,7 +978,10 @@ cudaError_t prepare_kernels(int sms)
     if ((e = prepare_inter<256, false>()) != cudaSuccess) return e;
     if ((e = prepare_inter<128, false>()) != cudaSuccess) return e;
     if ((e = prepare_inter<64, false>()) != cudaSuccess) return e;
-    return prepare_inter<32, false>();
+    if ((e = prepare_inter<32, false>()) != cudaSuccess) return e;
+    if ((e = prepare_inter2<128>()) != cudaSuccess) return e;
+    if ((e = prepare_inter2<64>()) != cudaSuccess) return e;
+    return prepare_inter2<32>();
 }
 
 int warp_slots_needed(int sms) { return sms * kWarpBlocksPerSM * (kWarpKernelThreads / 32); }
@@ -655,9 +1003,9 @@ cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const
         if ((e = cudaStreamWaitEvent(S.side[k], S.fork, 0)) != cudaSuccess) return e;
     const int wblocks = sms * kWarpBlocksPerSM;
     if ((e = launch_inter<256, true>(B, P, W, 0, S.side[0], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<128, true>(B, P, W, 1, S.side[0], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<64, true>(B, P, W, 2, S.side[1], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<32, true>(B, P, W, 3, S.side[1], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<128>(B, P, W, 1, S.side[0], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<64>(B, P, W, 2, S.side[1], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<32>(B, P, W, 3, S.side[1], sms)) != cudaSuccess) return e;
     if ((e = launch_warp<4, true>(B, P, W, 8, S.side[2], wblocks)) != cudaSuccess) return e;
     if ((e = launch_warp<4, false>(B, P, W, 9, S.side[2], wblocks)) != cudaSuccess) return e;
     if ((e = launch_inter<256, false>(B, P, W, 4, S.side[2], sms)) != cudaSuccess) return e;
@@ -684,9 +1032,9 @@ cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W
     k_scatter<<<sblocks, kScatterThreads, 0, st>>>(B.n, W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_inter<256, true>(B, P, W, 0, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<128, true>(B, P, W, 1, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<64, true>(B, P, W, 2, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<32, true>(B, P, W, 3, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<128>(B, P, W, 1, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<64>(B, P, W, 2, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<32>(B, P, W, 3, st, sms)) != cudaSuccess) return e;
     if ((e = launch_inter<256, false>(B, P, W, 4, st, sms)) != cudaSuccess) return e;
     if ((e = launch_inter<128, false>(B, P, W, 5, st, sms)) != cudaSuccess) return e;
     if ((e = launch_inter<64, false>(B, P, W, 6, st, sms)) != cudaSuccess) return e;

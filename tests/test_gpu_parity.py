@@ -59,11 +59,16 @@ def run(bsw, wl, flags=0, device=False, budget=16 << 30, w_override=None, params
         return db.out.cpu().numpy(), int(db.cells.item())
 
 
-@pytest.mark.parametrize("flags", [0, "plain", "i8", "i16", "i32"])
+def flag_of(bsw, name):
+    return {0: 0, "plain": bsw.BSW_PLAIN_KERNEL, "i8": bsw.BSW_FORCE_I8, "i16": bsw.BSW_FORCE_I16,
+            "i32": bsw.BSW_FORCE_I32, "packed": bsw.BSW_PACKED_PAIRS,
+            "i8packed": bsw.BSW_FORCE_I8 | bsw.BSW_PACKED_PAIRS}[name]
+
+
+@pytest.mark.parametrize("flags", [0, "plain", "i8", "i16", "i32", "packed", "i8packed"])
 def test_plain10k(bsw, flags):
     wl, ref, cells = workload_and_oracle("plain10k")
-    f = {0: 0, "plain": bsw.BSW_PLAIN_KERNEL, "i8": bsw.BSW_FORCE_I8, "i16": bsw.BSW_FORCE_I16,
-         "i32": bsw.BSW_FORCE_I32}[flags]
+    f = flag_of(bsw, flags)
     got, gc = run(bsw, wl, f)
     assert_same(got, ref, "plain10k/%s" % flags)
     assert gc == cells
@@ -82,6 +87,14 @@ def test_full_workloads_batched(bsw, config):
     wl, ref, cells = workload_and_oracle(config)
     got, gc = run(bsw, wl, 0, device=True)
     assert_same(got, ref, config)
+    assert gc == cells
+
+
+@pytest.mark.parametrize("config", ["read151", "read250"])
+def test_full_workloads_packed_pairs(bsw, config):
+    wl, ref, cells = workload_and_oracle(config)
+    got, gc = run(bsw, wl, bsw.BSW_PACKED_PAIRS, device=True)
+    assert_same(got, ref, config + "/packed")
     assert gc == cells
 
 
@@ -145,14 +158,13 @@ def adversarial():
 
 
 @pytest.mark.parametrize("zdrop", [100, 0, 1, 7])
-@pytest.mark.parametrize("flags", [0, "plain", "i16", "i32", "i8"])
+@pytest.mark.parametrize("flags", [0, "plain", "i16", "i32", "i8", "packed"])
 def test_adversarial(bsw, zdrop, flags):
     wl, ws = adversarial()
     params = W.Params(W.Scoring(), w=100, zdrop=zdrop, end_bonus=5)
     wl.params = params
     ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH, w_override=ws)
-    f = {0: 0, "plain": bsw.BSW_PLAIN_KERNEL, "i8": bsw.BSW_FORCE_I8, "i16": bsw.BSW_FORCE_I16,
-         "i32": bsw.BSW_FORCE_I32}[flags]
+    f = flag_of(bsw, flags)
     got, gc = run(bsw, wl, f, w_override=ws)
     assert_same(got, ref, "adversarial zdrop=%d flags=%s" % (zdrop, flags))
     assert gc == int(cells.sum())
@@ -164,7 +176,7 @@ def test_other_scorings(bsw, sc):
     params = W.Params(W.Scoring(*sc), w=60, zdrop=40, end_bonus=3)
     wl.params = params
     ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH)
-    for f in (0, bsw.BSW_PLAIN_KERNEL, bsw.BSW_FORCE_I32):
+    for f in (0, bsw.BSW_PLAIN_KERNEL, bsw.BSW_FORCE_I32, bsw.BSW_PACKED_PAIRS):
         got, gc = run(bsw, wl, f)
         assert_same(got, ref, "scoring %s flags %d" % (sc, f))
         assert gc == int(cells.sum())
