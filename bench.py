@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--pairs", type=int, default=None)
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point")
     return ap.parse_args()
 
 
@@ -187,7 +188,7 @@ def class_of(q_len, t_len, h0, match=1):
 
 CLASS_KERNEL = {0: "k_inter<256,u8>", 1: "k_inter<128,u8>", 2: "k_inter<64,u8>", 3: "k_inter<32,u8>",
                 4: "k_inter<256,i16>", 5: "k_inter<128,i16>", 6: "k_inter<64,i16>", 7: "k_inter<32,i16>",
-                8: "k_warp<4,s16>", 9: "k_warp<4,s32>"}
+                8: "k_warp<8,s16>", 9: "k_warp<8,s32>"}
 
 
 # ------------------------------------------------------------------ arms

@@ -33,7 +33,8 @@ namespace {
 constexpr uint32_t kKnownFlags = BSW_DEVICE_PTRS | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32 |
                                  BSW_PLAIN_KERNEL | BSW_NO_GRAPH | BSW_COPY_INPUTS | BSW_PACKED_PAIRS;
 constexpr int kServeLanes = 3;
-constexpr int64_t kMergePairs = 1 << 20;   // the serving loop merges queued batches up to this size
+constexpr int64_t kMergePairs = 1 << 20;   // the serving loop merges queued batches up to this many pairs
+constexpr int64_t kMergeCells = 4000000000ll;   // ... and up to this many estimated DP cells
 constexpr int kGraphCache = 8;
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -197,6 +198,7 @@ struct Lane {
 struct Extents {
     int64_t q_lo = INT64_MAX, q_hi = 0, t_lo = INT64_MAX, t_hi = 0;
     int maxn = 0;
+    int64_t est_cells = 0;   // sum of qlen * min(tlen, 2w + 1): a bound on the band area
 };
 
 int check_host_batch(const bsw_batch_t *b, const Params &P, Extents *x)
@@ -215,6 +217,7 @@ int check_host_batch(const bsw_batch_t *b, const Params &P, Extents *x)
             x->t_lo = std::min(x->t_lo, to / 4);
             x->t_hi = std::max(x->t_hi, (to + m + 3) / 4);
             x->maxn = std::max(x->maxn, n);
+            x->est_cells += (int64_t)n * std::min<int64_t>(m, 2 * (int64_t)w + 1);
         }
     }
     if (x->q_lo > x->q_hi) x->q_lo = x->q_hi = 0;
@@ -541,9 +544,12 @@ void server_main(bsw_ctx *c)
                 c->lane_created[li] = true;
             }
             std::vector<Request *> &reqs = c->lane_reqs[li];
-            int64_t pairs = 0;
-            while (!c->queue.empty() && (reqs.empty() || pairs + c->queue.front()->b.n_pairs <= kMergePairs)) {
+            int64_t pairs = 0, ecells = 0;
+            while (!c->queue.empty() &&
+                   (reqs.empty() || (pairs + c->queue.front()->b.n_pairs <= kMergePairs &&
+                                     ecells + c->queue.front()->ext.est_cells <= kMergeCells))) {
                 pairs += c->queue.front()->b.n_pairs;
+                ecells += c->queue.front()->ext.est_cells;
                 reqs.push_back(c->queue.front());
                 c->queue.pop_front();
             }

@@ -678,8 +678,15 @@ template <> struct SlotIO<false> {
 // prefix over the row, computed per lane and then as a warp scan of the lanes'
 // maps f -> max(f - cnt*e_ins, b).  Row decisions (band, stop, best, trim) are
 // warp-uniform.  `slots` holds n + 1 + 32*C slots.
-template <int C, bool S16>
-__device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, uint8_t *slots)
+//
+// RING: the slots live in a shared-memory ring of mask + 1 entries (a power of
+// two >= 2*w' + 3) indexed by column & mask.  The band never spans more than
+// 2*w' + 2 columns, so a column's ring entry is not reused while the column
+// can still be read, including the band-regrowth reads of earlier rows'
+// values.  Columns never written before get their first-row value of Eq. 3
+// when the band first reaches them (hw is the highest column set so far).
+template <int C, bool S16, bool RING>
+__device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, uint8_t *slots, int mask)
 {
     using IO = SlotIO<S16>;
     const int lane = threadIdx.x & 31;
@@ -688,10 +695,14 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
     const int a = P.a, mb = -P.b;
     const int e_del = P.e_del, e_ins = P.e_ins;
     const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
-
-    for (int c = lane; c <= n; c += 32)
-        IO::store(slots, c, c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins), 0);
-    __syncwarp();
+    auto at = [mask](int j) { return RING ? (j & mask) : j; };
+    int hw = -1;
+    if (!RING) {
+        for (int c = lane; c <= n; c += 32)
+            IO::store(slots, c, c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins), 0);
+        hw = n;
+        __syncwarp();
+    }
 
     const int64_t qoff = B.q_off[p];
     const uint8_t *tp = B.t + (B.t_off[p] >> 2);
@@ -702,6 +713,12 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
         const int tb = (__ldg(tp + (i >> 2)) >> (2 * (i & 3))) & 3;
         lo = max(lo, i - wb);
         hi = min(min(hi, i + wb + 1), n);
+        if (RING && hi - 1 > hw) {             // first visit of columns (hw, hi-1]
+            for (int c = hw + 1 + lane; c <= hi - 1; c += 32)
+                IO::store(slots, c & mask, c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins), 0);
+            hw = hi - 1;
+            __syncwarp();
+        }
         const int hl0 = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
         int carry_f = 0, carry_h = hl0;
         int rm_l = 0, rj_l = -1;
@@ -724,7 +741,7 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
                 const int j = j0 + k;
                 act[k] = j >= lo && j < hi;
                 int d = 0, e = 0;
-                if (act[k]) IO::load(slots, j, d, e);
+                if (act[k]) IO::load(slots, at(j), d, e);
                 const int sc = (int)((qbits >> (2 * k)) & 3u) == tb ? a : mb;
                 M[k] = d > 0 ? d + sc : 0;
                 E0[k] = e;
@@ -764,7 +781,7 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
             for (int k = 0; k < C; ++k) {
                 if (act[k]) {
                     const int e2 = __viaddmax_s32_relu(E0[k], -e_del, M[k] - oe_del);
-                    IO::store(slots, j0 + k, hin, e2);
+                    IO::store(slots, at(j0 + k), hin, e2);
                     hin = H[k];
                 }
             }
@@ -775,7 +792,8 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
         }
         const int hl = carry_h;
         __syncwarp();
-        if (lane == 0) IO::store(slots, hi, hl, 0);
+        if (lane == 0) IO::store(slots, at(hi), hl, 0);
+        hw = max(hw, hi);
         __syncwarp();
         const int rm = __reduce_max_sync(kFull, (unsigned)rm_l);
         const int rj = (int)__reduce_max_sync(kFull, (unsigned)(rm_l == rm ? rj_l + 1 : 0)) - 1;
@@ -798,7 +816,7 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
         for (int base = lo; base < hi; base += 32) {
             const int j = base + lane;
             int h = 0, e = 0;
-            if (j < hi) IO::load(slots, j, h, e);
+            if (j < hi) IO::load(slots, at(j), h, e);
             const unsigned bal = __ballot_sync(kFull, (h | e) != 0);
             if (bal) { nlo = base + __ffs(bal) - 1; break; }
         }
@@ -807,7 +825,7 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
         for (int top = hi; top >= lo; top -= 32) {
             const int j = top - lane;
             int h = 0, e = 0;
-            if (j >= lo) IO::load(slots, j, h, e);
+            if (j >= lo) IO::load(slots, at(j), h, e);
             const unsigned bal = __ballot_sync(kFull, (h | e) != 0);
             if (bal) { last = top - (__ffs(bal) - 1); break; }
         }
@@ -818,12 +836,17 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
 }
 
 // Persistent warp-per-pair kernel over a class list (or the re-run list).
+// ring_log2 > 0: each warp has a shared-memory slot ring of 1 << ring_log2
+// entries (dynamic shared memory); a pair whose band needs a larger ring uses
+// the warp's global slot scratch instead.
 template <int C, bool S16>
-__global__ void __launch_bounds__(256) k_warp(Batch B, Params P, Work W, int cls)
+__global__ void __launch_bounds__(256) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
 {
+    extern __shared__ uint8_t ring_mem[];
     const int lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     uint8_t *slots = W.slots + gw * W.slot_bytes_per_warp;
+    uint8_t *ring = ring_mem + (size_t)(threadIdx.x >> 5) * ((size_t)SlotIO<S16>::kBytes << ring_log2);
     const int count = W.cls_count[cls];
     const int32_t *list = cls == kRerun ? W.rerun : W.order + W.cls_start[cls];
     unsigned long long cells = 0;
@@ -834,11 +857,20 @@ __global__ void __launch_bounds__(256) k_warp(Batch B, Params P, Work W, int cls
         if (g >= count) break;
         const int p = list[g];
         const int n = B.q_len[p];
+        if (ring_log2 > 0) {
+            const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
+            int need = 1;
+            while (need < 2 * wb + 3) need <<= 1;
+            if (need <= (1 << ring_log2)) {
+                cells += warp_pair<C, S16, true>(B, P, p, ring, need - 1);
+                continue;
+            }
+        }
         if ((int64_t)(n + 1 + 32 * C) * SlotIO<S16>::kBytes > W.slot_bytes_per_warp) {
             if (lane == 0) atomicOr(W.status, kStTooLong);
             continue;
         }
-        cells += warp_pair<C, S16>(B, P, p, slots);
+        cells += warp_pair<C, S16, false>(B, P, p, slots, 0);
     }
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
@@ -874,7 +906,7 @@ __global__ void __launch_bounds__(256) k_plain(Batch B, Params P, Work W)
             if (lane == 0) atomicOr(W.status, kStTooLong);
             continue;
         }
-        cells += s16 ? warp_pair<1, true>(B, P, (int)p, slots) : warp_pair<1, false>(B, P, (int)p, slots);
+        cells += s16 ? warp_pair<1, true, false>(B, P, (int)p, slots, 0) : warp_pair<1, false, false>(B, P, (int)p, slots, 0);
     }
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
@@ -882,6 +914,9 @@ __global__ void __launch_bounds__(256) k_plain(Batch B, Params P, Work W)
 // ------------------------------------------------------------------ launcher
 
 namespace {
+
+// Shared memory a warp-per-pair block may use for its slot rings.
+constexpr size_t kRingSmemMax = 96 * 1024;
 
 // Resident blocks per SM of each k_inter instantiation, set by prepare_kernels.
 int g_inter_blocks[8] = {1, 1, 1, 1, 1, 1, 1, 1};
@@ -958,10 +993,22 @@ cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, c
     return launch_inter<NMAX, true>(B, P, W, cls, st, sms);
 }
 
+// Ring size for the context's band: the smallest power of two >= 2*w + 3,
+// capped so that a block's rings fit in shared memory (0: no ring).
+inline int ring_log2_for(const Params &P, int slot_bytes)
+{
+    int lg = 6;
+    while ((1 << lg) < 2 * P.w + 3 && lg < 16) ++lg;
+    const size_t per_block = (size_t)(kWarpKernelThreads / 32) * slot_bytes << lg;
+    return per_block <= kRingSmemMax ? lg : 0;
+}
+
 template <int C, bool S16>
 cudaError_t launch_warp(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int blocks)
 {
-    k_warp<C, S16><<<blocks, kWarpKernelThreads, 0, st>>>(B, P, W, cls);
+    const int lg = ring_log2_for(P, SlotIO<S16>::kBytes);
+    const size_t smem = lg ? (size_t)(kWarpKernelThreads / 32) * SlotIO<S16>::kBytes << lg : 0;
+    k_warp<C, S16><<<blocks, kWarpKernelThreads, smem, st>>>(B, P, W, cls, lg);
     return cudaGetLastError();
 }
 
@@ -971,6 +1018,10 @@ cudaError_t prepare_kernels(int sms)
 {
     (void)sms;
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_warp<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_warp<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
+        return e;
     if ((e = prepare_inter<256, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<128, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<64, true>()) != cudaSuccess) return e;
@@ -1006,8 +1057,8 @@ cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const
     if ((e = launch_u8<128>(B, P, W, 1, S.side[0], sms)) != cudaSuccess) return e;
     if ((e = launch_u8<64>(B, P, W, 2, S.side[1], sms)) != cudaSuccess) return e;
     if ((e = launch_u8<32>(B, P, W, 3, S.side[1], sms)) != cudaSuccess) return e;
-    if ((e = launch_warp<4, true>(B, P, W, 8, S.side[2], wblocks)) != cudaSuccess) return e;
-    if ((e = launch_warp<4, false>(B, P, W, 9, S.side[2], wblocks)) != cudaSuccess) return e;
+    if ((e = launch_warp<8, true>(B, P, W, 8, S.side[2], wblocks)) != cudaSuccess) return e;
+    if ((e = launch_warp<8, false>(B, P, W, 9, S.side[2], wblocks)) != cudaSuccess) return e;
     if ((e = launch_inter<256, false>(B, P, W, 4, S.side[2], sms)) != cudaSuccess) return e;
     if ((e = launch_inter<128, false>(B, P, W, 5, S.side[2], sms)) != cudaSuccess) return e;
     if ((e = launch_inter<64, false>(B, P, W, 6, S.side[2], sms)) != cudaSuccess) return e;
@@ -1017,7 +1068,7 @@ cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const
         if ((e = cudaStreamWaitEvent(S.main, S.join[k], 0)) != cudaSuccess) return e;
     }
     // Section V-D1: pairs whose scores left their lane range, exactly, in 32 bits.
-    return launch_warp<4, false>(B, P, W, kRerun, S.main, wblocks);
+    return launch_warp<8, false>(B, P, W, kRerun, S.main, wblocks);
 }
 
 cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms,
@@ -1039,9 +1090,9 @@ cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W
     if ((e = launch_inter<128, false>(B, P, W, 5, st, sms)) != cudaSuccess) return e;
     if ((e = launch_inter<64, false>(B, P, W, 6, st, sms)) != cudaSuccess) return e;
     if ((e = launch_inter<32, false>(B, P, W, 7, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_warp<4, true>(B, P, W, 8, st, warp_blocks)) != cudaSuccess) return e;
-    if ((e = launch_warp<4, false>(B, P, W, 9, st, warp_blocks)) != cudaSuccess) return e;
-    return launch_warp<4, false>(B, P, W, kRerun, st, warp_blocks);
+    if ((e = launch_warp<8, true>(B, P, W, 8, st, warp_blocks)) != cudaSuccess) return e;
+    if ((e = launch_warp<8, false>(B, P, W, 9, st, warp_blocks)) != cudaSuccess) return e;
+    return launch_warp<8, false>(B, P, W, kRerun, st, warp_blocks);
 }
 
 cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms)
