@@ -835,18 +835,218 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
     return ncell;
 }
 
+// Ring position of column j with one padding word per 8: lane L of a chunk
+// reads column cb + 8L + k, and 9L mod 32 is distinct for the 32 lanes, so
+// the strided accesses of a chunk hit 32 different banks.
+__device__ __forceinline__ int ring_pos(int j, int mask)
+{
+    const int r = j & mask;
+    return r + (r >> 3);
+}
+
+// The warp-per-pair extension with 16-bit slots in a shared-memory ring
+// (scores up to 32767) and 8 columns per lane.  Chunks that lie entirely in
+// the band take a path without per-column predicates; the row's best cell is
+// the maximum of H * 32768 + column over the warp (ties to the larger column).
+__device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, int p, uint32_t *ring,
+                                               int mask)
+{
+    constexpr int C = 8;
+    const int lane = threadIdx.x & 31;
+    const int n = B.q_len[p], m = B.t_len[p], h0 = B.h0[p];
+    const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
+    const int a = P.a, mb = -P.b;
+    const int e_del = P.e_del, e_ins = P.e_ins;
+    const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
+    const int64_t qoff = B.q_off[p];
+    const uint8_t *tp = B.t + (B.t_off[p] >> 2);
+    int hw = -1, lo = 0, hi = n;
+    int best = h0, bi = -1, bj = -1, gbest = -1, gi = -1, moff = 0;
+    unsigned long long ncell = 0;
+    for (int i = 0; i < m; ++i) {
+        const int tb = (__ldg(tp + (i >> 2)) >> (2 * (i & 3))) & 3;
+        const uint32_t tmask = (uint32_t)tb * 0x5555u;        // t_i in each 2-bit field
+        lo = max(lo, i - wb);
+        hi = min(min(hi, i + wb + 1), n);
+        if (hi - 1 > hw) {                                     // first visit of columns (hw, hi-1]
+            for (int c = hw + 1 + lane; c <= hi - 1; c += 32)
+                ring[ring_pos(c, mask)] = (uint32_t)(c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins));
+            hw = hi - 1;
+            __syncwarp();
+        }
+        const int hl0 = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
+        int carry_f = 0, carry_h = hl0, key_l = 0;
+        for (int cb = (lo / C) * C; lo < hi && cb < hi; cb += 32 * C) {
+            const int j0 = cb + lane * C;
+            const bool full = cb >= lo && cb + 32 * C <= hi;   // the same for the whole warp
+            uint32_t qbits = 0;
+            if (j0 < n) {
+                qbits = __ldg(B.q + ((qoff + j0) >> 2));
+                if (j0 + 4 < n) qbits |= (uint32_t)__ldg(B.q + ((qoff + j0 + 4) >> 2)) << 8;
+            }
+            const uint32_t x = qbits ^ tmask;
+            const uint32_t mism = (x | (x >> 1)) & 0x5555u;     // bit 2k: query base != t_i
+            // j0 is a multiple of 8 and the ring a multiple of 8 long, so the
+            // lane's 8 columns are 8 consecutive ring words.
+            uint32_t *rp = ring + ring_pos(j0, mask);
+            int M[C], Ev[C], Fl[C], H[C];
+            int floc = 0, cnt = C;
+            if (full) {
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const uint32_t raw = rp[k];
+                    const int d = (int)(raw & 0xffffu);
+                    Ev[k] = (int)(raw >> 16);
+                    const int sc = (mism >> (2 * k)) & 1u ? mb : a;
+                    M[k] = __viaddmin_s32(d, sc, d << 16);        // d > 0 ? d + sc : <= 0
+                    Fl[k] = floc;
+                    floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
+                }
+            } else {
+                cnt = 0;
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const int j = j0 + k;
+                    const bool act = j >= lo && j < hi;
+                    int d = 0, e = 0;
+                    if (act) {
+                        const uint32_t raw = rp[k];
+                        d = (int)(raw & 0xffffu);
+                        e = (int)(raw >> 16);
+                    }
+                    const int sc = (mism >> (2 * k)) & 1u ? mb : a;
+                    M[k] = act ? __viaddmin_s32(d, sc, d << 16) : 0;
+                    Ev[k] = e;
+                    Fl[k] = floc;
+                    if (act) {
+                        floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
+                        ++cnt;
+                    }
+                }
+            }
+            // F entering each lane: a warp scan of the lanes' maps f -> max(f - A, Bv).
+            int A = cnt * e_ins, Bv = cnt ? floc : kNeg;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int Ae = __shfl_up_sync(kFull, A, d), Be = __shfl_up_sync(kFull, Bv, d);
+                if (lane >= d) { Bv = max(Be - A, Bv); A = Ae + A; }
+            }
+            int Aex = __shfl_up_sync(kFull, A, 1), Bex = __shfl_up_sync(kFull, Bv, 1);
+            if (lane == 0) { Aex = 0; Bex = kNeg; }
+            int g = max(carry_f - Aex, Bex);
+            int hlast = 0;
+            if (full) {
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const int F = max(Fl[k], g);
+                    g -= e_ins;
+                    const int h = __vimax3_s32(M[k], Ev[k], F);
+                    H[k] = h;
+                    key_l = max(key_l, h * 32768 + j0 + k);
+                }
+                hlast = H[C - 1];
+            } else {
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const int j = j0 + k;
+                    const bool act = j >= lo && j < hi;
+                    const int F = max(Fl[k], g);
+                    if (act) g -= e_ins;
+                    const int h = __vimax3_s32(M[k], Ev[k], F);
+                    H[k] = h;
+                    if (act) {
+                        key_l = max(key_l, h * 32768 + j);
+                        hlast = h;
+                    }
+                }
+            }
+            int hin = __shfl_up_sync(kFull, hlast, 1);
+            if (lane == 0 || j0 <= lo) hin = carry_h;
+            if (full) {
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - oe_del);
+                    rp[k] = (uint32_t)hin | ((uint32_t)e2 << 16);
+                    hin = H[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const int j = j0 + k;
+                    if (j >= lo && j < hi) {
+                        const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - oe_del);
+                        rp[k] = (uint32_t)hin | ((uint32_t)e2 << 16);
+                        hin = H[k];
+                    }
+                }
+            }
+            const int A31 = __shfl_sync(kFull, A, 31), B31 = __shfl_sync(kFull, Bv, 31);
+            carry_f = max(carry_f - A31, B31);
+            const int end = min(cb + 32 * C, hi);
+            carry_h = __shfl_sync(kFull, hlast, (end - 1 - cb) / C);
+        }
+        const int hl = carry_h;
+        __syncwarp();
+        if (lane == 0) ring[ring_pos(hi, mask)] = (uint32_t)hl;
+        hw = max(hw, hi);
+        __syncwarp();
+        const int key = (int)__reduce_max_sync(kFull, (unsigned)key_l);
+        const int rm = key >> 15, rj = key & 32767;
+        if (hi > lo) ncell += (unsigned)(hi - lo);
+        if (max(lo, hi) == n) {
+            if (hl >= gbest) gi = i;
+            gbest = max(gbest, hl);
+        }
+        if (rm == 0) break;
+        if (rm > best) {
+            best = rm; bi = i; bj = rj;
+            moff = max(moff, abs(rj - i));
+        } else if (P.zdrop > 0) {
+            const int di = i - bi, dj = rj - bj;
+            const int drop = di > dj ? best - rm - (di - dj) * e_del : best - rm - (dj - di) * e_ins;
+            if (drop > P.zdrop) break;
+        }
+        int nlo = hi;                                          // rule c with ballots
+        for (int base = lo; base < hi; base += 32) {
+            const int j = base + lane;
+            const uint32_t v = j < hi ? ring[ring_pos(j, mask)] : 0u;
+            const unsigned bal = __ballot_sync(kFull, v != 0u);
+            if (bal) { nlo = base + __ffs(bal) - 1; break; }
+        }
+        lo = nlo;
+        int last = lo - 1;
+        for (int top = hi; top >= lo; top -= 32) {
+            const int j = top - lane;
+            const uint32_t v = j >= lo ? ring[ring_pos(j, mask)] : 0u;
+            const unsigned bal = __ballot_sync(kFull, v != 0u);
+            if (bal) { last = top - (__ffs(bal) - 1); break; }
+        }
+        hi = min(last + 2, n);
+    }
+    if (lane == 0) store_result(&B.out[p], best, bj + 1, bi + 1, gi + 1, gbest, moff);
+    return ncell;
+}
+
+// Bytes of one warp's ring: 2^lg slots, plus one padding word per 8 for the
+// 16-bit ring (ring_pos).
+template <bool S16>
+__host__ __device__ constexpr size_t ring_bytes(int lg)
+{
+    return S16 ? ((size_t)4 << lg) + ((size_t)4 << lg) / 8 : (size_t)8 << lg;
+}
+
 // Persistent warp-per-pair kernel over a class list (or the re-run list).
 // ring_log2 > 0: each warp has a shared-memory slot ring of 1 << ring_log2
 // entries (dynamic shared memory); a pair whose band needs a larger ring uses
 // the warp's global slot scratch instead.
 template <int C, bool S16>
-__global__ void __launch_bounds__(256) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
+__global__ void __launch_bounds__(256, 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
 {
     extern __shared__ uint8_t ring_mem[];
     const int lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     uint8_t *slots = W.slots + gw * W.slot_bytes_per_warp;
-    uint8_t *ring = ring_mem + (size_t)(threadIdx.x >> 5) * ((size_t)SlotIO<S16>::kBytes << ring_log2);
+    uint8_t *ring = ring_mem + (size_t)(threadIdx.x >> 5) * ring_bytes<S16>(ring_log2);
     const int count = W.cls_count[cls];
     const int32_t *list = cls == kRerun ? W.rerun : W.order + W.cls_start[cls];
     unsigned long long cells = 0;
@@ -859,10 +1059,11 @@ __global__ void __launch_bounds__(256) k_warp(Batch B, Params P, Work W, int cls
         const int n = B.q_len[p];
         if (ring_log2 > 0) {
             const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
-            int need = 1;
+            int need = 64;                     // at least 64: a lane's 8 columns are 8 ring words
             while (need < 2 * wb + 3) need <<= 1;
             if (need <= (1 << ring_log2)) {
-                cells += warp_pair<C, S16, true>(B, P, p, ring, need - 1);
+                if (S16) cells += warp_pair_ring16(B, P, p, reinterpret_cast<uint32_t *>(ring), need - 1);
+                else cells += warp_pair<C, S16, true>(B, P, p, ring, need - 1);
                 continue;
             }
         }
@@ -995,19 +1196,20 @@ cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, c
 
 // Ring size for the context's band: the smallest power of two >= 2*w + 3,
 // capped so that a block's rings fit in shared memory (0: no ring).
-inline int ring_log2_for(const Params &P, int slot_bytes)
+template <bool S16>
+int ring_log2_for(const Params &P)
 {
     int lg = 6;
     while ((1 << lg) < 2 * P.w + 3 && lg < 16) ++lg;
-    const size_t per_block = (size_t)(kWarpKernelThreads / 32) * slot_bytes << lg;
+    const size_t per_block = (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16>(lg);
     return per_block <= kRingSmemMax ? lg : 0;
 }
 
 template <int C, bool S16>
 cudaError_t launch_warp(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int blocks)
 {
-    const int lg = ring_log2_for(P, SlotIO<S16>::kBytes);
-    const size_t smem = lg ? (size_t)(kWarpKernelThreads / 32) * SlotIO<S16>::kBytes << lg : 0;
+    const int lg = ring_log2_for<S16>(P);
+    const size_t smem = lg ? (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16>(lg) : 0;
     k_warp<C, S16><<<blocks, kWarpKernelThreads, smem, st>>>(B, P, W, cls, lg);
     return cudaGetLastError();
 }
