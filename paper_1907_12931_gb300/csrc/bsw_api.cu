@@ -649,7 +649,8 @@ int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonu
     *out = nullptr;
     bsw_ctx *c = new (std::nothrow) bsw_ctx();
     if (!c) return BSW_ENOMEM;
-    c->P = Params{sc->match, sc->mismatch, sc->o_del, sc->e_del, sc->o_ins, sc->e_ins, w, zdrop, end_bonus, 0u, kLongMax};
+    c->P = Params{sc->match, sc->mismatch, sc->o_del, sc->e_del, sc->o_ins, sc->e_ins, w, zdrop, end_bonus, 0u, kLongMax,
+                  1u << 8, 1u << 16, 1u << 24};
     c->budget.cap = mem_budget_bytes;
     int rc = BSW_OK;
     if (cudaGetDevice(&c->device) != cudaSuccess ||

@@ -30,6 +30,9 @@ struct Params {
     int32_t a, b, o_del, e_del, o_ins, e_ins, w, zdrop, end_bonus;
     uint32_t flags;
     int32_t max_qlen;   // longer queries are rejected (kStTooLong)
+    // 1<<8, 1<<16, 1<<24 as launch parameters: multiplying by them moves a
+    // byte with a multiply-add (FMA pipe) instead of a permute or shift (ALU).
+    uint32_t k8, k16, k24;
 };
 
 struct Batch {

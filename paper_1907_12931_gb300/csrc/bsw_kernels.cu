@@ -249,20 +249,38 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
         int f = 0, key = 0;   // key = H*512 + j: its max is the row max, ties to larger j
         if (U8) {
             const uint32_t prof = mis4 ^ (flip << (8 * tb));   // byte c: score of (t_i, c)
+            const uint32_t k8 = P.k8, k16 = P.k16, k24 = P.k24;
+            if (oe_del == oe_ins && e_del == e_ins) {
 #pragma unroll 4
-            for (int j = lo; j < hi; ++j) {
-                const uint32_t wv = S[j * 32];
-                const int sc = (int)prmt(prof, 0u, wv);
-                const int d = (int)prmt(wv, 0u, 0x4442u);         // H(i-1, j-1)
-                const int d8 = (int)prmt(wv, 0u, 0x4424u);        // d << 8
-                const int M = __viaddmin_s32(d, sc, d8);          // d > 0 ? d + sc : <= 0
-                const int e = (int)(wv >> 24);                    // E(i, j)
-                const int h = __vimax3_s32(M, e, f);              // Eq. 2
-                key = max(key, h * 512 + j);
-                const int e2 = __viaddmax_s32_relu(e, -e_del, M - oe_del);   // E(i+1, j)
-                f = __viaddmax_s32_relu(f, -e_ins, M - oe_ins);              // F(i, j+1)
-                S[j * 32] = prmt(wv, prmt((uint32_t)hl, (uint32_t)e2, 0x0040u), 0x5410u);
-                hl = h;
+                for (int j = lo; j < hi; ++j) {
+                    const uint32_t wv = S[j * 32];
+                    const int sc = (int)prmt(prof, 0u, wv);
+                    const int d = (int)prmt(wv, 0u, 0x4442u);                  // H(i-1, j-1)
+                    const int M = __viaddmin_s32(d, sc, (int)((uint32_t)d * k8));   // d > 0 ? d + sc : <= 0
+                    const int e = (int)(wv >> 24);                             // E(i, j)
+                    const int h = __vimax3_s32(M, e, f);                       // Eq. 2
+                    key = max(key, h * 512 + j);
+                    const int t = M - oe_del;
+                    const int e2 = __viaddmax_s32_relu(e, -e_del, t);          // E(i+1, j)
+                    f = __viaddmax_s32_relu(f, -e_ins, t);                     // F(i, j+1)
+                    S[j * 32] = (uint32_t)e2 * k24 + ((uint32_t)hl * k16 + (wv & 0xffffu));
+                    hl = h;
+                }
+            } else {
+#pragma unroll 4
+                for (int j = lo; j < hi; ++j) {
+                    const uint32_t wv = S[j * 32];
+                    const int sc = (int)prmt(prof, 0u, wv);
+                    const int d = (int)prmt(wv, 0u, 0x4442u);
+                    const int M = __viaddmin_s32(d, sc, (int)((uint32_t)d * k8));
+                    const int e = (int)(wv >> 24);
+                    const int h = __vimax3_s32(M, e, f);
+                    key = max(key, h * 512 + j);
+                    const int e2 = __viaddmax_s32_relu(e, -e_del, M - oe_del);
+                    f = __viaddmax_s32_relu(f, -e_ins, M - oe_ins);
+                    S[j * 32] = (uint32_t)e2 * k24 + ((uint32_t)hl * k16 + (wv & 0xffffu));
+                    hl = h;
+                }
             }
             const uint32_t wh = S[hi * 32];
             S[hi * 32] = (wh & 0xffffu) | ((uint32_t)(hl & 0xff) << 16);
