@@ -40,7 +40,7 @@ OPS_PER_CELL = 8
 # 32-bit integer lane-operations one SM issues per clock (4 schedulers x 32 lanes).
 LANE_OPS_PER_CLK_PER_SM = 128
 METRIC = "BSW GCUPS on 1 GB300 (batched vs plain kernel, bit-exact); p50/p99 serve latency"
-KERNELS_PER_STEP = 14    # classify, scan, scatter, 8 per-thread classes, 2 warp classes, re-run
+KERNELS_PER_STEP = 18    # classify, scan, scatter, 12 per-thread classes, 2 warp classes, re-run
 
 WORKLOAD_TEXT = {
     "read151": "151 bp short-read seed extensions: 2,000,000 left/right pairs from 1,000,000 reads of a 100 Mbp "
@@ -174,21 +174,24 @@ def measured_peaks():
 
 
 def class_of(q_len, t_len, h0, match=1):
-    """Kernel class of each pair, as the library buckets it: 0-3 8-bit lanes for
-    129-256 / 65-128 / 33-64 / 1-32 query bases, 4-7 the same with 16-bit lanes,
-    8 warp per pair with 16-bit slots, 9 warp per pair with 32-bit slots, -1 empty."""
+    """Kernel class of each pair, as the library buckets it: 0-7 8-bit lanes for
+    query lengths (192,256], (128,192], (96,128], (64,96], (48,64], (32,48],
+    (16,32], [1,16]; 8-11 16-bit lanes for (128,256], (64,128], (32,64], [1,32];
+    12 warp per pair with 16-bit slots; 13 with 32-bit slots; -1 empty."""
     n = np.asarray(q_len, np.int64)
     m = np.asarray(t_len, np.int64)
     bound = np.asarray(h0, np.int64) + match * np.minimum(n, m)
-    sub = np.select([n > 128, n > 64, n > 32], [0, 1, 2], 3)
-    c = np.where(n > 256, np.where(bound <= 32767, 8, 9),
-                 np.where(bound <= 255 - match, sub, np.where(bound <= 32767, 4 + sub, 9)))
+    u8 = np.select([n > 192, n > 128, n > 96, n > 64, n > 48, n > 32, n > 16], [0, 1, 2, 3, 4, 5, 6], 7)
+    i16 = 8 + np.select([n > 128, n > 64, n > 32], [0, 1, 2], 3)
+    c = np.where(n > 256, np.where(bound <= 32767, 12, 13),
+                 np.where(bound <= 255 - match, u8, np.where(bound <= 32767, i16, 13)))
     return np.where((n <= 0) | (m <= 0), -1, c)
 
 
-CLASS_KERNEL = {0: "k_inter<256,u8>", 1: "k_inter<128,u8>", 2: "k_inter<64,u8>", 3: "k_inter<32,u8>",
-                4: "k_inter<256,i16>", 5: "k_inter<128,i16>", 6: "k_inter<64,i16>", 7: "k_inter<32,i16>",
-                8: "k_warp<8,s16>", 9: "k_warp<8,s32>"}
+CLASS_KERNEL = {0: "k_inter<256,u8>", 1: "k_inter<192,u8>", 2: "k_inter<128,u8>", 3: "k_inter<96,u8>",
+                4: "k_inter<64,u8>", 5: "k_inter<48,u8>", 6: "k_inter<32,u8>", 7: "k_inter<16,u8>",
+                8: "k_inter<256,i16>", 9: "k_inter<128,i16>", 10: "k_inter<64,i16>", 11: "k_inter<32,i16>",
+                12: "k_warp<8,s16>", 13: "k_warp<8,s32>"}
 
 
 # ------------------------------------------------------------------ arms
@@ -315,7 +318,7 @@ def run_gb300(args):
     # dominant kernel: the 8-bit class with the most cells, as a batch of its own
     all_cls = class_of(wl.q_len, wl.t_len, wl.h0, wl.params.scoring.match)
     est = wl.q_len.astype(np.float64) * np.minimum(wl.t_len, 2 * wl.params.w + 1)
-    dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(10)]))
+    dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(14)]))
     sub = wl.subset(np.nonzero(all_cls == dom)[0])
     sdb = bsw.DeviceBatch(bsw.HostBatch(sub))
     ms_dom = time_device(ctx, sdb, 0, max(3, args.steps // 4), 2, stream, dist)

@@ -12,11 +12,13 @@ constexpr int kShortMax = 256;
 // Longest query the warp-per-pair kernel's slot scratch is sized for.
 constexpr int kLongMax = 32768;
 
-// Pair classes.  Classes 0-3: 8-bit lanes for query lengths (128,256], (64,128],
-// (32,64], [1,32]; 4-7: the same with 16-bit lanes; 8: warp per pair with 16-bit
-// slots; 9: warp per pair with 32-bit slots; 10: the re-run list (32-bit).
-constexpr int kNumClass = 10;
-constexpr int kRerun = 10;
+// Pair classes.  Classes 0-7: 8-bit lanes for query lengths (192,256],
+// (128,192], (96,128], (64,96], (48,64], (32,48], (16,32], [1,16]; 8-11:
+// 16-bit lanes for (128,256], (64,128], (32,64], [1,32]; 12: warp per pair with
+// 16-bit slots; 13: warp per pair with 32-bit slots; 14: the re-run list.
+constexpr int kNumClass = 14;
+constexpr int kRerun = 14;
+constexpr int kClsW16 = 12, kClsW32 = 13;
 
 // Counting-sort bins.  Within a class the bins run from long to short queries,
 // so the persistent kernels take the longest work first.

@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
 }
 
 // Class c covers bins [kClassBins[c], kClassBins[c+1]).
-__constant__ int kClassBins[kNumClass + 1] = {0, 128, 192, 224, 256, 384, 448, 480, 512, 1152, 1792};
+// (8-bit bins: 256 - n, so n in (192,256] is bins [0,64), ...; 16-bit bins follow at 256.)
+__constant__ int kClassBins[kNumClass + 1] = {0, 64, 128, 160, 192, 208, 224, 240, 256,
+                                              384, 448, 480, 512, 1152, 1792};
 
 // One block of 1024 threads: exclusive scan of the histogram into the scatter
 // cursors, class ranges, and a reset of the histogram and work counters.
@@ -1138,13 +1140,15 @@ namespace {
 constexpr size_t kRingSmemMax = 96 * 1024;
 
 // Resident blocks per SM of each k_inter instantiation, set by prepare_kernels.
-int g_inter_blocks[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+int g_inter_blocks[12] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 
-template <int NMAX> constexpr int inter_warps() { return NMAX >= 256 ? 2 : NMAX >= 128 ? 4 : 8; }
+template <int NMAX> constexpr int inter_warps() { return 2; }
 template <int NMAX> constexpr size_t inter_smem() { return (size_t)inter_warps<NMAX>() * (NMAX + 1) * 32 * 4; }
 template <int NMAX, bool U8> constexpr int inter_index()
 {
-    return (U8 ? 0 : 4) + (NMAX >= 256 ? 0 : NMAX >= 128 ? 1 : NMAX >= 64 ? 2 : 3);
+    return U8 ? (NMAX >= 256 ? 0 : NMAX >= 192 ? 1 : NMAX >= 128 ? 2 : NMAX >= 96 ? 3 : NMAX >= 64 ? 4 : NMAX >= 48 ? 5
+                 : NMAX >= 32 ? 6 : 7)
+              : 8 + (NMAX >= 256 ? 0 : NMAX >= 128 ? 1 : NMAX >= 64 ? 2 : 3);
 }
 
 template <int NMAX, bool U8>
@@ -1204,9 +1208,10 @@ bool inter2_ok(const Params &P)
 template <int NMAX>
 cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms)
 {
-    if (NMAX <= 128 && inter2_ok(P)) {
-        const int blocks = sms * g_inter2_blocks[inter2_index<NMAX>()];
-        k_inter2<NMAX><<<blocks, inter2_warps<NMAX>() * 32, inter2_smem<NMAX>(), st>>>(B, P, W, cls);
+    constexpr int N2 = NMAX > 64 ? 128 : NMAX > 32 ? 64 : 32;   // the packed kernel's sizes
+    if (inter2_ok(P)) {
+        const int blocks = sms * g_inter2_blocks[inter2_index<N2>()];
+        k_inter2<N2><<<blocks, inter2_warps<N2>() * 32, inter2_smem<N2>(), st>>>(B, P, W, cls);
         return cudaGetLastError();
     }
     return launch_inter<NMAX, true>(B, P, W, cls, st, sms);
@@ -1243,9 +1248,13 @@ cudaError_t prepare_kernels(int sms)
     if ((e = cudaFuncSetAttribute(k_warp<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
         return e;
     if ((e = prepare_inter<256, true>()) != cudaSuccess) return e;
+    if ((e = prepare_inter<192, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<128, true>()) != cudaSuccess) return e;
+    if ((e = prepare_inter<96, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<64, true>()) != cudaSuccess) return e;
+    if ((e = prepare_inter<48, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<32, true>()) != cudaSuccess) return e;
+    if ((e = prepare_inter<16, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<256, false>()) != cudaSuccess) return e;
     if ((e = prepare_inter<128, false>()) != cudaSuccess) return e;
     if ((e = prepare_inter<64, false>()) != cudaSuccess) return e;
@@ -1274,15 +1283,19 @@ cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const
         if ((e = cudaStreamWaitEvent(S.side[k], S.fork, 0)) != cudaSuccess) return e;
     const int wblocks = sms * kWarpBlocksPerSM;
     if ((e = launch_inter<256, true>(B, P, W, 0, S.side[0], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<128>(B, P, W, 1, S.side[0], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<64>(B, P, W, 2, S.side[1], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<32>(B, P, W, 3, S.side[1], sms)) != cudaSuccess) return e;
-    if ((e = launch_warp<8, true>(B, P, W, 8, S.side[2], wblocks)) != cudaSuccess) return e;
-    if ((e = launch_warp<8, false>(B, P, W, 9, S.side[2], wblocks)) != cudaSuccess) return e;
-    if ((e = launch_inter<256, false>(B, P, W, 4, S.side[2], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<128, false>(B, P, W, 5, S.side[2], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<64, false>(B, P, W, 6, S.side[2], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<32, false>(B, P, W, 7, S.side[2], sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<192, true>(B, P, W, 1, S.side[0], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<128>(B, P, W, 2, S.side[0], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<96>(B, P, W, 3, S.side[1], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<64>(B, P, W, 4, S.side[1], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<48>(B, P, W, 5, S.side[1], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<32>(B, P, W, 6, S.side[2], sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<16>(B, P, W, 7, S.side[2], sms)) != cudaSuccess) return e;
+    if ((e = launch_warp<8, true>(B, P, W, kClsW16, S.side[2], wblocks)) != cudaSuccess) return e;
+    if ((e = launch_warp<8, false>(B, P, W, kClsW32, S.side[2], wblocks)) != cudaSuccess) return e;
+    if ((e = launch_inter<256, false>(B, P, W, 8, S.side[2], sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<128, false>(B, P, W, 9, S.side[2], sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<64, false>(B, P, W, 10, S.side[2], sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<32, false>(B, P, W, 11, S.side[2], sms)) != cudaSuccess) return e;
     for (int k = 0; k < 3; ++k) {
         if ((e = cudaEventRecord(S.join[k], S.side[k])) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(S.main, S.join[k], 0)) != cudaSuccess) return e;
@@ -1303,15 +1316,19 @@ cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W
     k_scatter<<<sblocks, kScatterThreads, 0, st>>>(B.n, W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_inter<256, true>(B, P, W, 0, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<128>(B, P, W, 1, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<64>(B, P, W, 2, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<32>(B, P, W, 3, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<256, false>(B, P, W, 4, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<128, false>(B, P, W, 5, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<64, false>(B, P, W, 6, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<32, false>(B, P, W, 7, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_warp<8, true>(B, P, W, 8, st, warp_blocks)) != cudaSuccess) return e;
-    if ((e = launch_warp<8, false>(B, P, W, 9, st, warp_blocks)) != cudaSuccess) return e;
+    if ((e = launch_inter<192, true>(B, P, W, 1, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<128>(B, P, W, 2, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<96>(B, P, W, 3, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<64>(B, P, W, 4, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<48>(B, P, W, 5, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<32>(B, P, W, 6, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_u8<16>(B, P, W, 7, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<256, false>(B, P, W, 8, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<128, false>(B, P, W, 9, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<64, false>(B, P, W, 10, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_inter<32, false>(B, P, W, 11, st, sms)) != cudaSuccess) return e;
+    if ((e = launch_warp<8, true>(B, P, W, kClsW16, st, warp_blocks)) != cudaSuccess) return e;
+    if ((e = launch_warp<8, false>(B, P, W, kClsW32, st, warp_blocks)) != cudaSuccess) return e;
     return launch_warp<8, false>(B, P, W, kRerun, st, warp_blocks);
 }
 
