@@ -896,9 +896,17 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         }
         const int hl0 = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
         int carry_f = 0, carry_h = hl0, key_l = 0;
+        // Columns outside [lo, hi) are read as empty slots (H = E = 0): they
+        // give M <= 0 and E = 0, so F passes through them unchanged on the left
+        // (it is 0 there) and they never reach the row best on the right; only
+        // their stores are suppressed.  Every lane then counts C columns, and
+        // the F scan over lanes is a plain prefix max of floc + (lane+1)*C*e_ins.
+        const int ce = C * e_ins;
+        const int lane_ce = (lane + 1) * ce;
         for (int cb = (lo / C) * C; lo < hi && cb < hi; cb += 32 * C) {
             const int j0 = cb + lane * C;
             const bool full = cb >= lo && cb + 32 * C <= hi;   // the same for the whole warp
+            const bool last = cb + 32 * C >= hi;                // the chunk holding column hi-1
             uint32_t qbits = 0;
             if (j0 < n) {
                 qbits = __ldg(B.q + ((qoff + j0) >> 2));
@@ -909,79 +917,38 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
             // j0 is a multiple of 8 and the ring a multiple of 8 long, so the
             // lane's 8 columns are 8 consecutive ring words.
             uint32_t *rp = ring + ring_pos(j0, mask);
+            const int kl = min(max(lo - j0, 0), C), kh = min(max(hi - j0, 0), C);
+            const uint32_t am = full ? 0xffu : (((1u << kh) - 1u) & ~((1u << kl) - 1u));
             int M[C], Ev[C], Fl[C], H[C];
-            int floc = 0, cnt = C;
-            if (full) {
+            int floc = 0;
 #pragma unroll
-                for (int k = 0; k < C; ++k) {
-                    const uint32_t raw = rp[k];
-                    const int d = (int)(raw & 0xffffu);
-                    Ev[k] = (int)(raw >> 16);
-                    const int sc = (mism >> (2 * k)) & 1u ? mb : a;
-                    M[k] = __viaddmin_s32(d, sc, d << 16);        // d > 0 ? d + sc : <= 0
-                    Fl[k] = floc;
-                    floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
-                }
-            } else {
-                cnt = 0;
-#pragma unroll
-                for (int k = 0; k < C; ++k) {
-                    const int j = j0 + k;
-                    const bool act = j >= lo && j < hi;
-                    int d = 0, e = 0;
-                    if (act) {
-                        const uint32_t raw = rp[k];
-                        d = (int)(raw & 0xffffu);
-                        e = (int)(raw >> 16);
-                    }
-                    const int sc = (mism >> (2 * k)) & 1u ? mb : a;
-                    M[k] = act ? __viaddmin_s32(d, sc, d << 16) : 0;
-                    Ev[k] = e;
-                    Fl[k] = floc;
-                    if (act) {
-                        floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
-                        ++cnt;
-                    }
-                }
+            for (int k = 0; k < C; ++k) {
+                uint32_t raw = rp[k];
+                if (!full) raw &= 0u - ((am >> k) & 1u);
+                const int d = (int)(raw & 0xffffu);
+                Ev[k] = (int)(raw >> 16);
+                const int sc = (mism >> (2 * k)) & 1u ? mb : a;
+                M[k] = __viaddmin_s32(d, sc, d << 16);        // d > 0 ? d + sc : <= 0
+                Fl[k] = floc;
+                floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
             }
-            // F entering each lane: a warp scan of the lanes' maps f -> max(f - A, Bv).
-            int A = cnt * e_ins, Bv = cnt ? floc : kNeg;
+            int v = floc + lane_ce;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int Ae = __shfl_up_sync(kFull, A, d), Be = __shfl_up_sync(kFull, Bv, d);
-                if (lane >= d) { Bv = max(Be - A, Bv); A = Ae + A; }
+            for (int d = 1; d < 32; d <<= 1) v = max(v, __shfl_up_sync(kFull, v, d));
+            int vex = __shfl_up_sync(kFull, v, 1);
+            if (lane == 0) vex = carry_f;
+            int g = max(carry_f, vex) - lane * ce;              // F entering the lane's first column
+            const int vall = __shfl_sync(kFull, v, 31);
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const int F = max(Fl[k], g);
+                g -= e_ins;
+                const int h = __vimax3_s32(M[k], Ev[k], F);
+                H[k] = h;
+                key_l = max(key_l, h * 32768 + j0 + k);
             }
-            int Aex = __shfl_up_sync(kFull, A, 1), Bex = __shfl_up_sync(kFull, Bv, 1);
-            if (lane == 0) { Aex = 0; Bex = kNeg; }
-            int g = max(carry_f - Aex, Bex);
-            int hlast = 0;
-            if (full) {
-#pragma unroll
-                for (int k = 0; k < C; ++k) {
-                    const int F = max(Fl[k], g);
-                    g -= e_ins;
-                    const int h = __vimax3_s32(M[k], Ev[k], F);
-                    H[k] = h;
-                    key_l = max(key_l, h * 32768 + j0 + k);
-                }
-                hlast = H[C - 1];
-            } else {
-#pragma unroll
-                for (int k = 0; k < C; ++k) {
-                    const int j = j0 + k;
-                    const bool act = j >= lo && j < hi;
-                    const int F = max(Fl[k], g);
-                    if (act) g -= e_ins;
-                    const int h = __vimax3_s32(M[k], Ev[k], F);
-                    H[k] = h;
-                    if (act) {
-                        key_l = max(key_l, h * 32768 + j);
-                        hlast = h;
-                    }
-                }
-            }
-            int hin = __shfl_up_sync(kFull, hlast, 1);
-            if (lane == 0 || j0 <= lo) hin = carry_h;
+            int hin = __shfl_up_sync(kFull, H[C - 1], 1);
+            if (lane == 0) hin = carry_h;
             if (full) {
 #pragma unroll
                 for (int k = 0; k < C; ++k) {
@@ -992,18 +959,22 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
             } else {
 #pragma unroll
                 for (int k = 0; k < C; ++k) {
-                    const int j = j0 + k;
-                    if (j >= lo && j < hi) {
-                        const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - oe_del);
-                        rp[k] = (uint32_t)hin | ((uint32_t)e2 << 16);
-                        hin = H[k];
-                    }
+                    const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - oe_del);
+                    if ((am >> k) & 1u) rp[k] = (uint32_t)hin | ((uint32_t)e2 << 16);
+                    hin = H[k];
                 }
             }
-            const int A31 = __shfl_sync(kFull, A, 31), B31 = __shfl_sync(kFull, Bv, 31);
-            carry_f = max(carry_f - A31, B31);
-            const int end = min(cb + 32 * C, hi);
-            carry_h = __shfl_sync(kFull, hlast, (end - 1 - cb) / C);
+            carry_f = max(carry_f, vall) - 32 * ce;
+            if (last) {                                          // H(i, hi-1)
+                const int owner = (hi - 1 - cb) / C, kk = (hi - 1 - cb) % C;
+                int hsel = H[0];
+#pragma unroll
+                for (int k = 1; k < C; ++k)
+                    if (k == kk) hsel = H[k];
+                carry_h = __shfl_sync(kFull, hsel, owner);
+            } else {
+                carry_h = __shfl_sync(kFull, H[C - 1], 31);
+            }
         }
         const int hl = carry_h;
         __syncwarp();
