@@ -40,7 +40,8 @@ OPS_PER_CELL = 8
 # 32-bit integer lane-operations one SM issues per clock (4 schedulers x 32 lanes).
 LANE_OPS_PER_CLK_PER_SM = 128
 METRIC = "BSW GCUPS on 1 GB300 (batched vs plain kernel, bit-exact); p50/p99 serve latency"
-KERNELS_PER_STEP = 18    # classify, scan, scatter, 12 per-thread classes, 2 warp classes, re-run
+U8_NMAX = (256, 192, 128, 96, 64, 48, 32, 16)
+I16_NMAX = (256, 128, 64, 32)
 
 WORKLOAD_TEXT = {
     "read151": "151 bp short-read seed extensions: 2,000,000 left/right pairs from 1,000,000 reads of a 100 Mbp "
@@ -62,6 +63,7 @@ def parse():
     ap.add_argument("--pairs", type=int, default=None)
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default plan (no autotune)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point")
     return ap.parse_args()
 
@@ -173,25 +175,41 @@ def measured_peaks():
         return {}
 
 
-def class_of(q_len, t_len, h0, match=1):
-    """Kernel class of each pair, as the library buckets it: 0-7 8-bit lanes for
-    query lengths (192,256], (128,192], (96,128], (64,96], (48,64], (32,48],
-    (16,32], [1,16]; 8-11 16-bit lanes for (128,256], (64,128], (32,64], [1,32];
-    12 warp per pair with 16-bit slots; 13 with 32-bit slots; -1 empty."""
+def _smallest_class(n, nmax, mask, first):
+    """Index (first + k) of the smallest enabled bound nmax[k] >= n (bit 0 always on)."""
+    c = np.full(n.shape, first, np.int64)
+    for k in range(1, len(nmax)):
+        if (mask >> k) & 1:
+            c = np.where(n <= nmax[k], first + k, c)
+    return c
+
+
+def class_of(q_len, t_len, h0, match, plan):
+    """Kernel class of each pair under a plan, as the library buckets it: 0-7
+    8-bit lanes (class bounds 256..16), 8-11 16-bit lanes (256..32), 12 warp per
+    pair with 16-bit slots, 13 with 32-bit slots, -1 empty."""
     n = np.asarray(q_len, np.int64)
     m = np.asarray(t_len, np.int64)
     bound = np.asarray(h0, np.int64) + match * np.minimum(n, m)
-    u8 = np.select([n > 192, n > 128, n > 96, n > 64, n > 48, n > 32, n > 16], [0, 1, 2, 3, 4, 5, 6], 7)
-    i16 = 8 + np.select([n > 128, n > 64, n > 32], [0, 1, 2], 3)
-    c = np.where(n > 256, np.where(bound <= 32767, 12, 13),
-                 np.where(bound <= 255 - match, u8, np.where(bound <= 32767, i16, 13)))
+    u8 = _smallest_class(n, U8_NMAX, plan.u8_bounds | 1, 0)
+    i16 = _smallest_class(n, I16_NMAX, plan.i16_bounds | 1, 8)
+    c = np.where(n > plan.short_max, np.where(bound <= 32767, 12, 13),
+                 np.where(bound <= 255, u8, np.where(bound <= 32767, i16, 13)))
     return np.where((n <= 0) | (m <= 0), -1, c)
 
 
-CLASS_KERNEL = {0: "k_inter<256,u8>", 1: "k_inter<192,u8>", 2: "k_inter<128,u8>", 3: "k_inter<96,u8>",
-                4: "k_inter<64,u8>", 5: "k_inter<48,u8>", 6: "k_inter<32,u8>", 7: "k_inter<16,u8>",
-                8: "k_inter<256,i16>", 9: "k_inter<128,i16>", 10: "k_inter<64,i16>", 11: "k_inter<32,i16>",
-                12: "k_warp<8,s16>", 13: "k_warp<8,s32>"}
+def class_kernel(c, plan, scoring):
+    """Name of the kernel that runs class c under the plan."""
+    packable = (scoring.match + min(scoring.mismatch, 255 - scoring.match)
+                + max(min(scoring.o_del + scoring.e_del, 255), min(scoring.o_ins + scoring.e_ins, 255)) <= 256)
+    if c < 8:
+        nm = U8_NMAX[c]
+        if plan.packed and nm <= 128 and packable:
+            return "k_inter2<%d>" % (128 if nm > 64 else 64 if nm > 32 else 32)
+        return "k_inter<%d,u8>" % nm
+    if c < 12:
+        return "k_inter<%d,i16>" % I16_NMAX[c - 8]
+    return "k_warp<%d,s16>" % plan.warp_cols if c == 12 else "k_warp<8,s32>"
 
 
 # ------------------------------------------------------------------ arms
@@ -291,6 +309,10 @@ def run_gb300(args):
     db = bsw.DeviceBatch(hb)
     stream = torch.cuda.Stream()
     in_bytes = hb.nbytes()
+    # the execution plan: autotuned on a sample of this batch (outside the timed region)
+    t_tune = time.perf_counter()
+    plan = ctx.get_plan() if args.no_tune else ctx.autotune(db, sample_pairs=wl.n_pairs)
+    t_tune = time.perf_counter() - t_tune
 
     # batched path, timed with clocks sampled
     clocks = ClockSampler(local)
@@ -301,6 +323,12 @@ def run_gb300(args):
     total_cells = dist.sum(cells)
     gcups = total_cells / (ms * 1e-3) / 1e9
     out_batched = db.out.cpu().numpy().copy()
+
+    # kernels per step and each class kernel's time within one step (events on
+    # the kernels' own streams; one untimed-region call without a graph)
+    ctx.extend_device(db, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH, stream.cuda_stream)
+    launches_per_step, step_class_ms = ctx.kernel_times()
+    ctx.sync(stream.cuda_stream)
 
     # plain one-pair-per-warp kernel on the same inputs
     p_steps = max(3, args.steps // 10)
@@ -315,13 +343,21 @@ def run_gb300(args):
     packed_equal = bool(np.array_equal(db.out.cpu().numpy(), out_batched))
     gcups_packed = total_cells / (ms_packed * 1e-3) / 1e9
 
-    # dominant kernel: the 8-bit class with the most cells, as a batch of its own
-    all_cls = class_of(wl.q_len, wl.t_len, wl.h0, wl.params.scoring.match)
+    # dominant kernel: the class with the most cells, as a batch of its own;
+    # its kernel's duration from the events around its launch, averaged
+    all_cls = class_of(wl.q_len, wl.t_len, wl.h0, wl.params.scoring.match, plan)
     est = wl.q_len.astype(np.float64) * np.minimum(wl.t_len, 2 * wl.params.w + 1)
     dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(14)]))
     sub = wl.subset(np.nonzero(all_cls == dom)[0])
     sdb = bsw.DeviceBatch(bsw.HostBatch(sub))
-    ms_dom = time_device(ctx, sdb, 0, max(3, args.steps // 4), 2, stream, dist)
+    for _ in range(2):
+        ctx.extend_device(sdb, bsw.BSW_NO_GRAPH, stream.cuda_stream)
+    dom_ms = []
+    for _ in range(max(3, args.steps // 4)):
+        ctx.extend_device(sdb, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH, stream.cuda_stream)
+        dom_ms.append(ctx.kernel_times()[1][dom])
+    ctx.sync(stream.cuda_stream)
+    ms_dom = dist.max(statistics.mean(dom_ms))
     dom_cells = int(sdb.cells.item())
     del sdb
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -374,8 +410,11 @@ def run_gb300(args):
                                      "bit_exact_vs_batched": packed_equal},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
-                         "kernel": "%s (batch of its own class: %d pairs, %d cells)"
-                                   % (CLASS_KERNEL[dom], sub.n_pairs, dom_cells),
+                         "kernel": "%s (batch of its own class: %d pairs, %d cells; CUDA events around the "
+                                   "kernel on its stream, mean of %d launches)"
+                                   % (class_kernel(dom, plan, wl.params.scoring), sub.n_pairs, dom_cells,
+                                      len(dom_ms)),
+                         "launch_ms": round(ms_dom, 4),
                          "ops_per_cell": OPS_PER_CELL,
                          "peak_basis": "%d SMs x %.0f MHz (median under load) x %d lane-ops/clk"
                                        % (sms, f_mhz, LANE_OPS_PER_CLK_PER_SM)},
@@ -383,7 +422,10 @@ def run_gb300(args):
             "parity_sample": parity,
             "e2e": {"value": round(e2e, 3), "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(t_e2e * 1e3, 3), "bit_exact_vs_device": e2e_equal},
-            "gpu_launches": KERNELS_PER_STEP * (args.steps),
+            "gpu_launches": launches_per_step * args.steps,
+            "kernels_per_step": launches_per_step,
+            "class_ms_in_step": {bsw.CLASS_NAMES[c]: round(t, 4) for c, t in enumerate(step_class_ms) if t > 0},
+            "plan": dict(plan.as_dict(), tuned=not args.no_tune, tune_s=round(t_tune, 2)),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"]},
             "peaks_file": {k: measured_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},

@@ -70,6 +70,9 @@ extern "C" {
 #define BSW_COPY_INPUTS   0x40u  /* submit: copy host inputs at submit time                */
 #define BSW_PACKED_PAIRS  0x80u  /* 8-bit classes up to 128 query bases: two pairs per
                                     thread in packed 16-bit lanes instead of one        */
+#define BSW_TIME_KERNELS  0x100u /* record CUDA events around each class kernel (host
+                                    pointers, or device pointers with BSW_NO_GRAPH);
+                                    read them with bsw_kernel_times                     */
 
 typedef struct bsw_ctx bsw_ctx_t;
 
@@ -220,6 +223,81 @@ int32_t bsw_band_width(const bsw_ctx_t *ctx, int32_t qlen, int32_t w);
 int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonus,
                              const bsw_batch_t *batch, bsw_result_t *out, int64_t *cells_out,
                              void *cuda_stream);
+
+/*
+ * Execution plan of the batched path: which kernel runs which pairs.  The
+ * paper fixes these choices for 512-bit vectors (Section V-C: sort by length,
+ * 8-bit lanes first, 16-bit re-run); here they are parameters.  Every plan
+ * computes the same results; plans differ only in speed.
+ *
+ *   short_max    queries of up to short_max bases run one pair per thread (the
+ *                per-thread length classes); longer ones one pair per warp.
+ *                64 <= short_max <= 256.
+ *   u8_bounds    bit k (k = 1..7) keeps the 8-bit class boundary at
+ *                192, 128, 96, 64, 48, 32, 16 bases; the 256 class (bit 0) is
+ *                always kept.  A query runs in the smallest kept class that
+ *                holds it (a class of bound N keeps N + 1 slots per thread).
+ *   i16_bounds   the same for the 16-bit classes: bits 1..3 = 128, 64, 32.
+ *   packed       1: the 8-bit classes up to 128 bases run two pairs per thread
+ *                in packed 16-bit lanes, where the scoring allows it (small
+ *                mismatch and gap costs); 0: one pair per thread.
+ *   warp_cols    columns each lane owns per row chunk in the 16-bit
+ *                warp-per-pair kernel: 4, 8 or 16.
+ *   inter_warps  warps per block of the per-thread kernels: 1, 2 or 4.
+ *   ms           output of bsw_autotune (the plan's time on its sample, in
+ *                milliseconds); ignored by bsw_set_plan.
+ */
+typedef struct {
+    int32_t short_max;
+    uint32_t u8_bounds, i16_bounds;
+    int32_t packed, warp_cols, inter_warps;
+    float ms;
+} bsw_plan_t;
+
+/* The context's current plan (a new context has {256, 0xff, 0xf, 0, 8, 2}).
+ * Errors: BSW_EINVAL (null argument). */
+int bsw_get_plan(const bsw_ctx_t *ctx, bsw_plan_t *plan);
+
+/* Use `plan` for every later call on the context.  Errors: BSW_EINVAL (a field
+ * out of range), BSW_ESTATE (submitted work still pending). */
+int bsw_set_plan(bsw_ctx_t *ctx, const bsw_plan_t *plan);
+
+/*
+ * Autotune the plan on a sample of `batch`: its first min(n_pairs,
+ * sample_pairs) pairs (sample_pairs <= 0: 2097152).  Each candidate plan is
+ * timed with CUDA events as the fastest of `reps` launches (reps <= 0: 3)
+ * after one warm-up launch, on the context's stream.  The search is
+ * coordinate descent from the default plan: short_max (256, 192, 128, 96,
+ * 64), warp_cols (8, 4, 16), packed, inter_warps (2, 1, 4), then each class
+ * boundary removed in turn (8-bit from 192 down, then 16-bit); a change is
+ * kept when it is at least 1% faster than the best so far.  The fastest plan
+ * becomes the context's plan and is written to *chosen (nullable).
+ *
+ * batch: host pointers, or device pointers with BSW_DEVICE_PTRS (other flags
+ * are rejected); the sample's results are computed and discarded.  The call
+ * returns when tuning is done.  Errors: as bsw_extend_batch, and BSW_ESTATE
+ * (submitted work still pending).
+ */
+int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *batch, int64_t sample_pairs, int32_t reps,
+                 bsw_plan_t *chosen);
+
+/*
+ * Kernel times of the last bsw_extend_batch call made with BSW_TIME_KERNELS.
+ * Waits for that call's work, then class_ms[c] = the time between the CUDA
+ * events recorded on the stream of class c's kernel just before and just
+ * after its launch (0 if the class was not launched).  Classes: 0-7 the 8-bit
+ * per-thread classes of bound 256, 192, 128, 96, 64, 48, 32, 16; 8-11 the
+ * 16-bit classes of bound 256, 128, 64, 32; 12 the 16-bit warp-per-pair
+ * kernel; 13 the 32-bit one; 14 the 32-bit re-run.  launches = the kernels
+ * the last batched call launched (timed or not; the plain kernel counts 1).
+ * Errors: BSW_EINVAL (null argument), BSW_ESTATE (no timed call yet),
+ * BSW_ECUDA.
+ */
+typedef struct {
+    int32_t launches;
+    float class_ms[15];
+} bsw_timing_t;
+int bsw_kernel_times(bsw_ctx_t *ctx, bsw_timing_t *out);
 
 /* Library version string. */
 const char *bsw_version(void);

@@ -33,6 +33,11 @@ BSW_PLAIN_KERNEL = 0x10
 BSW_NO_GRAPH = 0x20
 BSW_COPY_INPUTS = 0x40
 BSW_PACKED_PAIRS = 0x80
+BSW_TIME_KERNELS = 0x100
+
+# class_ms indices of bsw_timing_t
+CLASS_NAMES = ("u8<256>", "u8<192>", "u8<128>", "u8<96>", "u8<64>", "u8<48>", "u8<32>", "u8<16>",
+               "i16<256>", "i16<128>", "i16<64>", "i16<32>", "warp16", "warp32", "rerun32")
 
 FIELDS = ("score", "qle", "tle", "gtle", "gscore", "max_off")
 
@@ -56,6 +61,19 @@ class bsw_batch_t(ctypes.Structure):
                 ("q", ctypes.c_void_p), ("q_off", ctypes.c_void_p), ("q_len", ctypes.c_void_p),
                 ("t", ctypes.c_void_p), ("t_off", ctypes.c_void_p), ("t_len", ctypes.c_void_p),
                 ("h0", ctypes.c_void_p), ("w_override", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class bsw_plan_t(ctypes.Structure):
+    _fields_ = [("short_max", ctypes.c_int32), ("u8_bounds", ctypes.c_uint32), ("i16_bounds", ctypes.c_uint32),
+                ("packed", ctypes.c_int32), ("warp_cols", ctypes.c_int32), ("inter_warps", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bsw_timing_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int32), ("class_ms", ctypes.c_float * 15)]
 
 
 _lib = None
@@ -94,6 +112,14 @@ def lib():
             L.bsw_extend_batch_noalloc.restype = ctypes.c_int
             L.bsw_version.argtypes = []
             L.bsw_version.restype = ctypes.c_char_p
+            L.bsw_get_plan.argtypes = [vp, ctypes.POINTER(bsw_plan_t)]
+            L.bsw_get_plan.restype = ctypes.c_int
+            L.bsw_set_plan.argtypes = [vp, ctypes.POINTER(bsw_plan_t)]
+            L.bsw_set_plan.restype = ctypes.c_int
+            L.bsw_autotune.argtypes = [vp, ctypes.POINTER(bsw_batch_t), i64, i32, ctypes.POINTER(bsw_plan_t)]
+            L.bsw_autotune.restype = ctypes.c_int
+            L.bsw_kernel_times.argtypes = [vp, ctypes.POINTER(bsw_timing_t)]
+            L.bsw_kernel_times.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -163,6 +189,34 @@ def bsw_pack_2bit(codes: np.ndarray) -> np.ndarray:
 
 def bsw_band_width(ctx: int, qlen: int, w: int) -> int:
     return int(lib().bsw_band_width(ctx, int(qlen), int(w)))
+
+
+def bsw_get_plan(ctx: int) -> bsw_plan_t:
+    p = bsw_plan_t()
+    rc = lib().bsw_get_plan(ctx, ctypes.byref(p))
+    if rc != BSW_OK:
+        raise BswError(rc, "bsw_get_plan")
+    return p
+
+
+def bsw_set_plan(ctx: int, plan: bsw_plan_t) -> int:
+    return lib().bsw_set_plan(ctx, ctypes.byref(plan))
+
+
+def bsw_autotune(ctx: int, batch: bsw_batch_t, sample_pairs: int, reps: int) -> tuple[int, bsw_plan_t]:
+    p = bsw_plan_t()
+    rc = lib().bsw_autotune(ctx, ctypes.byref(batch), int(sample_pairs), int(reps), ctypes.byref(p))
+    return rc, p
+
+
+def bsw_kernel_times(ctx: int) -> tuple[int, bsw_timing_t]:
+    t = bsw_timing_t()
+    rc = lib().bsw_kernel_times(ctx, ctypes.byref(t))
+    return rc, t
+
+
+def make_plan(short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8, inter_warps=2) -> bsw_plan_t:
+    return bsw_plan_t(short_max, u8_bounds, i16_bounds, packed, warp_cols, inter_warps, 0.0)
 
 
 # --------------------------------------------------------------- marshalling
@@ -269,6 +323,28 @@ class Context:
 
     def poll(self, ticket: int, timeout_us: int = -1) -> int:
         return bsw_stream_poll(self.handle, ticket, timeout_us)
+
+    def get_plan(self) -> bsw_plan_t:
+        return bsw_get_plan(self.handle)
+
+    def set_plan(self, plan: bsw_plan_t) -> None:
+        rc = bsw_set_plan(self.handle, plan)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_set_plan")
+
+    def autotune(self, batch, sample_pairs: int = 0, reps: int = 0) -> bsw_plan_t:
+        """Tune the plan on a HostBatch or DeviceBatch; returns the chosen plan."""
+        rc, p = bsw_autotune(self.handle, batch.struct(0), sample_pairs, reps)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_autotune")
+        return p
+
+    def kernel_times(self) -> tuple[int, list]:
+        """(launches, per-class ms) of the last call made with BSW_TIME_KERNELS."""
+        rc, t = bsw_kernel_times(self.handle)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_kernel_times")
+        return t.launches, list(t.class_ms)
 
     def band_width(self, qlen: int, w: int | None = None) -> int:
         return bsw_band_width(self.handle, qlen, self.params.w if w is None else w)

@@ -35,6 +35,15 @@ struct Params {
     // 1<<8, 1<<16, 1<<24 as launch parameters: multiplying by them moves a
     // byte with a multiply-add (FMA pipe) instead of a permute or shift (ALU).
     uint32_t k8, k16, k24;
+    // Queries longer than this run one pair per warp (the per-thread classes
+    // take the rest, up to kShortMax); a tuning choice, 64 <= short_max <= 256.
+    int32_t short_max;
+};
+
+// Class c covers the counting-sort bins [b[c], b[c+1]); a class with an empty
+// range is not launched.  Set from the tuning plan (bucket boundaries).
+struct ClassTable {
+    int32_t b[kNumClass + 1];
 };
 
 struct Batch {

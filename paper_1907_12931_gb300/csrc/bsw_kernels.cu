@@ -62,11 +62,13 @@ __device__ __forceinline__ void store_result(bsw_result_t *out, int score, int q
 
 // ------------------------------------------------------------------ bucketing
 
-__device__ __forceinline__ int pick_bin(int n, long long bound, uint32_t flags)
+__device__ __forceinline__ int pick_bin(int n, long long bound, uint32_t flags, int short_max)
 {
     const int rank = 639 - min(n >> 6, 639);
     if (flags & BSW_FORCE_I32) return kBinW32 + rank;
-    if (n <= kShortMax) {
+    // The forced lane widths are test modes: they keep every query up to
+    // kShortMax on the per-thread kernels whatever the plan says.
+    if (n <= ((flags & (BSW_FORCE_I8 | BSW_FORCE_I16)) ? kShortMax : short_max)) {
         if (flags & BSW_FORCE_I8) return kBinU8 + (kShortMax - n);
         if (flags & BSW_FORCE_I16) return kBinI16 + (kShortMax - n);
         if (bound <= 255) return kBinU8 + (kShortMax - n);
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
             const long long bound = (long long)h0 + (long long)P.a * min(n, m);
             if (bound >= (1ll << 30)) atomicOr(W.status, kStInval);
             else if (n > P.max_qlen) atomicOr(W.status, kStTooLong);
-            else key = pick_bin(n, bound, P.flags);
+            else key = pick_bin(n, bound, P.flags, P.short_max);
         }
         W.key[p] = key;
         if (key >= 0) atomicAdd(&sh[key], 1u);
@@ -108,14 +110,11 @@ __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
         if (sh[k]) atomicAdd(&W.hist[k], sh[k]);
 }
 
-// Class c covers bins [kClassBins[c], kClassBins[c+1]).
-// (8-bit bins: 256 - n, so n in (192,256] is bins [0,64), ...; 16-bit bins follow at 256.)
-__constant__ int kClassBins[kNumClass + 1] = {0, 64, 128, 160, 192, 208, 224, 240, 256,
-                                              384, 448, 480, 512, 1152, 1792};
-
 // One block of 1024 threads: exclusive scan of the histogram into the scatter
-// cursors, class ranges, and a reset of the histogram and work counters.
-__global__ void __launch_bounds__(1024) k_scan(Work W)
+// cursors, class ranges (class c covers bins [T.b[c], T.b[c+1]); 8-bit bins
+// are 256 - n, 16-bit bins follow at 256), and a reset of the histogram and
+// work counters.
+__global__ void __launch_bounds__(1024) k_scan(Work W, ClassTable T)
 {
     __shared__ uint32_t pre[kNumBins + 1];
     __shared__ uint32_t wsum[32];
@@ -145,8 +144,8 @@ __global__ void __launch_bounds__(1024) k_scan(Work W)
     if (t == 0) pre[kNumBins] = wsum[31];
     __syncthreads();
     if (t < kNumClass) {
-        W.cls_start[t] = (int32_t)pre[kClassBins[t]];
-        W.cls_count[t] = (int32_t)(pre[kClassBins[t + 1]] - pre[kClassBins[t]]);
+        W.cls_start[t] = (int32_t)pre[T.b[t]];
+        W.cls_count[t] = (int32_t)(pre[T.b[t + 1]] - pre[T.b[t]]);
     }
     if (t == kRerun) { W.cls_start[t] = 0; W.cls_count[t] = 0; }
     if (t <= kNumClass) W.cls_next[t] = 0;
@@ -855,23 +854,27 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
     return ncell;
 }
 
-// Ring position of column j with one padding word per 8: lane L of a chunk
-// reads column cb + 8L + k, and 9L mod 32 is distinct for the 32 lanes, so
-// the strided accesses of a chunk hit 32 different banks.
+// Ring position of column j with one padding word per C: lane L of a chunk
+// reads column cb + C*L + k, and (C+1)*L mod 32 is distinct for the 32 lanes
+// (C+1 is odd), so the strided accesses of a chunk hit 32 different banks.
+template <int C>
 __device__ __forceinline__ int ring_pos(int j, int mask)
 {
     const int r = j & mask;
-    return r + (r >> 3);
+    return r + r / C;
 }
 
 // The warp-per-pair extension with 16-bit slots in a shared-memory ring
-// (scores up to 32767) and 8 columns per lane.  Chunks that lie entirely in
-// the band take a path without per-column predicates; the row's best cell is
-// the maximum of H * 32768 + column over the warp (ties to the larger column).
+// (scores up to 32767) and C columns per lane (4, 8 or 16).  Chunks that lie
+// entirely in the band take a path without per-column predicates; the row's
+// best cell is the maximum of H * 32768 + column over the warp (ties to the
+// larger column).
+template <int C>
 __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, int p, uint32_t *ring,
                                                int mask)
 {
-    constexpr int C = 8;
+    static_assert(C == 4 || C == 8 || C == 16, "columns per lane");
+    constexpr uint32_t kAll = (1u << C) - 1u;
     const int lane = threadIdx.x & 31;
     const int n = B.q_len[p], m = B.t_len[p], h0 = B.h0[p];
     const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
@@ -885,12 +888,12 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
     unsigned long long ncell = 0;
     for (int i = 0; i < m; ++i) {
         const int tb = (__ldg(tp + (i >> 2)) >> (2 * (i & 3))) & 3;
-        const uint32_t tmask = (uint32_t)tb * 0x5555u;        // t_i in each 2-bit field
+        const uint32_t tmask = (uint32_t)tb * 0x55555555u;    // t_i in each 2-bit field
         lo = max(lo, i - wb);
         hi = min(min(hi, i + wb + 1), n);
         if (hi - 1 > hw) {                                     // first visit of columns (hw, hi-1]
             for (int c = hw + 1 + lane; c <= hi - 1; c += 32)
-                ring[ring_pos(c, mask)] = (uint32_t)(c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins));
+                ring[ring_pos<C>(c, mask)] = (uint32_t)(c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins));
             hw = hi - 1;
             __syncwarp();
         }
@@ -908,17 +911,16 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
             const bool full = cb >= lo && cb + 32 * C <= hi;   // the same for the whole warp
             const bool last = cb + 32 * C >= hi;                // the chunk holding column hi-1
             uint32_t qbits = 0;
-            if (j0 < n) {
-                qbits = __ldg(B.q + ((qoff + j0) >> 2));
-                if (j0 + 4 < n) qbits |= (uint32_t)__ldg(B.q + ((qoff + j0 + 4) >> 2)) << 8;
-            }
+#pragma unroll
+            for (int u = 0; u < C / 4; ++u)
+                if (j0 + 4 * u < n) qbits |= (uint32_t)__ldg(B.q + ((qoff + j0) >> 2) + u) << (8 * u);
             const uint32_t x = qbits ^ tmask;
-            const uint32_t mism = (x | (x >> 1)) & 0x5555u;     // bit 2k: query base != t_i
-            // j0 is a multiple of 8 and the ring a multiple of 8 long, so the
-            // lane's 8 columns are 8 consecutive ring words.
-            uint32_t *rp = ring + ring_pos(j0, mask);
+            const uint32_t mism = (x | (x >> 1)) & 0x55555555u; // bit 2k: query base != t_i
+            // j0 is a multiple of C and the ring a multiple of C long, so the
+            // lane's C columns are C consecutive ring words.
+            uint32_t *rp = ring + ring_pos<C>(j0, mask);
             const int kl = min(max(lo - j0, 0), C), kh = min(max(hi - j0, 0), C);
-            const uint32_t am = full ? 0xffu : (((1u << kh) - 1u) & ~((1u << kl) - 1u));
+            const uint32_t am = full ? kAll : (((1u << kh) - 1u) & ~((1u << kl) - 1u));
             int M[C], Ev[C], Fl[C], H[C];
             int floc = 0;
 #pragma unroll
@@ -978,7 +980,7 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         }
         const int hl = carry_h;
         __syncwarp();
-        if (lane == 0) ring[ring_pos(hi, mask)] = (uint32_t)hl;
+        if (lane == 0) ring[ring_pos<C>(hi, mask)] = (uint32_t)hl;
         hw = max(hw, hi);
         __syncwarp();
         const int key = (int)__reduce_max_sync(kFull, (unsigned)key_l);
@@ -1000,7 +1002,7 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         int nlo = hi;                                          // rule c with ballots
         for (int base = lo; base < hi; base += 32) {
             const int j = base + lane;
-            const uint32_t v = j < hi ? ring[ring_pos(j, mask)] : 0u;
+            const uint32_t v = j < hi ? ring[ring_pos<C>(j, mask)] : 0u;
             const unsigned bal = __ballot_sync(kFull, v != 0u);
             if (bal) { nlo = base + __ffs(bal) - 1; break; }
         }
@@ -1008,7 +1010,7 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         int last = lo - 1;
         for (int top = hi; top >= lo; top -= 32) {
             const int j = top - lane;
-            const uint32_t v = j >= lo ? ring[ring_pos(j, mask)] : 0u;
+            const uint32_t v = j >= lo ? ring[ring_pos<C>(j, mask)] : 0u;
             const unsigned bal = __ballot_sync(kFull, v != 0u);
             if (bal) { last = top - (__ffs(bal) - 1); break; }
         }
@@ -1018,26 +1020,27 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
     return ncell;
 }
 
-// Bytes of one warp's ring: 2^lg slots, plus one padding word per 8 for the
+// Bytes of one warp's ring: 2^lg slots, plus one padding word per C for the
 // 16-bit ring (ring_pos).
-template <bool S16>
+template <bool S16, int C>
 __host__ __device__ constexpr size_t ring_bytes(int lg)
 {
-    return S16 ? ((size_t)4 << lg) + ((size_t)4 << lg) / 8 : (size_t)8 << lg;
+    return S16 ? ((size_t)4 << lg) + ((size_t)4 << lg) / C : (size_t)8 << lg;
 }
 
 // Persistent warp-per-pair kernel over a class list (or the re-run list).
 // ring_log2 > 0: each warp has a shared-memory slot ring of 1 << ring_log2
 // entries (dynamic shared memory); a pair whose band needs a larger ring uses
-// the warp's global slot scratch instead.
+// the warp's global slot scratch instead.  16 columns per lane need more
+// registers than two resident blocks per SM leave.
 template <int C, bool S16>
-__global__ void __launch_bounds__(256, 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
+__global__ void __launch_bounds__(256, C >= 16 ? 1 : 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
 {
     extern __shared__ uint8_t ring_mem[];
     const int lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     uint8_t *slots = W.slots + gw * W.slot_bytes_per_warp;
-    uint8_t *ring = ring_mem + (size_t)(threadIdx.x >> 5) * ring_bytes<S16>(ring_log2);
+    uint8_t *ring = ring_mem + (size_t)(threadIdx.x >> 5) * ring_bytes<S16, C>(ring_log2);
     const int count = W.cls_count[cls];
     const int32_t *list = cls == kRerun ? W.rerun : W.order + W.cls_start[cls];
     unsigned long long cells = 0;
@@ -1050,10 +1053,10 @@ __global__ void __launch_bounds__(256, 2) k_warp(Batch B, Params P, Work W, int 
         const int n = B.q_len[p];
         if (ring_log2 > 0) {
             const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
-            int need = 64;                     // at least 64: a lane's 8 columns are 8 ring words
+            int need = 64;                     // at least 64 >= C: a lane's C columns are C ring words
             while (need < 2 * wb + 3) need <<= 1;
             if (need <= (1 << ring_log2)) {
-                if (S16) cells += warp_pair_ring16(B, P, p, reinterpret_cast<uint32_t *>(ring), need - 1);
+                if (S16) cells += warp_pair_ring16<C>(B, P, p, reinterpret_cast<uint32_t *>(ring), need - 1);
                 else cells += warp_pair<C, S16, true>(B, P, p, ring, need - 1);
                 continue;
             }
@@ -1103,18 +1106,54 @@ __global__ void __launch_bounds__(256) k_plain(Batch B, Params P, Work W)
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
 
+
 // ------------------------------------------------------------------ launcher
+
+bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, int warp_cols, int inter_warps,
+               Plan *out)
+{
+    if (short_max < 64 || short_max > kShortMax) return false;
+    if (warp_cols != 4 && warp_cols != 8 && warp_cols != 16) return false;
+    if (inter_warps != 1 && inter_warps != 2 && inter_warps != 4) return false;
+    if ((u8_mask & ~0xffu) || (i16_mask & ~0xfu)) return false;
+    Plan L;
+    L.short_max = short_max;
+    L.packed = packed;
+    L.warp_cols = warp_cols;
+    L.inter_warps = inter_warps;
+    int32_t *b = L.cls.b;
+    // A disabled class gets an empty range; its queries fall to the next
+    // larger enabled class.
+    b[0] = kBinU8;
+    b[8] = kBinI16;
+    for (int c = 7; c >= 1; --c) b[c] = ((u8_mask >> c) & 1u) ? kBinU8 + kShortMax - kU8Nmax[c] : b[c + 1];
+    b[kClsW16] = kBinW16;
+    for (int c = 11; c >= 9; --c) b[c] = ((i16_mask >> (c - 8)) & 1u) ? kBinI16 + kShortMax - kI16Nmax[c - 8] : b[c + 1];
+    b[kClsW32] = kBinW32;
+    b[kNumClass] = kNumBins;
+    *out = L;
+    return true;
+}
+
+Plan default_plan()
+{
+    Plan L;
+    make_plan(kShortMax, 0xffu, 0xfu, false, 8, 2, &L);
+    return L;
+}
 
 namespace {
 
 // Shared memory a warp-per-pair block may use for its slot rings.
 constexpr size_t kRingSmemMax = 96 * 1024;
 
-// Resident blocks per SM of each k_inter instantiation, set by prepare_kernels.
-int g_inter_blocks[12] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+// Resident blocks per SM of each k_inter instantiation with 1, 2 and 4 warps
+// per block, set by prepare_kernels.
+int g_inter_blocks[12][3];
 
-template <int NMAX> constexpr int inter_warps() { return 2; }
-template <int NMAX> constexpr size_t inter_smem() { return (size_t)inter_warps<NMAX>() * (NMAX + 1) * 32 * 4; }
+int warps_index(int warps) { return warps <= 1 ? 0 : warps == 2 ? 1 : 2; }
+
+template <int NMAX> size_t inter_smem(int warps) { return (size_t)warps * (NMAX + 1) * 32 * 4; }
 template <int NMAX, bool U8> constexpr int inter_index()
 {
     return U8 ? (NMAX >= 256 ? 0 : NMAX >= 192 ? 1 : NMAX >= 128 ? 2 : NMAX >= 96 ? 3 : NMAX >= 64 ? 4 : NMAX >= 48 ? 5
@@ -1126,21 +1165,23 @@ template <int NMAX, bool U8>
 cudaError_t prepare_inter()
 {
     cudaError_t e = cudaFuncSetAttribute(k_inter<NMAX, U8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)inter_smem<NMAX>());
+                                         (int)inter_smem<NMAX>(4));
     if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inter<NMAX, U8>, inter_warps<NMAX>() * 32,
-                                                      inter_smem<NMAX>());
-    if (e != cudaSuccess) return e;
-    g_inter_blocks[inter_index<NMAX, U8>()] = nb > 0 ? nb : 1;
+    for (int wi = 0; wi < 3; ++wi) {
+        const int warps = 1 << wi;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inter<NMAX, U8>, warps * 32, inter_smem<NMAX>(warps));
+        if (e != cudaSuccess) return e;
+        g_inter_blocks[inter_index<NMAX, U8>()][wi] = nb > 0 ? nb : 1;
+    }
     return cudaSuccess;
 }
 
 template <int NMAX, bool U8>
-cudaError_t launch_inter(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms)
+cudaError_t launch_inter(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms, int warps)
 {
-    const int blocks = sms * g_inter_blocks[inter_index<NMAX, U8>()];
-    k_inter<NMAX, U8><<<blocks, inter_warps<NMAX>() * 32, inter_smem<NMAX>(), st>>>(B, P, W, cls);
+    const int blocks = sms * g_inter_blocks[inter_index<NMAX, U8>()][warps_index(warps)];
+    k_inter<NMAX, U8><<<blocks, warps * 32, inter_smem<NMAX>(warps), st>>>(B, P, W, cls);
     return cudaGetLastError();
 }
 
@@ -1166,55 +1207,149 @@ cudaError_t prepare_inter2()
 
 // The packed kernel holds every intermediate in a signed 16-bit lane only when
 // the mismatch and gap-open costs (clamped where larger ones act the same) fit.
-bool inter2_ok(const Params &P)
+bool inter2_scoring_ok(const Params &P)
 {
     const int bm = P.b < 255 - P.a ? P.b : 255 - P.a;
     const int od = P.o_del + P.e_del < 255 ? P.o_del + P.e_del : 255;
     const int oi = P.o_ins + P.e_ins < 255 ? P.o_ins + P.e_ins : 255;
-    return P.a + bm + od <= 256 && P.a + bm + oi <= 256 && (P.flags & BSW_PACKED_PAIRS);
+    return P.a + bm + od <= 256 && P.a + bm + oi <= 256;
 }
 
 // 8-bit class with queries up to NMAX: one pair per thread, or two pairs per
-// thread in packed 16-bit lanes when asked for and the scoring allows.
+// thread in packed 16-bit lanes when the plan (or the batch flag) asks for it
+// and the scoring allows.
 template <int NMAX>
-cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms)
+cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms, const Plan &L)
 {
     constexpr int N2 = NMAX > 64 ? 128 : NMAX > 32 ? 64 : 32;   // the packed kernel's sizes
-    if (inter2_ok(P)) {
+    if (NMAX <= 128 && (L.packed || (P.flags & BSW_PACKED_PAIRS)) && inter2_scoring_ok(P)) {
         const int blocks = sms * g_inter2_blocks[inter2_index<N2>()];
         k_inter2<N2><<<blocks, inter2_warps<N2>() * 32, inter2_smem<N2>(), st>>>(B, P, W, cls);
         return cudaGetLastError();
     }
-    return launch_inter<NMAX, true>(B, P, W, cls, st, sms);
+    return launch_inter<NMAX, true>(B, P, W, cls, st, sms, L.inter_warps);
 }
 
 // Ring size for the context's band: the smallest power of two >= 2*w + 3,
 // capped so that a block's rings fit in shared memory (0: no ring).
-template <bool S16>
+template <bool S16, int C>
 int ring_log2_for(const Params &P)
 {
     int lg = 6;
     while ((1 << lg) < 2 * P.w + 3 && lg < 16) ++lg;
-    const size_t per_block = (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16>(lg);
+    const size_t per_block = (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16, C>(lg);
     return per_block <= kRingSmemMax ? lg : 0;
 }
 
 template <int C, bool S16>
 cudaError_t launch_warp(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int blocks)
 {
-    const int lg = ring_log2_for<S16>(P);
-    const size_t smem = lg ? (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16>(lg) : 0;
+    const int lg = ring_log2_for<S16, C>(P);
+    const size_t smem = lg ? (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16, C>(lg) : 0;
     k_warp<C, S16><<<blocks, kWarpKernelThreads, smem, st>>>(B, P, W, cls, lg);
+    return cudaGetLastError();
+}
+
+// One class kernel: the per-thread kernels take the SM count, the warp
+// kernels a block count.
+using ClassLaunch = cudaError_t (*)(const Batch &, const Params &, const Work &, int, cudaStream_t, int, int,
+                                   const Plan &);
+
+template <int NMAX>
+cudaError_t cls_u8(const Batch &B, const Params &P, const Work &W, int c, cudaStream_t st, int sms, int, const Plan &L)
+{
+    return launch_u8<NMAX>(B, P, W, c, st, sms, L);
+}
+
+template <int NMAX>
+cudaError_t cls_i16(const Batch &B, const Params &P, const Work &W, int c, cudaStream_t st, int sms, int, const Plan &L)
+{
+    return launch_inter<NMAX, false>(B, P, W, c, st, sms, L.inter_warps);
+}
+
+cudaError_t cls_w16(const Batch &B, const Params &P, const Work &W, int c, cudaStream_t st, int, int wblocks,
+                    const Plan &L)
+{
+    if (L.warp_cols == 4) return launch_warp<4, true>(B, P, W, c, st, wblocks);
+    if (L.warp_cols == 16) return launch_warp<16, true>(B, P, W, c, st, wblocks);
+    return launch_warp<8, true>(B, P, W, c, st, wblocks);
+}
+
+cudaError_t cls_w32(const Batch &B, const Params &P, const Work &W, int c, cudaStream_t st, int, int wblocks,
+                    const Plan &)
+{
+    return launch_warp<8, false>(B, P, W, c, st, wblocks);
+}
+
+constexpr ClassLaunch kClassLaunch[kNumClass + 1] = {
+    cls_u8<256>, cls_u8<192>, cls_u8<128>, cls_u8<96>, cls_u8<64>, cls_u8<48>, cls_u8<32>, cls_u8<16>,
+    cls_i16<256>, cls_i16<128>, cls_i16<64>, cls_i16<32>, cls_w16, cls_w32, cls_w32};
+
+// Launch order of the classes in the forked path and the side stream of each:
+// the long 8-bit classes first, each stream ending with shorter work.
+constexpr int kForkOrder[kNumClass] = {0, 1, 2, 3, 4, 5, 6, 7, kClsW16, kClsW32, 8, 9, 10, 11};
+constexpr int kClassStream[kNumClass] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2};
+
+// Whether class c can hold pairs under the plan and the batch flags (classes
+// that cannot are not launched).
+bool class_live(int c, const Plan &L, uint32_t flags)
+{
+    if (c >= kClsW16) return true;
+    if (flags & BSW_FORCE_I32) return false;
+    const bool u8 = c < 8;
+    if ((flags & BSW_FORCE_I8) && !u8) return false;
+    if ((flags & BSW_FORCE_I16) && u8) return false;
+    if (L.cls.b[c] == L.cls.b[c + 1]) return false;
+    if (flags & (BSW_FORCE_I8 | BSW_FORCE_I16)) return true;
+    const int base = u8 ? kBinU8 : kBinI16;
+    const int nmin = kShortMax - (L.cls.b[c + 1] - base) + 1;   // the class's shortest query
+    return nmin <= L.short_max;
+}
+
+cudaError_t launch_class(int c, const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms, int wblocks,
+                         const Plan &L, ClassTimer *T)
+{
+    cudaError_t e;
+    if (T && (e = cudaEventRecord(T->t0[c], st)) != cudaSuccess) return e;
+    if ((e = kClassLaunch[c](B, P, W, c, st, sms, wblocks, L)) != cudaSuccess) return e;
+    if (T) {
+        if ((e = cudaEventRecord(T->t1[c], st)) != cudaSuccess) return e;
+        T->used[c] = true;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_prepass(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms, const Plan &L)
+{
+    const int cblocks = (int)((B.n + 511) / 512 < (int64_t)sms * 4 ? (B.n + 511) / 512 : (int64_t)sms * 4);
+    k_classify<<<cblocks, 512, 0, st>>>(B, P, W);
+    k_scan<<<1, 1024, 0, st>>>(W, L.cls);
+    const int sblocks = (int)((B.n + kScatterTile - 1) / kScatterTile < (int64_t)sms * 2
+                                  ? (B.n + kScatterTile - 1) / kScatterTile : (int64_t)sms * 2);
+    k_scatter<<<sblocks, kScatterThreads, 0, st>>>(B.n, W);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+bool packed_scoring_ok(const Params &P) { return inter2_scoring_ok(P); }
+
+int batched_launches(const Plan &L, uint32_t flags)
+{
+    int k = 3;   // classify, scan, scatter
+    for (int c = 0; c <= kNumClass; ++c) k += class_live(c, L, flags) ? 1 : 0;
+    return k;
+}
+
 cudaError_t prepare_kernels(int sms)
 {
     (void)sms;
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_warp<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
+        return e;
     if ((e = cudaFuncSetAttribute(k_warp<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_warp<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_warp<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
         return e;
@@ -1237,70 +1372,44 @@ cudaError_t prepare_kernels(int sms)
 
 int warp_slots_needed(int sms) { return sms * kWarpBlocksPerSM * (kWarpKernelThreads / 32); }
 
-cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const Streams &S, int sms)
+cudaError_t launch_batched(const Batch &B, const Params &P0, const Work &W, const Streams &S, int sms, const Plan &L,
+                           ClassTimer *T)
 {
     cudaError_t e;
     if (B.n <= 0) return cudaSuccess;
-    const int cblocks = (int)((B.n + 511) / 512 < (int64_t)sms * 4 ? (B.n + 511) / 512 : (int64_t)sms * 4);
-    k_classify<<<cblocks, 512, 0, S.main>>>(B, P, W);
-    k_scan<<<1, 1024, 0, S.main>>>(W);
-    const int sblocks = (int)((B.n + kScatterTile - 1) / kScatterTile < (int64_t)sms * 2 ? (B.n + kScatterTile - 1) / kScatterTile : (int64_t)sms * 2);
-    k_scatter<<<sblocks, kScatterThreads, 0, S.main>>>(B.n, W);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    Params P = P0;
+    P.short_max = L.short_max;
+    if ((e = launch_prepass(B, P, W, S.main, sms, L)) != cudaSuccess) return e;
     // Fork: classes run concurrently on the side streams so that one class's
     // tail overlaps the next class's start.
     if ((e = cudaEventRecord(S.fork, S.main)) != cudaSuccess) return e;
     for (int k = 0; k < 3; ++k)
         if ((e = cudaStreamWaitEvent(S.side[k], S.fork, 0)) != cudaSuccess) return e;
     const int wblocks = sms * kWarpBlocksPerSM;
-    if ((e = launch_inter<256, true>(B, P, W, 0, S.side[0], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<192, true>(B, P, W, 1, S.side[0], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<128>(B, P, W, 2, S.side[0], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<96>(B, P, W, 3, S.side[1], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<64>(B, P, W, 4, S.side[1], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<48>(B, P, W, 5, S.side[1], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<32>(B, P, W, 6, S.side[2], sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<16>(B, P, W, 7, S.side[2], sms)) != cudaSuccess) return e;
-    if ((e = launch_warp<8, true>(B, P, W, kClsW16, S.side[2], wblocks)) != cudaSuccess) return e;
-    if ((e = launch_warp<8, false>(B, P, W, kClsW32, S.side[2], wblocks)) != cudaSuccess) return e;
-    if ((e = launch_inter<256, false>(B, P, W, 8, S.side[2], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<128, false>(B, P, W, 9, S.side[2], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<64, false>(B, P, W, 10, S.side[2], sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<32, false>(B, P, W, 11, S.side[2], sms)) != cudaSuccess) return e;
+    for (int c : kForkOrder)
+        if (class_live(c, L, P.flags) &&
+            (e = launch_class(c, B, P, W, S.side[kClassStream[c]], sms, wblocks, L, T)) != cudaSuccess)
+            return e;
     for (int k = 0; k < 3; ++k) {
         if ((e = cudaEventRecord(S.join[k], S.side[k])) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(S.main, S.join[k], 0)) != cudaSuccess) return e;
     }
     // Section V-D1: pairs whose scores left their lane range, exactly, in 32 bits.
-    return launch_warp<8, false>(B, P, W, kRerun, S.main, wblocks);
+    return launch_class(kRerun, B, P, W, S.main, sms, wblocks, L, T);
 }
 
-cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms,
-                                  int warp_blocks)
+cudaError_t launch_batched_serial(const Batch &B, const Params &P0, const Work &W, cudaStream_t st, int sms,
+                                  int warp_blocks, const Plan &L)
 {
     cudaError_t e;
     if (B.n <= 0) return cudaSuccess;
-    const int cblocks = (int)((B.n + 511) / 512 < (int64_t)sms * 4 ? (B.n + 511) / 512 : (int64_t)sms * 4);
-    k_classify<<<cblocks, 512, 0, st>>>(B, P, W);
-    k_scan<<<1, 1024, 0, st>>>(W);
-    const int sblocks = (int)((B.n + kScatterTile - 1) / kScatterTile < (int64_t)sms * 2 ? (B.n + kScatterTile - 1) / kScatterTile : (int64_t)sms * 2);
-    k_scatter<<<sblocks, kScatterThreads, 0, st>>>(B.n, W);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_inter<256, true>(B, P, W, 0, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<192, true>(B, P, W, 1, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<128>(B, P, W, 2, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<96>(B, P, W, 3, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<64>(B, P, W, 4, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<48>(B, P, W, 5, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<32>(B, P, W, 6, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_u8<16>(B, P, W, 7, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<256, false>(B, P, W, 8, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<128, false>(B, P, W, 9, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<64, false>(B, P, W, 10, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_inter<32, false>(B, P, W, 11, st, sms)) != cudaSuccess) return e;
-    if ((e = launch_warp<8, true>(B, P, W, kClsW16, st, warp_blocks)) != cudaSuccess) return e;
-    if ((e = launch_warp<8, false>(B, P, W, kClsW32, st, warp_blocks)) != cudaSuccess) return e;
-    return launch_warp<8, false>(B, P, W, kRerun, st, warp_blocks);
+    Params P = P0;
+    P.short_max = L.short_max;
+    if ((e = launch_prepass(B, P, W, st, sms, L)) != cudaSuccess) return e;
+    for (int c = 0; c <= kNumClass; ++c)
+        if (class_live(c, L, P.flags) && (e = launch_class(c, B, P, W, st, sms, warp_blocks, L, nullptr)) != cudaSuccess)
+            return e;
+    return cudaSuccess;
 }
 
 cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms)

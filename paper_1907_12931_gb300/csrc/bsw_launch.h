@@ -10,11 +10,49 @@ namespace bsw {
 constexpr int kWarpKernelThreads = 256;
 constexpr int kWarpBlocksPerSM = 2;
 
+// Query-length upper bounds of the 8-bit (classes 0-7) and 16-bit (classes
+// 8-11) per-thread kernels.
+constexpr int kU8Nmax[8] = {256, 192, 128, 96, 64, 48, 32, 16};
+constexpr int kI16Nmax[4] = {256, 128, 64, 32};
+
 struct Streams {
     cudaStream_t main;
     cudaStream_t side[3];
     cudaEvent_t fork;
     cudaEvent_t join[3];
+};
+
+// How one batch is laid out over the kernels: which query lengths run one
+// pair per thread and which one pair per warp, the per-thread length classes
+// (bucket boundaries), two pairs per thread or one, the warp kernel's columns
+// per lane (tile width) and the per-thread kernels' warps per block.  Every
+// plan computes the same results; only the speed differs.
+struct Plan {
+    int32_t short_max;
+    ClassTable cls;
+    bool packed;
+    int32_t warp_cols;     // 4, 8 or 16
+    int32_t inter_warps;   // 1, 2 or 4
+};
+
+// u8_mask bit k enables kU8Nmax[k] as a class (bit 0 is always on), i16_mask
+// bit k enables kI16Nmax[k]; a query goes to the smallest enabled class that
+// holds it.  Returns false for values out of range.
+bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, int warp_cols, int inter_warps,
+               Plan *out);
+Plan default_plan();
+
+// Whether the scoring lets the packed two-pairs-per-thread kernel run.
+bool packed_scoring_ok(const Params &P);
+
+// Kernels one launch_batched call makes under the plan and batch flags.
+int batched_launches(const Plan &L, uint32_t flags);
+
+// Optional CUDA events around each class kernel (timing-enabled events,
+// recorded on the stream the kernel is launched on).
+struct ClassTimer {
+    cudaEvent_t t0[kNumClass + 1], t1[kNumClass + 1];
+    bool used[kNumClass + 1];
 };
 
 // Kernel attributes and occupancy; call once per device before any launch
@@ -27,13 +65,14 @@ int warp_slots_needed(int sms);
 // Length-bucketed batched path: classify + counting sort + per-class
 // persistent kernels (forked over the side streams) + 32-bit re-run.
 // W.hist must be zero on entry (k_scan leaves it zero); W.cells and W.status
-// accumulate.
-cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const Streams &S, int sms);
+// accumulate.  T (nullable) records each launched class kernel's events.
+cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const Streams &S, int sms, const Plan &L,
+                           ClassTimer *T = nullptr);
 
 // The same path on one stream (no side streams, no events); the warp-per-pair
 // kernels use warp_blocks blocks of kWarpKernelThreads threads.
 cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms,
-                                  int warp_blocks);
+                                  int warp_blocks, const Plan &L);
 
 // Baseline: one pair per warp in input order.
 cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms);

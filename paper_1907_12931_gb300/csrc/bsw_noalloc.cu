@@ -126,7 +126,7 @@ extern "C" int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int3
     W.slot_bytes_per_warp = kNaSlotBytes;
 
     Params P{sc->match, sc->mismatch, sc->o_del, sc->e_del, sc->o_ins, sc->e_ins, w, zdrop, end_bonus, b->flags,
-             kNaMaxQlen, 1u << 8, 1u << 16, 1u << 24};
+             kNaMaxQlen, 1u << 8, 1u << 16, 1u << 24, kShortMax};
     Batch B{b->n_pairs, b->q, b->q_off, b->q_len, b->t, b->t_off, b->t_len, b->h0, b->w_override, out};
     // The histogram, the cell count and the status word must start at zero;
     // the array keeps whatever the previous call left.
@@ -137,7 +137,7 @@ extern "C" int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int3
         cudaGetLastError();
         return BSW_ECUDA;
     }
-    if ((e = launch_batched_serial(B, P, W, st, s->sms, kNaWarpBlocks)) != cudaSuccess) {
+    if ((e = launch_batched_serial(B, P, W, st, s->sms, kNaWarpBlocks, default_plan())) != cudaSuccess) {
         cudaGetLastError();
         return BSW_ECUDA;
     }

@@ -1,0 +1,185 @@
+"""Execution plans, the autotuner and per-kernel timing (needs a GPU).
+
+Every plan (which kernel runs which pairs: the per-thread/warp boundary, the
+per-thread length classes, one or two pairs per thread, the warp kernel's
+columns per lane, warps per block) must give the oracle's results bit for bit;
+the autotuner only chooses among them.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_12931_gb300 import workload as W
+from test_gpu_parity import NTH, adversarial, assert_same, workload_and_oracle
+
+pytestmark = pytest.mark.gpu
+
+PLANS = [
+    {},
+    {"short_max": 64},
+    {"short_max": 64, "warp_cols": 4},
+    {"short_max": 96, "warp_cols": 16},
+    {"u8_bounds": 0x1, "i16_bounds": 0x1},
+    {"u8_bounds": 0x55, "i16_bounds": 0x5, "inter_warps": 1},
+    {"packed": 1, "inter_warps": 4},
+    {"short_max": 128, "packed": 1, "u8_bounds": 0x0, "warp_cols": 16},
+]
+
+
+@pytest.fixture(scope="module")
+def bsw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_12931_gb300 import bsw as _b
+    _b.lib()
+    return _b
+
+
+def run_plan(bsw, wl, plan, flags=0, w_override=None, device=False):
+    with bsw.Context(wl.params, 16 << 30) as ctx:
+        ctx.set_plan(bsw.make_plan(**plan))
+        hb = bsw.HostBatch(wl, w_override=w_override)
+        if not device:
+            return ctx.extend_host(hb, flags)
+        import torch
+        db = bsw.DeviceBatch(hb)
+        ctx.extend_device(db, flags)
+        ctx.sync()
+        torch.cuda.synchronize()
+        return db.out.cpu().numpy(), int(db.cells.item())
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=[str(sorted(p.items())) for p in PLANS])
+@pytest.mark.parametrize("config", [("read250", 40_000), ("long10k", 400)])
+def test_plan_parity_workloads(bsw, plan, config):
+    wl, ref, cells = workload_and_oracle(*config)
+    got, gc = run_plan(bsw, wl, plan, device=True)
+    assert_same(got, ref, "%s plan %s" % (config[0], plan))
+    assert gc == cells
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=[str(sorted(p.items())) for p in PLANS])
+def test_plan_parity_adversarial(bsw, plan):
+    """Band edges, w = 0/1/unbounded (the unbounded band leaves the shared-memory
+    ring for the global slot path), u8 bound edges, every query length class."""
+    wl, ws = adversarial()
+    wl.params = W.Params(W.Scoring(), w=100, zdrop=100, end_bonus=5)
+    ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH, w_override=ws)
+    got, gc = run_plan(bsw, wl, plan, w_override=ws)
+    assert_same(got, ref, "adversarial plan %s" % plan)
+    assert gc == int(cells.sum())
+
+
+@pytest.mark.parametrize("flag", ["BSW_FORCE_I8", "BSW_FORCE_I16", "BSW_FORCE_I32"])
+def test_forced_lanes_under_plan(bsw, flag):
+    """Forced lane widths keep every query up to 256 on the per-thread kernels
+    whatever short_max says, and saturating pairs are re-run exactly."""
+    wl, ws = adversarial()
+    wl.params = W.Params(W.Scoring(), w=100, zdrop=100, end_bonus=5)
+    ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH, w_override=ws)
+    plan = {"short_max": 64, "u8_bounds": 0x1, "i16_bounds": 0x3, "warp_cols": 4}
+    got, gc = run_plan(bsw, wl, plan, flags=getattr(bsw, flag), w_override=ws)
+    assert_same(got, ref, "adversarial %s" % flag)
+    assert gc == int(cells.sum())
+
+
+def test_set_plan_rejects_bad_fields(bsw):
+    wl, _, _ = workload_and_oracle("plain10k")
+    bad = [{"short_max": 63}, {"short_max": 257}, {"warp_cols": 5}, {"warp_cols": 32}, {"inter_warps": 3},
+           {"packed": 2}, {"u8_bounds": 0x100}, {"i16_bounds": 0x10}]
+    with bsw.Context(wl.params) as ctx:
+        before = ctx.get_plan().as_dict()
+        assert before == {"short_max": 256, "u8_bounds": 0xff, "i16_bounds": 0xf, "packed": 0, "warp_cols": 8,
+                          "inter_warps": 2, "ms": 0.0}
+        for b in bad:
+            with pytest.raises(bsw.BswError) as ei:
+                ctx.set_plan(bsw.make_plan(**b))
+            assert ei.value.code == bsw.BSW_EINVAL
+        assert ctx.get_plan().as_dict() == before
+        ctx.set_plan(bsw.make_plan(short_max=128, u8_bounds=0x0))
+        p = ctx.get_plan()
+        assert p.short_max == 128 and p.u8_bounds == 0x1   # the 256 class is always kept
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_autotune_then_parity(bsw, device):
+    wl, ref, cells = workload_and_oracle("read151", 200_000)
+    with bsw.Context(wl.params, 16 << 30) as ctx:
+        hb = bsw.HostBatch(wl)
+        if device:
+            import torch
+            db = bsw.DeviceBatch(hb)
+            p = ctx.autotune(db, sample_pairs=100_000, reps=2)
+        else:
+            p = ctx.autotune(hb, sample_pairs=100_000, reps=2)
+        assert p.ms > 0
+        q = ctx.get_plan()
+        assert q.as_dict() == p.as_dict()
+        assert 64 <= p.short_max <= 256 and p.warp_cols in (4, 8, 16) and p.inter_warps in (1, 2, 4)
+        if device:
+            ctx.extend_device(db)
+            ctx.sync()
+            torch.cuda.synchronize()
+            got, gc = db.out.cpu().numpy(), int(db.cells.item())
+        else:
+            got, gc = ctx.extend_host(hb)
+    assert_same(got, ref, "read151 after autotune (%s)" % p.as_dict())
+    assert gc == cells
+
+
+def test_autotune_long_queries(bsw):
+    wl, ref, cells = workload_and_oracle("long10k", 2000)
+    with bsw.Context(wl.params, 16 << 30) as ctx:
+        hb = bsw.HostBatch(wl)
+        p = ctx.autotune(hb, reps=1)
+        got, gc = ctx.extend_host(hb)
+    assert p.ms > 0
+    assert_same(got, ref, "long10k after autotune (%s)" % p.as_dict())
+    assert gc == cells
+
+
+def test_autotune_rejects_flags_and_empty_is_noop(bsw):
+    wl, _, _ = workload_and_oracle("plain10k")
+    with bsw.Context(wl.params) as ctx:
+        hb = bsw.HostBatch(wl)
+        rc, _ = bsw.bsw_autotune(ctx.handle, hb.struct(bsw.BSW_PLAIN_KERNEL), 0, 1)
+        assert rc == bsw.BSW_EINVAL
+        rc, p = bsw.bsw_autotune(ctx.handle, hb.struct(0), -5, 1)   # <= 0: the default sample
+        assert rc == bsw.BSW_OK and p.ms > 0
+        empty = hb.struct(0)
+        empty.n_pairs = 0
+        before = ctx.get_plan().as_dict()
+        rc, p = bsw.bsw_autotune(ctx.handle, empty, 0, 1)
+        assert rc == bsw.BSW_OK and p.as_dict() == before
+
+
+def test_kernel_times(bsw):
+    import torch
+    wl, ref, _ = workload_and_oracle("read151", 200_000)
+    with bsw.Context(wl.params, 16 << 30) as ctx:
+        rc, _ = bsw.bsw_kernel_times(ctx.handle)
+        assert rc == bsw.BSW_ESTATE                       # no timed call yet
+        db = bsw.DeviceBatch(bsw.HostBatch(wl))
+        with pytest.raises(bsw.BswError):                 # events inside a graph: refused
+            ctx.extend_device(db, bsw.BSW_TIME_KERNELS)
+        ctx.extend_device(db, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH)
+        launches, ms = ctx.kernel_times()
+        ctx.sync()
+        torch.cuda.synchronize()
+        assert_same(db.out.cpu().numpy(), ref, "timed launch")
+        assert launches == 18                              # 3 bucketing + 14 classes + re-run
+        assert ms[3] > 0 and ms[14] > 0                    # u8<96> carries most cells; re-run always launches
+        assert all(t >= 0 for t in ms)
+        # a plan with fewer classes launches fewer kernels
+        ctx.set_plan(bsw.make_plan(short_max=128, u8_bounds=0x5, i16_bounds=0x1))
+        ctx.extend_device(db, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH)
+        launches2, ms2 = ctx.kernel_times()
+        # u8<256> would hold only queries over 128 bases, which short_max 128
+        # sends to the warp kernel, so it is skipped; live: u8<128>, i16<256>,
+        # the two warp classes and the re-run
+        assert launches2 == 3 + 5
+        assert ms2[0] == 0 and ms2[1] == 0 and ms2[3] == 0 and ms2[2] > 0
+        ctx.sync()
+        torch.cuda.synchronize()
+        assert_same(db.out.cpu().numpy(), ref, "timed launch, reduced plan")
