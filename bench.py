@@ -40,6 +40,11 @@ OPS_PER_CELL = 8
 # 32-bit integer lane-operations one SM issues per clock (4 schedulers x 32 lanes).
 LANE_OPS_PER_CLK_PER_SM = 128
 METRIC = "BSW GCUPS on 1 GB300 (batched vs plain kernel, bit-exact); p50/p99 serve latency"
+# DRAM bytes read + written per launch of a workload's dominant kernel, from
+# one ncu capture of the current kernel (profiles/k_inter96_u8_read151.md);
+# other kernels and workloads report null.
+MEASURED_TRAFFIC = {("read151", "k_inter<96,u8>"): 139_303_424}
+
 U8_NMAX = (256, 192, 128, 96, 64, 48, 32, 16)
 I16_NMAX = (256, 128, 64, 32)
 
@@ -64,6 +69,8 @@ def parse():
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default plan (no autotune)")
+    ap.add_argument("--plan", default=None,
+                    help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps (no autotune)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point")
     return ap.parse_args()
 
@@ -214,14 +221,35 @@ def class_kernel(c, plan, scoring):
 
 # ------------------------------------------------------------------ arms
 
-def cpu_baseline(wl, pairs: int):
+def cpu_baseline(wl, min_s: float = 10.0, single_s: float = 4.0):
+    """The oracle on the host cores: whole-workload passes on every core until
+    min_s seconds have passed, then single-thread passes over the first pairs
+    until single_s seconds have passed.  Returns the first pass's results too."""
     import oracle
-    sample = wl.subset(np.arange(min(pairs, wl.n_pairs)))
     cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    res, cells, _ = oracle.extend_batch(sample, nthreads=cores)
-    dt = time.perf_counter() - t0
-    return sample, res, cells, dt, cores
+    res = None
+    passes, cells_all, t_all = 0, 0, 0.0
+    while t_all < min_s and passes < 50:
+        t0 = time.perf_counter()
+        r, cells, _ = oracle.extend_batch(wl, nthreads=cores)
+        t_all += time.perf_counter() - t0
+        cells_all += int(cells.sum())
+        passes += 1
+        if res is None:
+            res = r
+    n1 = min(wl.n_pairs, 50_000)
+    one = wl.subset(np.arange(n1))
+    p1, cells_1, t_1 = 0, 0, 0.0
+    while t_1 < single_s and p1 < 50:
+        t0 = time.perf_counter()
+        _, cells, _ = oracle.extend_batch(one, nthreads=1)
+        t_1 += time.perf_counter() - t0
+        cells_1 += int(cells.sum())
+        p1 += 1
+    return {"value": round(cells_all / t_all / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d pass(es) over all %d pairs on %d threads, %.1f s" % (passes, wl.n_pairs, cores, t_all),
+            "single_thread": {"value": round(cells_1 / t_1 / 1e9, 4), "unit": "GCUPS", "cores": 1,
+                              "sample": "%d pass(es) over the first %d pairs, %.1f s" % (p1, n1, t_1)}}, res
 
 
 def run_reference(args):
@@ -309,9 +337,13 @@ def run_gb300(args):
     db = bsw.DeviceBatch(hb)
     stream = torch.cuda.Stream()
     in_bytes = hb.nbytes()
-    # the execution plan: autotuned on a sample of this batch (outside the timed region)
+    # the execution plan: autotuned on this batch (outside the timed region), or given
     t_tune = time.perf_counter()
-    plan = ctx.get_plan() if args.no_tune else ctx.autotune(db, sample_pairs=wl.n_pairs)
+    if args.plan:
+        ctx.set_plan(bsw.make_plan(*[int(x, 0) for x in args.plan.split(",")]))
+        plan = ctx.get_plan()
+    else:
+        plan = ctx.get_plan() if args.no_tune else ctx.autotune(db, sample_pairs=wl.n_pairs)
     t_tune = time.perf_counter() - t_tune
 
     # batched path, timed with clocks sampled
@@ -364,6 +396,8 @@ def run_gb300(args):
     f_mhz = clk["sm_mhz"] or 1470.0
     achieved = dom_cells * OPS_PER_CELL / (ms_dom * 1e-3) / 1e12
     peak = sms * f_mhz * 1e6 * LANE_OPS_PER_CLK_PER_SM / 1e12
+    dom_kernel = class_kernel(dom, plan, wl.params.scoring)
+    traffic = MEASURED_TRAFFIC.get((args.config, dom_kernel)) if args.pairs is None else None
 
     # end to end through the C ABI with pinned host buffers
     hbp = pinned_host_batch(bsw, bsw.HostBatch(wl))
@@ -383,15 +417,13 @@ def run_gb300(args):
     h2d = qb + tb + n * (8 + 4 + 8 + 4 + 4)
     d2h = n * 24 + 8 + 4
 
-    # CPU baseline (rank 0): the oracle on a bounded sample, also a parity spot check
+    # CPU baseline (rank 0): the oracle on the host cores, also a parity check of every pair
     cpu = None
     parity = None
     if rank == 0 and not args.no_cpu:
-        sample, res, scells, dt, cores = cpu_baseline(wl, 400_000)
-        cpu = {"value": round(int(scells.sum()) / dt / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
-               "sample": "first %d of %d pairs (%.2f s on %d threads)" % (sample.n_pairs, n, dt, cores)}
-        mism = int((res != out_batched[: sample.n_pairs]).any(axis=1).sum())
-        parity = {"pairs_checked": sample.n_pairs, "fields": 6, "mismatches": mism}
+        cpu, res = cpu_baseline(wl)
+        mism = int((res != out_batched).any(axis=1).sum())
+        parity = {"pairs_checked": int(res.shape[0]), "fields": 6, "mismatches": mism}
 
     if rank == 0:
         line = {
@@ -409,11 +441,11 @@ def run_gb300(args):
             "two_pairs_per_thread": {"value": round(gcups_packed, 3), "unit": "GCUPS", "ms_per_step": round(ms_packed, 4),
                                      "bit_exact_vs_batched": packed_equal},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "dram_gbs": round(traffic / (ms_dom * 1e-3) / 1e9, 1) if traffic else None,
                          "kernel": "%s (batch of its own class: %d pairs, %d cells; CUDA events around the "
                                    "kernel on its stream, mean of %d launches)"
-                                   % (class_kernel(dom, plan, wl.params.scoring), sub.n_pairs, dom_cells,
-                                      len(dom_ms)),
+                                   % (dom_kernel, sub.n_pairs, dom_cells, len(dom_ms)),
                          "launch_ms": round(ms_dom, 4),
                          "ops_per_cell": OPS_PER_CELL,
                          "peak_basis": "%d SMs x %.0f MHz (median under load) x %d lane-ops/clk"
@@ -425,7 +457,7 @@ def run_gb300(args):
             "gpu_launches": launches_per_step * args.steps,
             "kernels_per_step": launches_per_step,
             "class_ms_in_step": {bsw.CLASS_NAMES[c]: round(t, 4) for c, t in enumerate(step_class_ms) if t > 0},
-            "plan": dict(plan.as_dict(), tuned=not args.no_tune, tune_s=round(t_tune, 2)),
+            "plan": dict(plan.as_dict(), tuned=not (args.no_tune or args.plan), tune_s=round(t_tune, 2)),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"]},
             "peaks_file": {k: measured_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},

@@ -270,8 +270,11 @@ int bsw_set_plan(bsw_ctx_t *ctx, const bsw_plan_t *plan);
  * coordinate descent from the default plan: short_max (256, 192, 128, 96,
  * 64), warp_cols (8, 4, 16), packed, inter_warps (2, 1, 4), then each class
  * boundary removed in turn (8-bit from 192 down, then 16-bit); a change is
- * kept when it is at least 1% faster than the best so far.  The fastest plan
- * becomes the context's plan and is written to *chosen (nullable).
+ * kept when it is at least 1% faster than the best so far.  A knob that only
+ * affects classes holding no pair of the sample is not tried, and the
+ * boundary of a class holding no pair of the sample is removed untimed.  The
+ * fastest plan becomes the context's plan and is written to *chosen
+ * (nullable), with its time measured again.
  *
  * batch: host pointers, or device pointers with BSW_DEVICE_PTRS (other flags
  * are rejected); the sample's results are computed and discarded.  The call

@@ -919,8 +919,8 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
 
     // One candidate: a warm-up launch, then the fastest of reps, timed with
     // events on the lane's stream (the batched path joins its side streams
-    // back into it).
-    auto time_plan = [&](const bsw_plan_t &k, float *ms) -> int {
+    // back into it).  counts receives the pairs each class held.
+    auto time_plan = [&](const bsw_plan_t &k, float *ms, int32_t *counts) -> int {
         Plan L;
         if (!make_plan(k.short_max, k.u8_bounds, k.i16_bounds, k.packed != 0, k.warp_cols, k.inter_warps, &L))
             return BSW_EINVAL;
@@ -944,19 +944,27 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         cudaError_t e = cudaMemcpy(ctx->h_status, W.status, 4, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_rc(e);
         if (*ctx->h_status) return BSW_EINVAL;
+        if ((e = cudaMemcpy(counts, W.cls_count, 4 * (kNumClass + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_rc(e);
         *ms = best;
         return BSW_OK;
     };
 
+    // Coordinate descent.  Knobs that only affect classes the sample leaves
+    // empty are not timed (their differences would be noise), and the
+    // boundary of a class the sample leaves empty is removed outright (one
+    // launch fewer, the same work).
     bsw_plan_t best{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0.0f};
     float tbest = 0.0f;
-    if ((rc = time_plan(best, &tbest)) != BSW_OK) return rc;
+    int32_t cnt[kNumClass + 1], cnt_best[kNumClass + 1];
+    if ((rc = time_plan(best, &tbest, cnt_best)) != BSW_OK) return rc;
     auto consider = [&](const bsw_plan_t &k) -> int {
         float t = 0.0f;
-        const int r = time_plan(k, &t);
+        const int r = time_plan(k, &t, cnt);
         if (r == BSW_OK && t < 0.99f * tbest) {
             best = k;
             tbest = t;
+            std::memcpy(cnt_best, cnt, sizeof(cnt));
         }
         return r;
     };
@@ -965,31 +973,51 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         k.short_max = sm;
         if ((rc = consider(k)) != BSW_OK) return rc;
     }
-    for (int cols : {4, 16}) {
-        bsw_plan_t k = best;
-        k.warp_cols = cols;
-        if ((rc = consider(k)) != BSW_OK) return rc;
-    }
-    if (can_pack) {
+    auto any = [&](int c0, int c1) {   // classes [c0, c1) hold pairs under the best plan
+        for (int c = c0; c < c1; ++c)
+            if (cnt_best[c] > 0) return true;
+        return false;
+    };
+    if (any(kClsW16, kClsW16 + 1))
+        for (int cols : {4, 16}) {
+            bsw_plan_t k = best;
+            k.warp_cols = cols;
+            if ((rc = consider(k)) != BSW_OK) return rc;
+        }
+    if (can_pack && any(2, 8)) {       // the 8-bit classes of bound 128 and below
         bsw_plan_t k = best;
         k.packed = 1;
         if ((rc = consider(k)) != BSW_OK) return rc;
     }
-    for (int wp : {1, 4}) {
-        bsw_plan_t k = best;
-        k.inter_warps = wp;
-        if ((rc = consider(k)) != BSW_OK) return rc;
-    }
+    if (any(0, kClsW16))
+        for (int wp : {1, 4}) {
+            bsw_plan_t k = best;
+            k.inter_warps = wp;
+            if ((rc = consider(k)) != BSW_OK) return rc;
+        }
+    // Class boundaries: removing boundary c moves class c's pairs into the
+    // next larger kept class.
     for (int bit = 1; bit < 8; ++bit) {
+        if (!((best.u8_bounds >> bit) & 1u)) continue;
         bsw_plan_t k = best;
         k.u8_bounds &= ~(1u << bit);
+        if (cnt_best[bit] == 0) {
+            best = k;
+            continue;
+        }
         if ((rc = consider(k)) != BSW_OK) return rc;
     }
     for (int bit = 1; bit < 4; ++bit) {
+        if (!((best.i16_bounds >> bit) & 1u)) continue;
         bsw_plan_t k = best;
         k.i16_bounds &= ~(1u << bit);
+        if (cnt_best[8 + bit] == 0) {
+            best = k;
+            continue;
+        }
         if ((rc = consider(k)) != BSW_OK) return rc;
     }
+    if ((rc = time_plan(best, &tbest, cnt)) != BSW_OK) return rc;
     make_plan(best.short_max, best.u8_bounds, best.i16_bounds, best.packed != 0, best.warp_cols, best.inter_warps,
               &ctx->plan);
     best.ms = tbest;

@@ -187,14 +187,18 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(int64_t n, Work W)
 // Slot word layouts (32 bits per column, column j of lane L at S[j*32 + L]):
 //   8-bit lanes : bits 0-15 a byte-permute selector for the query base q
 //                 (q*0x1111 | 0x8880 picks byte q of the row's score profile
-//                 and sign-extends it), bits 16-23 H, bits 24-31 E.
+//                 and sign-extends it), bits 16-23 E, bits 24-31 H.  E is
+//                 read with a byte load of the lane's own word and E, H are
+//                 written back with one 16-bit store (shared-memory pipe)
+//                 instead of masks and permutes (integer pipe).
 //   16-bit lanes: bits 0-14 H, bits 15-29 E, bits 30-31 q.
 template <bool U8>
 __device__ __forceinline__ uint32_t slot_init(int q, int h)
 {
-    return U8 ? ((uint32_t)q * 0x1111u | 0x8880u | ((uint32_t)h << 16)) : ((uint32_t)h | ((uint32_t)q << 30));
+    return U8 ? ((uint32_t)q * 0x1111u | 0x8880u | ((uint32_t)h << 24)) : ((uint32_t)h | ((uint32_t)q << 30));
 }
 
+// Whether a slot word holds a nonzero H or E.
 template <bool U8>
 __device__ __forceinline__ bool slot_nonzero(uint32_t w)
 {
@@ -247,44 +251,48 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
         hi = min(min(hi, i + wb + 1), n);
         // Eq. 3, first column, while the band still touches it.
         int hl = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
-        int f = 0, key = 0;   // key = H*512 + j: its max is the row max, ties to larger j
+        int f = 0, key = 0;   // key = H*256 + j (j < 256): its max is the row max, ties to larger j
         if (U8) {
             const uint32_t prof = mis4 ^ (flip << (8 * tb));   // byte c: score of (t_i, c)
-            const uint32_t k8 = P.k8, k16 = P.k16, k24 = P.k24;
+            const uint32_t k8 = P.k8;
+            // E is loaded as a byte before the word: a byte load issued after
+            // the word load would be folded into a shift and mask of the word
+            // (integer pipe); issued first it stays a shared-memory load.
+            const uint8_t *SE = reinterpret_cast<const uint8_t *>(S) + 2;     // E byte of column 0's word
+            uint16_t *SEH = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(S) + 2);   // E | H << 8
             if (oe_del == oe_ins && e_del == e_ins) {
 #pragma unroll 4
                 for (int j = lo; j < hi; ++j) {
+                    const int e = SE[j * 128];                                 // E(i, j)
                     const uint32_t wv = S[j * 32];
                     const int sc = (int)prmt(prof, 0u, wv);
-                    const int d = (int)prmt(wv, 0u, 0x4442u);                  // H(i-1, j-1)
+                    const int d = (int)(wv >> 24);                             // H(i-1, j-1)
                     const int M = __viaddmin_s32(d, sc, (int)((uint32_t)d * k8));   // d > 0 ? d + sc : <= 0
-                    const int e = (int)(wv >> 24);                             // E(i, j)
                     const int h = __vimax3_s32(M, e, f);                       // Eq. 2
-                    key = max(key, h * 512 + j);
+                    key = max(key, (int)((uint32_t)h * k8) + j);
                     const int t = M - oe_del;
                     const int e2 = __viaddmax_s32_relu(e, -e_del, t);          // E(i+1, j)
                     f = __viaddmax_s32_relu(f, -e_ins, t);                     // F(i, j+1)
-                    S[j * 32] = (uint32_t)e2 * k24 + ((uint32_t)hl * k16 + (wv & 0xffffu));
+                    SEH[j * 64] = (uint16_t)((uint32_t)hl * k8 + (uint32_t)e2);   // H(i, j-1), E(i+1, j)
                     hl = h;
                 }
             } else {
 #pragma unroll 4
                 for (int j = lo; j < hi; ++j) {
+                    const int e = SE[j * 128];
                     const uint32_t wv = S[j * 32];
                     const int sc = (int)prmt(prof, 0u, wv);
-                    const int d = (int)prmt(wv, 0u, 0x4442u);
+                    const int d = (int)(wv >> 24);
                     const int M = __viaddmin_s32(d, sc, (int)((uint32_t)d * k8));
-                    const int e = (int)(wv >> 24);
                     const int h = __vimax3_s32(M, e, f);
-                    key = max(key, h * 512 + j);
+                    key = max(key, (int)((uint32_t)h * k8) + j);
                     const int e2 = __viaddmax_s32_relu(e, -e_del, M - oe_del);
                     f = __viaddmax_s32_relu(f, -e_ins, M - oe_ins);
-                    S[j * 32] = (uint32_t)e2 * k24 + ((uint32_t)hl * k16 + (wv & 0xffffu));
+                    SEH[j * 64] = (uint16_t)((uint32_t)hl * k8 + (uint32_t)e2);
                     hl = h;
                 }
             }
-            const uint32_t wh = S[hi * 32];
-            S[hi * 32] = (wh & 0xffffu) | ((uint32_t)(hl & 0xff) << 16);
+            SEH[hi * 64] = (uint16_t)((uint32_t)(hl & 0xff) * k8);   // H(i, hi-1), E = 0
         } else {
             const int a = P.a, mb = -P.b;
 #pragma unroll 4
@@ -304,7 +312,7 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
             const uint32_t wh = S[hi * 32];
             S[hi * 32] = (wh & 0xc0000000u) | (uint32_t)(hl & 0x7fff);
         }
-        const int rm = key >> 9, rj = key & 511;
+        const int rm = U8 ? key >> 8 : key >> 9, rj = U8 ? key & 255 : key & 511;
         if (rm > VMAX) {                                   // Section V-D1: widen and redo
             W.rerun[atomicAdd(&W.cls_count[kRerun], 1)] = p;
             return 0;
@@ -1153,7 +1161,7 @@ int g_inter_blocks[12][3];
 
 int warps_index(int warps) { return warps <= 1 ? 0 : warps == 2 ? 1 : 2; }
 
-template <int NMAX> size_t inter_smem(int warps) { return (size_t)warps * (NMAX + 1) * 32 * 4; }
+template <int NMAX, bool U8> size_t inter_smem(int warps) { return (size_t)warps * (NMAX + 1) * 32 * 4; }
 template <int NMAX, bool U8> constexpr int inter_index()
 {
     return U8 ? (NMAX >= 256 ? 0 : NMAX >= 192 ? 1 : NMAX >= 128 ? 2 : NMAX >= 96 ? 3 : NMAX >= 64 ? 4 : NMAX >= 48 ? 5
@@ -1165,12 +1173,12 @@ template <int NMAX, bool U8>
 cudaError_t prepare_inter()
 {
     cudaError_t e = cudaFuncSetAttribute(k_inter<NMAX, U8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)inter_smem<NMAX>(4));
+                                         (int)inter_smem<NMAX, U8>(4));
     if (e != cudaSuccess) return e;
     for (int wi = 0; wi < 3; ++wi) {
         const int warps = 1 << wi;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inter<NMAX, U8>, warps * 32, inter_smem<NMAX>(warps));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inter<NMAX, U8>, warps * 32, inter_smem<NMAX, U8>(warps));
         if (e != cudaSuccess) return e;
         g_inter_blocks[inter_index<NMAX, U8>()][wi] = nb > 0 ? nb : 1;
     }
@@ -1181,7 +1189,7 @@ template <int NMAX, bool U8>
 cudaError_t launch_inter(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms, int warps)
 {
     const int blocks = sms * g_inter_blocks[inter_index<NMAX, U8>()][warps_index(warps)];
-    k_inter<NMAX, U8><<<blocks, warps * 32, inter_smem<NMAX>(warps), st>>>(B, P, W, cls);
+    k_inter<NMAX, U8><<<blocks, warps * 32, inter_smem<NMAX, U8>(warps), st>>>(B, P, W, cls);
     return cudaGetLastError();
 }
 

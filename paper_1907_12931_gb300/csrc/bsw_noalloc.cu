@@ -130,20 +130,18 @@ extern "C" int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int3
     Batch B{b->n_pairs, b->q, b->q_off, b->q_len, b->t, b->t_off, b->t_len, b->h0, b->w_override, out};
     // The histogram, the cell count and the status word must start at zero;
     // the array keeps whatever the previous call left.
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(W.hist, 0, 4 * kNumBins, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(W.cells, 0, 8, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(W.status, 0, 4, st)) != cudaSuccess) {
+    if (cudaMemsetAsync(W.hist, 0, 4 * kNumBins, st) != cudaSuccess || cudaMemsetAsync(W.cells, 0, 8, st) != cudaSuccess ||
+        cudaMemsetAsync(W.status, 0, 4, st) != cudaSuccess) {
         cudaGetLastError();
         return BSW_ECUDA;
     }
-    if ((e = launch_batched_serial(B, P, W, st, s->sms, kNaWarpBlocks, default_plan())) != cudaSuccess) {
+    if (launch_batched_serial(B, P, W, st, s->sms, kNaWarpBlocks, default_plan()) != cudaSuccess) {
         cudaGetLastError();
         return BSW_ECUDA;
     }
     uint32_t status = 0;
-    if ((e = cudaMemcpyAsync(&status, W.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+    if (cudaMemcpyAsync(&status, W.status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return BSW_ECUDA;
     }

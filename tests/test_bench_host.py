@@ -1,0 +1,65 @@
+"""Host logic of bench.py (no GPU): the class mapping it uses to isolate the
+dominant kernel, and the CPU-baseline record."""
+import itertools
+
+import numpy as np
+
+import bench
+from paper_1907_12931_gb300 import workload as W
+
+
+class _Plan:
+    def __init__(self, short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8):
+        self.short_max, self.u8_bounds, self.i16_bounds = short_max, u8_bounds, i16_bounds
+        self.packed, self.warp_cols = packed, warp_cols
+
+
+def _class_one(n, m, h0, match, plan):
+    """One pair, written out from the plan's definition in include/bsw.h."""
+    if n <= 0 or m <= 0:
+        return -1
+    bound = h0 + match * min(n, m)
+    if n > plan.short_max:
+        return 12 if bound <= 32767 else 13
+    if bound <= 255:
+        kept = [k for k in range(8) if k == 0 or (plan.u8_bounds >> k) & 1]
+        return max((k for k in kept if bench.U8_NMAX[k] >= n), key=lambda k: k)
+    if bound <= 32767:
+        kept = [k for k in range(4) if k == 0 or (plan.i16_bounds >> k) & 1]
+        return 8 + max(k for k in kept if bench.I16_NMAX[k] >= n)
+    return 13
+
+
+def test_class_of_matches_definition():
+    rng = np.random.default_rng(7)
+    n = np.concatenate([np.arange(0, 300), rng.integers(0, 20000, 500)])
+    m = rng.integers(0, 400, n.shape[0])
+    m[::7] = 0
+    h0 = rng.integers(0, 300, n.shape[0])
+    h0[::11] = 40000
+    plans = [_Plan(), _Plan(short_max=64), _Plan(short_max=128, u8_bounds=0x5, i16_bounds=0x1),
+             _Plan(u8_bounds=0x0, i16_bounds=0x0), _Plan(short_max=192, u8_bounds=0xa3, i16_bounds=0xb)]
+    for plan, match in itertools.product(plans, (1, 2)):
+        got = bench.class_of(n, m, h0, match, plan)
+        want = [_class_one(int(a), int(b), int(c), match, plan) for a, b, c in zip(n, m, h0)]
+        np.testing.assert_array_equal(got, want)
+
+
+def test_class_kernel_names():
+    sc = W.Scoring()
+    assert bench.class_kernel(3, _Plan(), sc) == "k_inter<96,u8>"
+    assert bench.class_kernel(3, _Plan(packed=1), sc) == "k_inter2<128>"
+    assert bench.class_kernel(0, _Plan(packed=1), sc) == "k_inter<256,u8>"
+    assert bench.class_kernel(9, _Plan(), sc) == "k_inter<128,i16>"
+    assert bench.class_kernel(12, _Plan(warp_cols=16), sc) == "k_warp<16,s16>"
+    assert bench.class_kernel(13, _Plan(), sc) == "k_warp<8,s32>"
+    # large gap costs: the packed kernel does not apply
+    assert bench.class_kernel(3, _Plan(packed=1), W.Scoring(1, 200, 100, 1, 100, 1)) == "k_inter<96,u8>"
+
+
+def test_cpu_baseline_record():
+    wl = W.make("plain10k", n_pairs=300)
+    cpu, res = bench.cpu_baseline(wl, min_s=0.05, single_s=0.02)
+    assert res.shape == (300, 6)
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] > 0
+    assert cpu["single_thread"]["cores"] == 1 and cpu["single_thread"]["value"] > 0
