@@ -9,7 +9,9 @@ bsw_stream_poll.  The peak is the throughput with every request queued at
 once; the offered load is then swept from 10% to 100% of it, and p50/p99
 latency (arrival to completion) and throughput are reported per load point.
 Every request's results are compared with the CPU oracle.  Submissions draw
-from 48 distinct requests (16 per pool, each packed once).
+from 48 distinct requests (16 per pool, each packed once).  Before the sweep
+each context's plan is autotuned on its pool (the short-read context on the
+250 bp pool, which spans both short-read length ranges).
 """
 from __future__ import annotations
 
@@ -116,6 +118,8 @@ def main(args) -> int:
     ctx_short = bsw.Context(pools[0].wl.params, 14 << 30)
     ctx_long = bsw.Context(pools[2].wl.params, 6 << 30)
     ctxs = [ctx_short, ctx_short, ctx_long]
+    plans = {"short": ctx_short.autotune(bsw.HostBatch(pools[1].wl)).as_dict(),
+             "long": ctx_long.autotune(bsw.HostBatch(pools[2].wl)).as_dict()}
     nreq = int(getattr(args, "serve_requests", 0) or 1000)
     rng = np.random.default_rng(2024)
 
@@ -155,7 +159,7 @@ def main(args) -> int:
         "config": {"workload": "serve: Poisson arrivals, requests of 1-50000 pairs from read151/read250/long10k "
                                "pools (p = 1/3 each), 20 GB budget over two contexts",
                    "requests_per_point": nreq, "peak_gcups_all_queued": round(peak_gcups, 2),
-                   "mean_cells_per_request": int(mean_cells)},
+                   "mean_cells_per_request": int(mean_cells), "plans": plans},
         "points": points, "bit_exact_mismatches": total_mism,
     }
     print(json.dumps(line), flush=True)
