@@ -872,129 +872,147 @@ __device__ __forceinline__ int ring_pos(int j, int mask)
     return r + r / C;
 }
 
+// One row chunk of the 16-bit ring kernel: lane L owns the CC columns
+// [cb + CC*L, cb + CC*L + CC) of a ring laid out for C columns per lane
+// (CC = C, C/2 or C/4: the lane's columns stay consecutive ring words).
+// Columns outside the band read empty slots (ring invariant below), so no
+// load is masked.  F entering the chunk is carry_f; the F scan across lanes is
+// a prefix max of floc + (lane+1)*CC*e_ins.  LAST: the chunk holding column
+// hi - 1; it stores columns up to and including hi (column hi's slot gets
+// H(i, hi-1) with E = 0, the row-end value) and none beyond.
+template <int C, int CC, bool LAST>
+__device__ __forceinline__ void ring16_chunk(const uint8_t *qp, int n, uint32_t tmask, uint32_t *ring, int mask,
+                                             int cb, int hi, int a, int mb, int e_del, int e_ins, int oe_del,
+                                             int oe_ins, int lane, int &carry_f, int &carry_h, int &key_l)
+{
+    const int j0 = cb + lane * CC;
+    uint32_t qbits = 0;
+    if (CC >= 4) {
+#pragma unroll
+        for (int u = 0; u < CC / 4; ++u)
+            if (j0 + 4 * u < n) qbits |= (uint32_t)__ldg(qp + (j0 >> 2) + u) << (8 * u);
+    } else if (j0 < n) {
+        qbits = (uint32_t)__ldg(qp + (j0 >> 2)) >> (2 * (j0 & 3));
+    }
+    const uint32_t x = qbits ^ tmask;
+    const uint32_t mism = (x | (x >> 1)) & 0x55555555u;   // bit 2k: query base != t_i
+    uint32_t *rp = ring + ring_pos<C>(j0, mask);
+    int M[CC], Ev[CC], Fl[CC], H[CC];
+    int floc = 0;
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        const uint32_t raw = rp[k];
+        const int d = (int)(raw & 0xffffu);                 // H(i-1, j-1)
+        Ev[k] = (int)(raw >> 16);                           // E(i, j)
+        const int sc = (mism >> (2 * k)) & 1u ? mb : a;
+        M[k] = __viaddmin_s32(d, sc, d << 16);              // d > 0 ? d + sc : <= 0
+        Fl[k] = floc;
+        floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
+    }
+    const int ce = CC * e_ins;
+    int v = floc + (lane + 1) * ce;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) v = max(v, __shfl_up_sync(kFull, v, d));
+    int vex = __shfl_up_sync(kFull, v, 1);
+    if (lane == 0) vex = carry_f;
+    int g = max(carry_f, vex) - lane * ce;                  // F entering the lane's first column
+    const int vall = __shfl_sync(kFull, v, 31);
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        const int F = max(Fl[k], g);
+        g -= e_ins;
+        const int h = __vimax3_s32(M[k], Ev[k], F);
+        H[k] = h;
+        key_l = max(key_l, h * 32768 + j0 + k);
+    }
+    int hin = __shfl_up_sync(kFull, H[CC - 1], 1);
+    if (lane == 0) hin = carry_h;
+    const int kst = LAST ? hi - j0 : CC;                    // columns j0 + k, k <= kst, are stored
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - oe_del);
+        if (!LAST || k <= kst) rp[k] = (uint32_t)hin | ((uint32_t)e2 << 16);
+        hin = H[k];
+    }
+    carry_f = max(carry_f, vall) - 32 * ce;
+    if (!LAST) carry_h = __shfl_sync(kFull, H[CC - 1], 31);
+    else if (hi == cb + 32 * CC && lane == 31) ring[ring_pos<C>(hi, mask)] = (uint32_t)H[CC - 1];
+}
+
 // The warp-per-pair extension with 16-bit slots in a shared-memory ring
-// (scores up to 32767) and C columns per lane (4, 8 or 16).  Chunks that lie
-// entirely in the band take a path without per-column predicates; the row's
-// best cell is the maximum of H * 32768 + column over the warp (ties to the
-// larger column).
+// (scores up to 32767), C columns per lane (4, 8 or 16).  Each row runs
+// chunks of 32*C columns and a last chunk of 32*C, 16*C or 8*C columns,
+// whichever is the smallest that holds the rest of the band.
+//
+// Ring invariant: at the start of a row every slot outside [lo, hi) is zero
+// (H = E = 0) unless the band will initialise it on first visit.  It holds
+// because the band only ever drops all-zero slots at the right (rule c), the
+// slots it leaves at the left are zeroed when it leaves them (rule a) or are
+// zero already (rule c), the slot at hi is zeroed at the start of the row
+// (its value, the previous row-end, is not read in this row), and the ring is
+// cleared when the pair starts.  So out-of-band lanes read empty slots: at the
+// left they compute H = E = F = 0 and store zeros, and at the right their H is
+// an F below some in-band M, strictly below the row best, and they store
+// nothing.  A ring of at least 512 slots keeps the lanes of a chunk (at most
+// 256 + 7 columns from lo) off each other's slots.
 template <int C>
 __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, int p, uint32_t *ring,
                                                int mask)
 {
     static_assert(C == 4 || C == 8 || C == 16, "columns per lane");
-    constexpr uint32_t kAll = (1u << C) - 1u;
     const int lane = threadIdx.x & 31;
     const int n = B.q_len[p], m = B.t_len[p], h0 = B.h0[p];
     const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
     const int a = P.a, mb = -P.b;
     const int e_del = P.e_del, e_ins = P.e_ins;
     const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
-    const int64_t qoff = B.q_off[p];
+    const uint8_t *qp = B.q + (B.q_off[p] >> 2);
     const uint8_t *tp = B.t + (B.t_off[p] >> 2);
+    const int words = mask + 1 + (mask + 1) / C;
+    for (int w = lane; w < words; w += 32) ring[w] = 0u;
     int hw = -1, lo = 0, hi = n;
     int best = h0, bi = -1, bj = -1, gbest = -1, gi = -1, moff = 0;
     unsigned long long ncell = 0;
     for (int i = 0; i < m; ++i) {
         const int tb = (__ldg(tp + (i >> 2)) >> (2 * (i & 3))) & 3;
         const uint32_t tmask = (uint32_t)tb * 0x55555555u;    // t_i in each 2-bit field
-        lo = max(lo, i - wb);
+        const int lo_new = max(lo, i - wb);
+        for (int c = lo + lane; c < lo_new; c += 32) ring[ring_pos<C>(c, mask)] = 0u;   // left the band
+        lo = lo_new;
         hi = min(min(hi, i + wb + 1), n);
-        if (hi - 1 > hw) {                                     // first visit of columns (hw, hi-1]
-            for (int c = hw + 1 + lane; c <= hi - 1; c += 32)
-                ring[ring_pos<C>(c, mask)] = (uint32_t)(c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins));
-            hw = hi - 1;
-            __syncwarp();
-        }
+        for (int c = hw + 1 + lane; c <= hi - 1; c += 32)     // first visit of columns (hw, hi-1]
+            ring[ring_pos<C>(c, mask)] = (uint32_t)(c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins));
+        hw = max(hw, hi - 1);
+        if (lane == 0) ring[ring_pos<C>(hi, mask)] = 0u;
+        __syncwarp();
         const int hl0 = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
         int carry_f = 0, carry_h = hl0, key_l = 0;
-        // Columns outside [lo, hi) are read as empty slots (H = E = 0): they
-        // give M <= 0 and E = 0, so F passes through them unchanged on the left
-        // (it is 0 there) and they never reach the row best on the right; only
-        // their stores are suppressed.  Every lane then counts C columns, and
-        // the F scan over lanes is a plain prefix max of floc + (lane+1)*C*e_ins.
-        const int ce = C * e_ins;
-        const int lane_ce = (lane + 1) * ce;
-        for (int cb = (lo / C) * C; lo < hi && cb < hi; cb += 32 * C) {
-            const int j0 = cb + lane * C;
-            const bool full = cb >= lo && cb + 32 * C <= hi;   // the same for the whole warp
-            const bool last = cb + 32 * C >= hi;                // the chunk holding column hi-1
-            uint32_t qbits = 0;
-#pragma unroll
-            for (int u = 0; u < C / 4; ++u)
-                if (j0 + 4 * u < n) qbits |= (uint32_t)__ldg(B.q + ((qoff + j0) >> 2) + u) << (8 * u);
-            const uint32_t x = qbits ^ tmask;
-            const uint32_t mism = (x | (x >> 1)) & 0x55555555u; // bit 2k: query base != t_i
-            // j0 is a multiple of C and the ring a multiple of C long, so the
-            // lane's C columns are C consecutive ring words.
-            uint32_t *rp = ring + ring_pos<C>(j0, mask);
-            const int kl = min(max(lo - j0, 0), C), kh = min(max(hi - j0, 0), C);
-            const uint32_t am = full ? kAll : (((1u << kh) - 1u) & ~((1u << kl) - 1u));
-            int M[C], Ev[C], Fl[C], H[C];
-            int floc = 0;
-#pragma unroll
-            for (int k = 0; k < C; ++k) {
-                uint32_t raw = rp[k];
-                if (!full) raw &= 0u - ((am >> k) & 1u);
-                const int d = (int)(raw & 0xffffu);
-                Ev[k] = (int)(raw >> 16);
-                const int sc = (mism >> (2 * k)) & 1u ? mb : a;
-                M[k] = __viaddmin_s32(d, sc, d << 16);        // d > 0 ? d + sc : <= 0
-                Fl[k] = floc;
-                floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
+        int cb = (lo / C) * C;
+        if (lo < hi) {
+            while (hi - cb > 32 * C) {
+                ring16_chunk<C, C, false>(qp, n, tmask, ring, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                                          lane, carry_f, carry_h, key_l);
+                cb += 32 * C;
             }
-            int v = floc + lane_ce;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) v = max(v, __shfl_up_sync(kFull, v, d));
-            int vex = __shfl_up_sync(kFull, v, 1);
-            if (lane == 0) vex = carry_f;
-            int g = max(carry_f, vex) - lane * ce;              // F entering the lane's first column
-            const int vall = __shfl_sync(kFull, v, 31);
-#pragma unroll
-            for (int k = 0; k < C; ++k) {
-                const int F = max(Fl[k], g);
-                g -= e_ins;
-                const int h = __vimax3_s32(M[k], Ev[k], F);
-                H[k] = h;
-                key_l = max(key_l, h * 32768 + j0 + k);
-            }
-            int hin = __shfl_up_sync(kFull, H[C - 1], 1);
-            if (lane == 0) hin = carry_h;
-            if (full) {
-#pragma unroll
-                for (int k = 0; k < C; ++k) {
-                    const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - oe_del);
-                    rp[k] = (uint32_t)hin | ((uint32_t)e2 << 16);
-                    hin = H[k];
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < C; ++k) {
-                    const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - oe_del);
-                    if ((am >> k) & 1u) rp[k] = (uint32_t)hin | ((uint32_t)e2 << 16);
-                    hin = H[k];
-                }
-            }
-            carry_f = max(carry_f, vall) - 32 * ce;
-            if (last) {                                          // H(i, hi-1)
-                const int owner = (hi - 1 - cb) / C, kk = (hi - 1 - cb) % C;
-                int hsel = H[0];
-#pragma unroll
-                for (int k = 1; k < C; ++k)
-                    if (k == kk) hsel = H[k];
-                carry_h = __shfl_sync(kFull, hsel, owner);
-            } else {
-                carry_h = __shfl_sync(kFull, H[C - 1], 31);
-            }
+            if (hi - cb > 16 * C)
+                ring16_chunk<C, C, true>(qp, n, tmask, ring, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                                         lane, carry_f, carry_h, key_l);
+            else if (hi - cb > 8 * C)
+                ring16_chunk<C, C / 2, true>(qp, n, tmask, ring, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                                             lane, carry_f, carry_h, key_l);
+            else
+                ring16_chunk<C, C / 4, true>(qp, n, tmask, ring, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                                             lane, carry_f, carry_h, key_l);
+        } else if (lane == 0) {
+            ring[ring_pos<C>(hi, mask)] = (uint32_t)hl0;      // empty band: the row-end value is the first column's
         }
-        const int hl = carry_h;
         __syncwarp();
-        if (lane == 0) ring[ring_pos<C>(hi, mask)] = (uint32_t)hl;
-        hw = max(hw, hi);
-        __syncwarp();
+        hw = max(hw, hi);                                      // slot hi holds the row-end value now
         const int key = (int)__reduce_max_sync(kFull, (unsigned)key_l);
         const int rm = key >> 15, rj = key & 32767;
         if (hi > lo) ncell += (unsigned)(hi - lo);
-        if (max(lo, hi) == n) {
+        if (max(lo, hi) == n) {                                // H(i, n-1), now in slot hi
+            const int hl = (int)(ring[ring_pos<C>(hi, mask)] & 0xffffu);
             if (hl >= gbest) gi = i;
             gbest = max(gbest, hl);
         }
@@ -1027,6 +1045,9 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
     if (lane == 0) store_result(&B.out[p], best, bj + 1, bi + 1, gi + 1, gbest, moff);
     return ncell;
 }
+
+// Smallest 16-bit ring (slots): more than the 256 + 7 columns of a chunk.
+constexpr int kRing16Min = 512;
 
 // Bytes of one warp's ring: 2^lg slots, plus one padding word per C for the
 // 16-bit ring (ring_pos).
@@ -1061,7 +1082,9 @@ __global__ void __launch_bounds__(256, C >= 16 ? 1 : 2) k_warp(Batch B, Params P
         const int n = B.q_len[p];
         if (ring_log2 > 0) {
             const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
-            int need = 64;                     // at least 64 >= C: a lane's C columns are C ring words
+            // at least 2w'+3 slots; the 16-bit ring at least 512 (see
+            // warp_pair_ring16), the 32-bit one at least 64 >= 8 columns
+            int need = S16 ? kRing16Min : 64;
             while (need < 2 * wb + 3) need <<= 1;
             if (need <= (1 << ring_log2)) {
                 if (S16) cells += warp_pair_ring16<C>(B, P, p, reinterpret_cast<uint32_t *>(ring), need - 1);
@@ -1243,7 +1266,7 @@ cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, c
 template <bool S16, int C>
 int ring_log2_for(const Params &P)
 {
-    int lg = 6;
+    int lg = S16 ? 9 : 6;
     while ((1 << lg) < 2 * P.w + 3 && lg < 16) ++lg;
     const size_t per_block = (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16, C>(lg);
     return per_block <= kRingSmemMax ? lg : 0;
