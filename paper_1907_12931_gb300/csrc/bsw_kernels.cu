@@ -872,18 +872,21 @@ __device__ __forceinline__ int ring_pos(int j, int mask)
     return r + r / C;
 }
 
-// One row chunk of the 16-bit ring kernel: lane L owns the CC columns
-// [cb + CC*L, cb + CC*L + CC) of a ring laid out for C columns per lane
-// (CC = C, C/2 or C/4: the lane's columns stay consecutive ring words).
-// Columns outside the band read empty slots (ring invariant below), so no
-// load is masked.  F entering the chunk is carry_f; the F scan across lanes is
-// a prefix max of floc + (lane+1)*CC*e_ins.  LAST: the chunk holding column
-// hi - 1; it stores columns up to and including hi (column hi's slot gets
-// H(i, hi-1) with E = 0, the row-end value) and none beyond.
-template <int C, int CC, bool LAST>
-__device__ __forceinline__ void ring16_chunk(const uint8_t *qp, int n, uint32_t tmask, uint32_t *ring, int mask,
-                                             int cb, int hi, int a, int mb, int e_del, int e_ins, int oe_del,
-                                             int oe_ins, int lane, int &carry_f, int &carry_h, int &key_l)
+// One row chunk of the ring kernel: lane L owns the CC columns
+// [cb + CC*L, cb + CC*L + CC) of rings laid out for C columns per lane
+// (CC = C, C/2 or C/4: the lane's columns stay consecutive ring words).  RH
+// holds H(i-1, j-1) and RE holds E(i, j) of column j, one 32-bit word each,
+// so loads and stores need no packing.  Columns outside the band read empty
+// slots (ring invariant below), so no load is masked.  F entering the chunk
+// is carry_f; the F scan across lanes is a prefix max of
+// floc + (lane+1)*CC*e_ins.  LAST: the chunk holding column hi - 1; it stores
+// columns up to and including hi (column hi's slot gets H(i, hi-1) with E = 0,
+// the row-end value) and none beyond.  SYM: o_del = o_ins and e_del = e_ins,
+// so E and F open from the same M - o - e.
+template <int C, int CC, bool LAST, bool SYM>
+__device__ __forceinline__ void ring_chunk(const uint8_t *qp, int n, uint32_t tmask, int *RH, int *RE, int mask,
+                                           int cb, int hi, int a, int mb, int e_del, int e_ins, int oe_del,
+                                           int oe_ins, int lane, int &carry_f, int &carry_h, int &key_l)
 {
     const int j0 = cb + lane * CC;
     uint32_t qbits = 0;
@@ -896,18 +899,19 @@ __device__ __forceinline__ void ring16_chunk(const uint8_t *qp, int n, uint32_t 
     }
     const uint32_t x = qbits ^ tmask;
     const uint32_t mism = (x | (x >> 1)) & 0x55555555u;   // bit 2k: query base != t_i
-    uint32_t *rp = ring + ring_pos<C>(j0, mask);
-    int M[CC], Ev[CC], Fl[CC], H[CC];
+    const int pos = ring_pos<C>(j0, mask);
+    int *rh = RH + pos, *re = RE + pos;
+    int M[CC], T[CC], Ev[CC], Fl[CC], H[CC];
     int floc = 0;
 #pragma unroll
     for (int k = 0; k < CC; ++k) {
-        const uint32_t raw = rp[k];
-        const int d = (int)(raw & 0xffffu);                 // H(i-1, j-1)
-        Ev[k] = (int)(raw >> 16);                           // E(i, j)
+        const int d = rh[k];                                // H(i-1, j-1)
+        Ev[k] = re[k];                                      // E(i, j)
         const int sc = (mism >> (2 * k)) & 1u ? mb : a;
         M[k] = __viaddmin_s32(d, sc, d << 16);              // d > 0 ? d + sc : <= 0
+        T[k] = M[k] - oe_ins;
         Fl[k] = floc;
-        floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
+        floc = __viaddmax_s32_relu(floc, -e_ins, T[k]);
     }
     const int ce = CC * e_ins;
     int v = floc + (lane + 1) * ce;
@@ -915,12 +919,11 @@ __device__ __forceinline__ void ring16_chunk(const uint8_t *qp, int n, uint32_t 
     for (int d = 1; d < 32; d <<= 1) v = max(v, __shfl_up_sync(kFull, v, d));
     int vex = __shfl_up_sync(kFull, v, 1);
     if (lane == 0) vex = carry_f;
-    int g = max(carry_f, vex) - lane * ce;                  // F entering the lane's first column
+    const int g = max(carry_f, vex) - lane * ce;            // F entering the lane's first column
     const int vall = __shfl_sync(kFull, v, 31);
 #pragma unroll
     for (int k = 0; k < CC; ++k) {
-        const int F = max(Fl[k], g);
-        g -= e_ins;
+        const int F = __viaddmax_s32(g, -k * e_ins, Fl[k]);
         const int h = __vimax3_s32(M[k], Ev[k], F);
         H[k] = h;
         key_l = max(key_l, h * 32768 + j0 + k);
@@ -930,17 +933,26 @@ __device__ __forceinline__ void ring16_chunk(const uint8_t *qp, int n, uint32_t 
     const int kst = LAST ? hi - j0 : CC;                    // columns j0 + k, k <= kst, are stored
 #pragma unroll
     for (int k = 0; k < CC; ++k) {
-        const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - oe_del);
-        if (!LAST || k <= kst) rp[k] = (uint32_t)hin | ((uint32_t)e2 << 16);
+        const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, SYM ? T[k] : M[k] - oe_del);
+        if (!LAST || k <= kst) {
+            rh[k] = hin;
+            re[k] = e2;
+        }
         hin = H[k];
     }
     carry_f = max(carry_f, vall) - 32 * ce;
-    if (!LAST) carry_h = __shfl_sync(kFull, H[CC - 1], 31);
-    else if (hi == cb + 32 * CC && lane == 31) ring[ring_pos<C>(hi, mask)] = (uint32_t)H[CC - 1];
+    if (!LAST) {
+        carry_h = __shfl_sync(kFull, H[CC - 1], 31);
+    } else if (hi == cb + 32 * CC && lane == 31) {
+        const int ph = ring_pos<C>(hi, mask);
+        RH[ph] = H[CC - 1];
+        RE[ph] = 0;
+    }
 }
 
-// The warp-per-pair extension with 16-bit slots in a shared-memory ring
-// (scores up to 32767), C columns per lane (4, 8 or 16).  Each row runs
+// The warp-per-pair extension with its row in shared-memory rings (scores
+// up to 32767, for the row key H * 32768 + column), C columns per lane (4, 8
+// or 16).  Each row runs
 // chunks of 32*C columns and a last chunk of 32*C, 16*C or 8*C columns,
 // whichever is the smallest that holds the rest of the band.
 //
@@ -955,8 +967,8 @@ __device__ __forceinline__ void ring16_chunk(const uint8_t *qp, int n, uint32_t 
 // an F below some in-band M, strictly below the row best, and they store
 // nothing.  A ring of at least 512 slots keeps the lanes of a chunk (at most
 // 256 + 7 columns from lo) off each other's slots.
-template <int C>
-__device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, int p, uint32_t *ring,
+template <int C, bool SYM>
+__device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, int p, int *RH, int *RE,
                                                int mask)
 {
     static_assert(C == 4 || C == 8 || C == 16, "columns per lane");
@@ -969,7 +981,10 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
     const uint8_t *qp = B.q + (B.q_off[p] >> 2);
     const uint8_t *tp = B.t + (B.t_off[p] >> 2);
     const int words = mask + 1 + (mask + 1) / C;
-    for (int w = lane; w < words; w += 32) ring[w] = 0u;
+    for (int w = lane; w < words; w += 32) {
+        RH[w] = 0;
+        RE[w] = 0;
+    }
     int hw = -1, lo = 0, hi = n;
     int best = h0, bi = -1, bj = -1, gbest = -1, gi = -1, moff = 0;
     unsigned long long ncell = 0;
@@ -977,34 +992,41 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         const int tb = (__ldg(tp + (i >> 2)) >> (2 * (i & 3))) & 3;
         const uint32_t tmask = (uint32_t)tb * 0x55555555u;    // t_i in each 2-bit field
         const int lo_new = max(lo, i - wb);
-        for (int c = lo + lane; c < lo_new; c += 32) ring[ring_pos<C>(c, mask)] = 0u;   // left the band
+        for (int c = lo + lane; c < lo_new; c += 32) {           // left the band
+            RH[ring_pos<C>(c, mask)] = 0;
+            RE[ring_pos<C>(c, mask)] = 0;
+        }
         lo = lo_new;
         hi = min(min(hi, i + wb + 1), n);
         for (int c = hw + 1 + lane; c <= hi - 1; c += 32)     // first visit of columns (hw, hi-1]
-            ring[ring_pos<C>(c, mask)] = (uint32_t)(c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins));
+            RH[ring_pos<C>(c, mask)] = c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins);
         hw = max(hw, hi - 1);
-        if (lane == 0) ring[ring_pos<C>(hi, mask)] = 0u;
+        if (lane == 0) {
+            RH[ring_pos<C>(hi, mask)] = 0;
+            RE[ring_pos<C>(hi, mask)] = 0;
+        }
         __syncwarp();
         const int hl0 = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
         int carry_f = 0, carry_h = hl0, key_l = 0;
         int cb = (lo / C) * C;
         if (lo < hi) {
             while (hi - cb > 32 * C) {
-                ring16_chunk<C, C, false>(qp, n, tmask, ring, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                ring_chunk<C, C, false, SYM>(qp, n, tmask, RH, RE, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
                                           lane, carry_f, carry_h, key_l);
                 cb += 32 * C;
             }
             if (hi - cb > 16 * C)
-                ring16_chunk<C, C, true>(qp, n, tmask, ring, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                ring_chunk<C, C, true, SYM>(qp, n, tmask, RH, RE, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
                                          lane, carry_f, carry_h, key_l);
             else if (hi - cb > 8 * C)
-                ring16_chunk<C, C / 2, true>(qp, n, tmask, ring, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                ring_chunk<C, C / 2, true, SYM>(qp, n, tmask, RH, RE, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
                                              lane, carry_f, carry_h, key_l);
             else
-                ring16_chunk<C, C / 4, true>(qp, n, tmask, ring, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                ring_chunk<C, C / 4, true, SYM>(qp, n, tmask, RH, RE, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
                                              lane, carry_f, carry_h, key_l);
         } else if (lane == 0) {
-            ring[ring_pos<C>(hi, mask)] = (uint32_t)hl0;      // empty band: the row-end value is the first column's
+            RH[ring_pos<C>(hi, mask)] = hl0;                  // empty band: the row-end value is the first column's
+            RE[ring_pos<C>(hi, mask)] = 0;
         }
         __syncwarp();
         hw = max(hw, hi);                                      // slot hi holds the row-end value now
@@ -1012,7 +1034,7 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         const int rm = key >> 15, rj = key & 32767;
         if (hi > lo) ncell += (unsigned)(hi - lo);
         if (max(lo, hi) == n) {                                // H(i, n-1), now in slot hi
-            const int hl = (int)(ring[ring_pos<C>(hi, mask)] & 0xffffu);
+            const int hl = RH[ring_pos<C>(hi, mask)];
             if (hl >= gbest) gi = i;
             gbest = max(gbest, hl);
         }
@@ -1028,16 +1050,16 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         int nlo = hi;                                          // rule c with ballots
         for (int base = lo; base < hi; base += 32) {
             const int j = base + lane;
-            const uint32_t v = j < hi ? ring[ring_pos<C>(j, mask)] : 0u;
-            const unsigned bal = __ballot_sync(kFull, v != 0u);
+            const int v = j < hi ? RH[ring_pos<C>(j, mask)] | RE[ring_pos<C>(j, mask)] : 0;
+            const unsigned bal = __ballot_sync(kFull, v != 0);
             if (bal) { nlo = base + __ffs(bal) - 1; break; }
         }
         lo = nlo;
         int last = lo - 1;
         for (int top = hi; top >= lo; top -= 32) {
             const int j = top - lane;
-            const uint32_t v = j >= lo ? ring[ring_pos<C>(j, mask)] : 0u;
-            const unsigned bal = __ballot_sync(kFull, v != 0u);
+            const int v = j >= lo ? RH[ring_pos<C>(j, mask)] | RE[ring_pos<C>(j, mask)] : 0;
+            const unsigned bal = __ballot_sync(kFull, v != 0);
             if (bal) { last = top - (__ffs(bal) - 1); break; }
         }
         hi = min(last + 2, n);
@@ -1049,12 +1071,13 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
 // Smallest 16-bit ring (slots): more than the 256 + 7 columns of a chunk.
 constexpr int kRing16Min = 512;
 
-// Bytes of one warp's ring: 2^lg slots, plus one padding word per C for the
-// 16-bit ring (ring_pos).
+// Bytes of one warp's rings: for the 16-bit kernel two rings (H and E) of
+// 2^lg 32-bit slots plus one padding word per C (ring_pos), for the 32-bit one
+// 2^lg slots of 8 bytes.
 template <bool S16, int C>
 __host__ __device__ constexpr size_t ring_bytes(int lg)
 {
-    return S16 ? ((size_t)4 << lg) + ((size_t)4 << lg) / C : (size_t)8 << lg;
+    return S16 ? 2 * (((size_t)4 << lg) + ((size_t)4 << lg) / C) : (size_t)8 << lg;
 }
 
 // Persistent warp-per-pair kernel over a class list (or the re-run list).
@@ -1087,7 +1110,13 @@ __global__ void __launch_bounds__(256, C >= 16 ? 1 : 2) k_warp(Batch B, Params P
             int need = S16 ? kRing16Min : 64;
             while (need < 2 * wb + 3) need <<= 1;
             if (need <= (1 << ring_log2)) {
-                if (S16) cells += warp_pair_ring16<C>(B, P, p, reinterpret_cast<uint32_t *>(ring), need - 1);
+                if (S16) {
+                    int *RH = reinterpret_cast<int *>(ring);
+                    int *RE = RH + (ring_bytes<true, C>(ring_log2) / 8);
+                    cells += P.o_del == P.o_ins && P.e_del == P.e_ins
+                                 ? warp_pair_ring16<C, true>(B, P, p, RH, RE, need - 1)
+                                 : warp_pair_ring16<C, false>(B, P, p, RH, RE, need - 1);
+                }
                 else cells += warp_pair<C, S16, true>(B, P, p, ring, need - 1);
                 continue;
             }
