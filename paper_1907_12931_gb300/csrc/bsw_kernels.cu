@@ -862,14 +862,28 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
     return ncell;
 }
 
-// Ring position of column j with one padding word per C: lane L of a chunk
-// reads column cb + C*L + k, and (C+1)*L mod 32 is distinct for the 32 lanes
-// (C+1 is odd), so the strided accesses of a chunk hit 32 different banks.
+// Ring position of column j, one padding word per 32 slots.  Lane L of a
+// chunk with CC columns per lane (CC a power of two up to 32) reads column
+// cb + CC*L + k (cb a multiple of CC); its words are consecutive, and the 32
+// lanes' words for one k fall in 32 different banks: with L = (32/CC)*m + r
+// the word is 32*m + CC*r + m + k + const, bank CC*r + m + k + const.
 template <int C>
 __device__ __forceinline__ int ring_pos(int j, int mask)
 {
     const int r = j & mask;
-    return r + r / C;
+    return r + (r >> 5);
+}
+
+// Columns the chunks of one row cover from the first chunk's start, for a
+// span of s columns from there to hi: full chunks of 32*C, then a last chunk
+// of 32*C, 16*C or 8*C columns (the ring kernel's choice).  Nondecreasing in s.
+template <int C>
+__host__ __device__ constexpr int chunk_cover(int s)
+{
+    return s <= 0 ? 0
+         : 32 * C * ((s - 1) / (32 * C)) +
+               ((s - 32 * C * ((s - 1) / (32 * C))) > 16 * C ? 32 * C
+                : (s - 32 * C * ((s - 1) / (32 * C))) > 8 * C ? 16 * C : 8 * C);
 }
 
 // One row chunk of the ring kernel: lane L owns the CC columns
@@ -965,8 +979,9 @@ __device__ __forceinline__ void ring_chunk(const uint8_t *qp, int n, uint32_t tm
 // cleared when the pair starts.  So out-of-band lanes read empty slots: at the
 // left they compute H = E = F = 0 and store zeros, and at the right their H is
 // an F below some in-band M, strictly below the row best, and they store
-// nothing.  A ring of at least 512 slots keeps the lanes of a chunk (at most
-// 256 + 7 columns from lo) off each other's slots.
+// nothing.  The ring is sized by ring_slots, so that no out-of-band lane
+// (at most chunk_cover(2w' + C) columns from the first chunk's start) reads a
+// slot of a band column through the ring's wrap.
 template <int C, bool SYM>
 __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, int p, int *RH, int *RE,
                                                int mask)
@@ -980,7 +995,7 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
     const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
     const uint8_t *qp = B.q + (B.q_off[p] >> 2);
     const uint8_t *tp = B.t + (B.t_off[p] >> 2);
-    const int words = mask + 1 + (mask + 1) / C;
+    const int words = mask + 1 + (mask + 1) / 32;
     for (int w = lane; w < words; w += 32) {
         RH[w] = 0;
         RE[w] = 0;
@@ -1068,25 +1083,37 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
     return ncell;
 }
 
-// Smallest 16-bit ring (slots): more than the 256 + 7 columns of a chunk.
-constexpr int kRing16Min = 512;
+// Slots of the ring for band w' and C columns per lane: a power of two, at
+// least 2w' + 3 (the band spans at most 2w' + 2 slots with the row end) and
+// at least the columns a row's chunks cover for the widest span 2w' + C (so
+// out-of-band lanes, which reach that far past lo, never alias a band slot).
+template <int C>
+__host__ __device__ inline int ring_slots(int wb)
+{
+    int need = 64;
+    while (need < 2 * wb + 3 || need < chunk_cover<C>(2 * wb + C)) need <<= 1;
+    return need;
+}
 
 // Bytes of one warp's rings: for the 16-bit kernel two rings (H and E) of
-// 2^lg 32-bit slots plus one padding word per C (ring_pos), for the 32-bit one
-// 2^lg slots of 8 bytes.
+// 2^lg 32-bit slots plus one padding word per 32 (ring_pos), for the 32-bit
+// one 2^lg slots of 8 bytes.
 template <bool S16, int C>
 __host__ __device__ constexpr size_t ring_bytes(int lg)
 {
-    return S16 ? 2 * (((size_t)4 << lg) + ((size_t)4 << lg) / C) : (size_t)8 << lg;
+    return S16 ? 2 * (((size_t)4 << lg) + ((size_t)4 << lg) / 32) : (size_t)8 << lg;
 }
 
 // Persistent warp-per-pair kernel over a class list (or the re-run list).
 // ring_log2 > 0: each warp has a shared-memory slot ring of 1 << ring_log2
 // entries (dynamic shared memory); a pair whose band needs a larger ring uses
 // the warp's global slot scratch instead.  16 columns per lane need more
-// registers than two resident blocks per SM leave.
+// registers than two resident blocks of 8 warps leave: that kernel runs
+// blocks of 4 warps, 3 per SM.
+template <int C> constexpr int warp_threads() { return C >= 16 ? 128 : kWarpKernelThreads; }
+
 template <int C, bool S16>
-__global__ void __launch_bounds__(256, C >= 16 ? 1 : 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
+__global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
 {
     extern __shared__ uint8_t ring_mem[];
     const int lane = threadIdx.x & 31;
@@ -1105,9 +1132,9 @@ __global__ void __launch_bounds__(256, C >= 16 ? 1 : 2) k_warp(Batch B, Params P
         const int n = B.q_len[p];
         if (ring_log2 > 0) {
             const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
-            // at least 2w'+3 slots; the 16-bit ring at least 512 (see
-            // warp_pair_ring16), the 32-bit one at least 64 >= 8 columns
-            int need = S16 ? kRing16Min : 64;
+            // the 16-bit ring: ring_slots; the 32-bit one at least 2w'+3
+            // and 64 >= 8 columns
+            int need = S16 ? ring_slots<C>(wb) : 64;
             while (need < 2 * wb + 3) need <<= 1;
             if (need <= (1 << ring_log2)) {
                 if (S16) {
@@ -1295,9 +1322,10 @@ cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, c
 template <bool S16, int C>
 int ring_log2_for(const Params &P)
 {
-    int lg = S16 ? 9 : 6;
-    while ((1 << lg) < 2 * P.w + 3 && lg < 16) ++lg;
-    const size_t per_block = (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16, C>(lg);
+    int lg = 6;
+    const int need = S16 ? ring_slots<C>(P.w) : 2 * P.w + 3;
+    while ((1 << lg) < need && lg < 16) ++lg;
+    const size_t per_block = (size_t)(warp_threads<C>() / 32) * ring_bytes<S16, C>(lg);
     return per_block <= kRingSmemMax ? lg : 0;
 }
 
@@ -1305,8 +1333,11 @@ template <int C, bool S16>
 cudaError_t launch_warp(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int blocks)
 {
     const int lg = ring_log2_for<S16, C>(P);
-    const size_t smem = lg ? (size_t)(kWarpKernelThreads / 32) * ring_bytes<S16, C>(lg) : 0;
-    k_warp<C, S16><<<blocks, kWarpKernelThreads, smem, st>>>(B, P, W, cls, lg);
+    // blocks counts blocks of kWarpKernelThreads; the same number of warps in
+    // blocks of warp_threads<C>()
+    constexpr int tpb = warp_threads<C>();
+    const size_t smem = lg ? (size_t)(tpb / 32) * ring_bytes<S16, C>(lg) : 0;
+    k_warp<C, S16><<<blocks * (kWarpKernelThreads / tpb), tpb, smem, st>>>(B, P, W, cls, lg);
     return cudaGetLastError();
 }
 

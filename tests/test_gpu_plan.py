@@ -183,3 +183,26 @@ def test_kernel_times(bsw):
         ctx.sync()
         torch.cuda.synchronize()
         assert_same(db.out.cpu().numpy(), ref, "timed launch, reduced plan")
+
+
+@pytest.mark.parametrize("cols", [4, 8, 16])
+def test_ring_wrap_band_edges(bsw, cols):
+    """Band widths just under a power of two with full-width bands (near
+    identical sequences): the chunks' out-of-band lanes reach furthest past the
+    band there, and must never read a band column through the ring's wrap."""
+    rng = np.random.default_rng(99)
+    qs, ts, hs = [], [], []
+    for n in (700, 1100, 1600, 2300):
+        for _ in range(3):
+            ref = rng.integers(0, 4, n + 1200)
+            q = ref[:n].copy()
+            flip = rng.random(n) < 0.01
+            q[flip] = (q[flip] + 1) % 4
+            qs.append(q.astype(np.uint8)); ts.append(ref[: n + 600].astype(np.uint8)); hs.append(int(rng.integers(20, 60)))
+    wl = W.from_lists(qs, ts, hs, align=4)
+    for w in (126, 127, 254, 255, 500, 508, 510, 511):
+        wl.params = W.Params(W.Scoring(), w=w, zdrop=0, end_bonus=5)
+        ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH)
+        got, gc = run_plan(bsw, wl, {"short_max": 64, "warp_cols": cols}, device=True)
+        assert_same(got, ref, "w=%d cols=%d" % (w, cols))
+        assert gc == int(cells.sum())
