@@ -21,8 +21,13 @@ constexpr int kRerun = 14;
 constexpr int kClsW16 = 12, kClsW32 = 13;
 
 // Counting-sort bins.  Within a class the bins run from long to short queries,
-// so the persistent kernels take the longest work first.
-constexpr int kBinU8 = 0, kBinI16 = 256, kBinW16 = 512, kBinW32 = 1152, kNumBins = 1792;
+// so the persistent kernels take the longest work first.  The 8-bit bins also
+// split each query length by h0 (16 buckets of 16, largest first): a pair's
+// band starts about h0 columns wide, so 32 pairs of one bucket keep the lanes
+// of a warp on similar trip counts.
+constexpr int kU8H0Buckets = 16;
+constexpr int kBinU8 = 0, kBinI16 = 256 * kU8H0Buckets, kBinW16 = kBinI16 + 256, kBinW32 = kBinW16 + 640,
+              kNumBins = kBinW32 + 640;
 
 // Status bits written by the kernels.
 constexpr uint32_t kStInval = 1u;      // an input value is out of range

@@ -62,16 +62,17 @@ __device__ __forceinline__ void store_result(bsw_result_t *out, int score, int q
 
 // ------------------------------------------------------------------ bucketing
 
-__device__ __forceinline__ int pick_bin(int n, long long bound, uint32_t flags, int short_max)
+__device__ __forceinline__ int pick_bin(int n, long long bound, uint32_t flags, int short_max, int h0)
 {
+    const int u8 = kBinU8 + (kShortMax - n) * kU8H0Buckets + (kU8H0Buckets - 1 - min(h0 >> 4, kU8H0Buckets - 1));
     const int rank = 639 - min(n >> 6, 639);
     if (flags & BSW_FORCE_I32) return kBinW32 + rank;
     // The forced lane widths are test modes: they keep every query up to
     // kShortMax on the per-thread kernels whatever the plan says.
     if (n <= ((flags & (BSW_FORCE_I8 | BSW_FORCE_I16)) ? kShortMax : short_max)) {
-        if (flags & BSW_FORCE_I8) return kBinU8 + (kShortMax - n);
+        if (flags & BSW_FORCE_I8) return u8;
         if (flags & BSW_FORCE_I16) return kBinI16 + (kShortMax - n);
-        if (bound <= 255) return kBinU8 + (kShortMax - n);
+        if (bound <= 255) return u8;
         if (bound <= 32767) return kBinI16 + (kShortMax - n);
         return kBinW32 + rank;
     }
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
             const long long bound = (long long)h0 + (long long)P.a * min(n, m);
             if (bound >= (1ll << 30)) atomicOr(W.status, kStInval);
             else if (n > P.max_qlen) atomicOr(W.status, kStTooLong);
-            else key = pick_bin(n, bound, P.flags, P.short_max);
+            else key = pick_bin(n, bound, P.flags, P.short_max, h0);
         }
         W.key[p] = key;
         if (key >= 0) atomicAdd(&sh[key], 1u);
@@ -111,17 +112,23 @@ __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
 }
 
 // One block of 1024 threads: exclusive scan of the histogram into the scatter
-// cursors, class ranges (class c covers bins [T.b[c], T.b[c+1]); 8-bit bins
-// are 256 - n, 16-bit bins follow at 256), and a reset of the histogram and
-// work counters.
+// cursors, class ranges (class c covers bins [T.b[c], T.b[c+1])), and a reset
+// of the histogram and work counters.  Thread t scans kScanPer consecutive bins.
+constexpr int kScanPer = (kNumBins + 1023) / 1024;
+
 __global__ void __launch_bounds__(1024) k_scan(Work W, ClassTable T)
 {
     __shared__ uint32_t pre[kNumBins + 1];
     __shared__ uint32_t wsum[32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const uint32_t a = (2 * t < kNumBins) ? W.hist[2 * t] : 0u;
-    const uint32_t b = (2 * t + 1 < kNumBins) ? W.hist[2 * t + 1] : 0u;
-    const uint32_t s = a + b;
+    uint32_t v[kScanPer];
+    uint32_t s = 0;
+#pragma unroll
+    for (int u = 0; u < kScanPer; ++u) {
+        const int idx = t * kScanPer + u;
+        v[u] = idx < kNumBins ? W.hist[idx] : 0u;
+        s += v[u];
+    }
     uint32_t x = s;
     for (int d = 1; d < 32; d <<= 1) {
         uint32_t y = __shfl_up_sync(kFull, x, d);
@@ -130,17 +137,25 @@ __global__ void __launch_bounds__(1024) k_scan(Work W, ClassTable T)
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        uint32_t v = wsum[lane];
+        uint32_t w = wsum[lane];
         for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, v, d);
-            if (lane >= d) v += y;
+            uint32_t y = __shfl_up_sync(kFull, w, d);
+            if (lane >= d) w += y;
         }
-        wsum[lane] = v;
+        wsum[lane] = w;
     }
     __syncthreads();
-    const uint32_t excl = x - s + (wid ? wsum[wid - 1] : 0u);
-    if (2 * t < kNumBins) { pre[2 * t] = excl; W.cursor[2 * t] = excl; W.hist[2 * t] = 0; }
-    if (2 * t + 1 < kNumBins) { pre[2 * t + 1] = excl + a; W.cursor[2 * t + 1] = excl + a; W.hist[2 * t + 1] = 0; }
+    uint32_t run = x - s + (wid ? wsum[wid - 1] : 0u);
+#pragma unroll
+    for (int u = 0; u < kScanPer; ++u) {
+        const int idx = t * kScanPer + u;
+        if (idx < kNumBins) {
+            pre[idx] = run;
+            W.cursor[idx] = run;
+            W.hist[idx] = 0;
+        }
+        run += v[u];
+    }
     if (t == 0) pre[kNumBins] = wsum[31];
     __syncthreads();
     if (t < kNumClass) {
@@ -1213,7 +1228,8 @@ bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, 
     // larger enabled class.
     b[0] = kBinU8;
     b[8] = kBinI16;
-    for (int c = 7; c >= 1; --c) b[c] = ((u8_mask >> c) & 1u) ? kBinU8 + kShortMax - kU8Nmax[c] : b[c + 1];
+    for (int c = 7; c >= 1; --c)
+        b[c] = ((u8_mask >> c) & 1u) ? kBinU8 + (kShortMax - kU8Nmax[c]) * kU8H0Buckets : b[c + 1];
     b[kClsW16] = kBinW16;
     for (int c = 11; c >= 9; --c) b[c] = ((i16_mask >> (c - 8)) & 1u) ? kBinI16 + kShortMax - kI16Nmax[c - 8] : b[c + 1];
     b[kClsW32] = kBinW32;
@@ -1392,8 +1408,8 @@ bool class_live(int c, const Plan &L, uint32_t flags)
     if ((flags & BSW_FORCE_I16) && u8) return false;
     if (L.cls.b[c] == L.cls.b[c + 1]) return false;
     if (flags & (BSW_FORCE_I8 | BSW_FORCE_I16)) return true;
-    const int base = u8 ? kBinU8 : kBinI16;
-    const int nmin = kShortMax - (L.cls.b[c + 1] - base) + 1;   // the class's shortest query
+    const int nmin = u8 ? kShortMax - (L.cls.b[c + 1] - kBinU8) / kU8H0Buckets + 1   // the class's shortest query
+                        : kShortMax - (L.cls.b[c + 1] - kBinI16) + 1;
     return nmin <= L.short_max;
 }
 
