@@ -877,16 +877,17 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
     return ncell;
 }
 
-// Ring position of column j, one padding word per 32 slots.  Lane L of a
-// chunk with CC columns per lane (CC a power of two up to 32) reads column
-// cb + CC*L + k (cb a multiple of CC); its words are consecutive, and the 32
-// lanes' words for one k fall in 32 different banks: with L = (32/CC)*m + r
-// the word is 32*m + CC*r + m + k + const, bank CC*r + m + k + const.
+// Ring position of column j with one padding word per C: lane L of a full
+// chunk reads column cb + C*L + k (cb a multiple of C), at word
+// const + (C+1)*L + k, and C+1 is odd, so the 32 lanes hit 32 banks.  (The
+// smaller last chunks of a row, C/2 or C/4 columns per lane, see up to 2-way
+// conflicts; one pad per 32 instead would need 32-aligned chunk starts and,
+// for w' = 500, rings of twice the size.)
 template <int C>
 __device__ __forceinline__ int ring_pos(int j, int mask)
 {
     const int r = j & mask;
-    return r + (r >> 5);
+    return r + r / C;
 }
 
 // Columns the chunks of one row cover from the first chunk's start, for a
@@ -1010,7 +1011,7 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
     const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
     const uint8_t *qp = B.q + (B.q_off[p] >> 2);
     const uint8_t *tp = B.t + (B.t_off[p] >> 2);
-    const int words = mask + 1 + (mask + 1) / 32;
+    const int words = mask + 1 + (mask + 1) / C;
     for (int w = lane; w < words; w += 32) {
         RH[w] = 0;
         RE[w] = 0;
@@ -1116,7 +1117,7 @@ __host__ __device__ inline int ring_slots(int wb)
 template <bool S16, int C>
 __host__ __device__ constexpr size_t ring_bytes(int lg)
 {
-    return S16 ? 2 * (((size_t)4 << lg) + ((size_t)4 << lg) / 32) : (size_t)8 << lg;
+    return S16 ? 2 * (((size_t)4 << lg) + ((size_t)4 << lg) / C) : (size_t)8 << lg;
 }
 
 // Persistent warp-per-pair kernel over a class list (or the re-run list).
