@@ -48,6 +48,12 @@ def _load():
             lib.bswgen_fill.restype = ctypes.c_int
             lib.bswgen_random_codes.argtypes = [u64, i64, vp]
             lib.bswgen_random_codes.restype = None
+            lib.bswgen_seeds.argtypes = [u64, i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_int]
+            lib.bswgen_seeds.restype = ctypes.c_int
+            lib.bswgen_ref_copy.argtypes = [i64, i64, vp]
+            lib.bswgen_ref_copy.restype = ctypes.c_int
+            lib.bswgen_ref_len.argtypes = []
+            lib.bswgen_ref_len.restype = i64
             _lib = lib
     return _lib
 
@@ -187,3 +193,95 @@ def encode(s: str) -> np.ndarray:
     """ACGT string -> codes 0..3."""
     lut = {"A": 0, "C": 1, "G": 2, "T": 3}
     return np.array([lut[ch] for ch in s.upper()], np.uint8)
+
+
+# ------------------------------------------------------------ seeds on reads
+
+@dataclasses.dataclass
+class SeedWorkload:
+    """Reads, the reference and seeds for the extension driver.  Read r is
+    reads[read_off[r] : read_off[r] + read_len[r]]; seed k lies at read
+    positions [qbeg[k], qbeg[k] + slen[k]) of read seed_read[k] and starts at
+    reference position rbeg[k]; seeds of one read are consecutive."""
+    name: str
+    params: Params
+    reads: np.ndarray       # uint8 codes
+    read_off: np.ndarray    # int64, multiples of 4
+    read_len: np.ndarray    # int32
+    ref: np.ndarray         # uint8 codes (the whole reference)
+    seed_read: np.ndarray   # int32
+    qbeg: np.ndarray        # int32
+    slen: np.ndarray        # int32
+    rbeg: np.ndarray        # int64
+
+    @property
+    def n_seeds(self) -> int:
+        return int(self.qbeg.shape[0])
+
+    @property
+    def n_reads(self) -> int:
+        return int(self.read_len.shape[0])
+
+
+# Seed workloads: read length, reads, seeds per read, seed; scoring as above, w 100, zdrop 100.
+SEED_CONFIGS = {
+    "seeds151": dict(read_len=151, n_reads=500_000, spr=2, seed=11),
+    "seeds250": dict(read_len=250, n_reads=500_000, spr=2, seed=12),
+}
+
+_ref_cache = None
+_ref_lock = threading.Lock()
+
+
+def reference() -> np.ndarray:
+    """The 100 Mbp reference of the read workloads (codes), built once."""
+    global _ref_cache
+    lib = _load()
+    with _ref_lock:
+        if _ref_cache is None:
+            n = int(lib.bswgen_ref_len())
+            r = np.zeros(n, np.uint8)
+            if lib.bswgen_ref_copy(0, n, r.ctypes.data) != 0:
+                raise RuntimeError("bswgen_ref_copy failed")
+            _ref_cache = r
+    return _ref_cache
+
+
+def make_seeds(config: str, n_reads: int | None = None, seed: int | None = None,
+               nthreads: int | None = None) -> SeedWorkload:
+    """Generate seed workload `config` (a SEED_CONFIGS key)."""
+    c = SEED_CONFIGS[config]
+    nr = c["n_reads"] if n_reads is None else int(n_reads)
+    rl, spr = c["read_len"], c["spr"]
+    ns = nr * spr
+    reads = np.zeros(nr * rl, np.uint8)
+    s_read = np.zeros(ns, np.int32)
+    s_q = np.zeros(ns, np.int32)
+    s_l = np.zeros(ns, np.int32)
+    s_r = np.zeros(ns, np.int64)
+    nth = nthreads or min(32, os.cpu_count() or 1)
+    rc = _load().bswgen_seeds(c["seed"] if seed is None else int(seed), nr, rl, spr, reads.ctypes.data,
+                              s_read.ctypes.data, s_q.ctypes.data, s_l.ctypes.data, s_r.ctypes.data, nth)
+    if rc != 0:
+        raise RuntimeError("bswgen_seeds failed: %d" % rc)
+    read_len = np.full(nr, rl, np.int32)
+    read_off, total = layout(read_len, 4)
+    packed = np.zeros(total, np.uint8)
+    packed[np.repeat(read_off, rl) + np.tile(np.arange(rl), nr)] = reads
+    return SeedWorkload(config, Params(Scoring(), w=100, zdrop=100, end_bonus=5), packed, read_off, read_len,
+                        reference(), s_read, s_q, s_l, s_r)
+
+
+def seeds_from_lists(reads, ref, seeds, params: Params | None = None, name: str = "custom") -> SeedWorkload:
+    """A seed workload from explicit reads (code sequences), a reference (codes)
+    and seeds (read index, read start, length, reference start), the seeds of
+    one read listed together."""
+    rlen = np.array([len(r) for r in reads], np.int32)
+    roff, total = layout(rlen, 4)
+    packed = np.zeros(total, np.uint8)
+    for k, r in enumerate(reads):
+        packed[roff[k]:roff[k] + len(r)] = np.asarray(r, np.uint8)
+    sr = np.array([s[0] for s in seeds], np.int32)
+    return SeedWorkload(name, params or Params(), packed, roff, rlen, np.asarray(ref, np.uint8), sr,
+                        np.array([s[1] for s in seeds], np.int32), np.array([s[2] for s in seeds], np.int32),
+                        np.array([s[3] for s in seeds], np.int64))

@@ -315,3 +315,93 @@ void bswgen_random_codes(uint64_t seed, int64_t n, uint8_t *out)
     uint64_t s = sm_hash(seed, 0xC0DE);
     for (int64_t i = 0; i < n; ++i) out[i] = (uint8_t)uni(&s, 4);
 }
+
+/* ------------------------------------------------------ seeds on reads */
+
+/*
+ * Seed workloads for the extension driver: n_reads reads of read_len bases
+ * from the 100 Mbp reference (read_len 151: the donor / 1% substitution recipe
+ * of workload 1; otherwise the 2% divergence recipe of workload 2), each with
+ * seeds_per_read seeds of 19..min(50, read_len) bases at uniform offsets.  A
+ * seed's reference start is the reference position of its first read base
+ * (the seed is taken as ungapped from there).  Seeds of one read are listed
+ * together, in the order drawn.
+ */
+typedef struct {
+    uint64_t seed; int64_t r_beg, r_end; int32_t read_len, spr;
+    uint8_t *reads; int32_t *s_read, *s_qbeg, *s_len; int64_t *s_rbeg;
+} sjob_t;
+
+static void *seeds_range(void *arg)
+{
+    sjob_t *J = (sjob_t *)arg;
+    const uint8_t *ref = get_ref(1);
+    const int32_t rlen = J->read_len;
+    int64_t *map = (int64_t *)malloc(sizeof(int64_t) * (size_t)rlen);
+    if (!map) return NULL;
+    mut_t mu;
+    if (rlen == 151) { mu.thr_indel = 0; mu.thr_sub = ppm_thr(10000); mu.indel_max = 1; }
+    else { mu.thr_indel = ppm_thr(2000); mu.thr_sub = ppm_thr(18000); mu.indel_max = 10; }
+    const uint64_t snp_thr = ppm_thr(1000);
+    const uint64_t donor_seed = sm_hash(REF_SEED, 0xD0D0);
+    for (int64_t r = J->r_beg; r < J->r_end; ++r) {
+        uint64_t rng = sm_hash(J->seed ^ 0x5EED5EEDULL, (uint64_t)r);
+        const int64_t r0 = 400 + (int64_t)uni(&rng, (uint32_t)(REF_LEN_LARGE - 2 * (int64_t)rlen - 2000));
+        uint8_t *read = J->reads + r * rlen;
+        if (rlen == 151) {
+            for (int32_t k = 0; k < rlen; ++k) {
+                int64_t p = r0 + k;
+                uint8_t b = ref[p];
+                uint64_t hv = sm_hash(donor_seed, (uint64_t)p);
+                if (hv < snp_thr) b = (uint8_t)((b + 1 + (uint32_t)((hv >> 8) % 3)) & 3);
+                if (sm_next(&rng) < mu.thr_sub) b = (uint8_t)((b + 1 + uni(&rng, 3)) & 3);
+                read[k] = b;
+                map[k] = p;
+            }
+        } else {
+            mutate_copy(ref, REF_LEN_LARGE, r0, rlen, &rng, &mu, read, map);
+        }
+        const int32_t lmax = rlen < 50 ? rlen : 50;
+        for (int32_t k = 0; k < J->spr; ++k) {
+            const int64_t s = r * J->spr + k;
+            const int32_t L = 19 + (int32_t)uni(&rng, (uint32_t)(lmax - 19 + 1));
+            const int32_t q = (int32_t)uni(&rng, (uint32_t)(rlen - L + 1));
+            J->s_read[s] = (int32_t)r;
+            J->s_qbeg[s] = q;
+            J->s_len[s] = L;
+            J->s_rbeg[s] = map[q];
+        }
+    }
+    free(map);
+    return NULL;
+}
+
+int bswgen_seeds(uint64_t seed, int64_t n_reads, int32_t read_len, int32_t seeds_per_read, uint8_t *reads,
+                 int32_t *s_read, int32_t *s_qbeg, int32_t *s_len, int64_t *s_rbeg, int nthreads)
+{
+    if (n_reads < 0 || read_len < 19 || read_len > 10000 || seeds_per_read < 1) return -1;
+    if (!get_ref(1)) return -2;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 64) nthreads = 64;
+    if (n_reads < nthreads) nthreads = n_reads > 0 ? (int)n_reads : 1;
+    pthread_t th[64];
+    sjob_t jobs[64];
+    for (int i = 0; i < nthreads; ++i)
+        jobs[i] = (sjob_t){seed, n_reads * i / nthreads, n_reads * (i + 1) / nthreads, read_len, seeds_per_read,
+                           reads, s_read, s_qbeg, s_len, s_rbeg};
+    for (int i = 1; i < nthreads; ++i) pthread_create(&th[i], NULL, seeds_range, &jobs[i]);
+    seeds_range(&jobs[0]);
+    for (int i = 1; i < nthreads; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
+
+/* The 100 Mbp reference (codes), bases [start, start + n). */
+int bswgen_ref_copy(int64_t start, int64_t n, uint8_t *out)
+{
+    const uint8_t *ref = get_ref(1);
+    if (!ref || start < 0 || n < 0 || start + n > REF_LEN_LARGE) return -1;
+    memcpy(out, ref + start, (size_t)n);
+    return 0;
+}
+
+int64_t bswgen_ref_len(void) { return REF_LEN_LARGE; }
