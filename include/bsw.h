@@ -302,6 +302,65 @@ typedef struct {
 } bsw_timing_t;
 int bsw_kernel_times(bsw_ctx_t *ctx, bsw_timing_t *out);
 
+/*
+ * Seed-extension driver (Section V-C2: every seed of a read is extended and
+ * the results are filtered afterwards; Section V-A for each extension).
+ *
+ * bsw_set_reference uploads the reference once per context: ref_len bases,
+ * 2-bit packed as for batches (4 per byte, first base in the low bits).  The
+ * copy is charged to the context's budget and replaces any earlier one.
+ * Errors: BSW_EINVAL, BSW_EBUDGET, BSW_ENOMEM, BSW_ECUDA, BSW_ESTATE
+ * (submitted work pending).
+ */
+int bsw_set_reference(bsw_ctx_t *ctx, const uint8_t *ref, int64_t ref_len);
+
+typedef struct {
+    int32_t read_id;   /* the seed's read, 0..n_reads-1                          */
+    int32_t qbeg;      /* seed start in the read                                 */
+    int32_t len;       /* seed length: read bases [qbeg, qbeg + len)             */
+    int32_t reserved;  /* 0                                                      */
+    int64_t rbeg;      /* seed start in the reference (the seed is ungapped)     */
+} bsw_seed_t;
+
+typedef struct {
+    int32_t qb, qe;          /* aligned read interval [qb, qe)                   */
+    int64_t rb, re;          /* aligned reference interval [rb, re)              */
+    int32_t score;           /* score of the chosen ends                          */
+    int32_t w_left, w_right; /* band of each side's last run; 0: no read bases    */
+    int32_t kept;            /* 0: covered by an earlier kept seed of the read    */
+} bsw_aln_t;
+
+/*
+ * Extend every seed against the context's reference (bsw_set_reference):
+ *   1. left: the read bases before the seed, reversed, against the qbeg + w
+ *      reference bases before rbeg (fewer at the reference start), reversed,
+ *      from h0 = len * match;
+ *   2. the left end: the read start (gtle, gscore) unless gscore <= 0 or
+ *      gscore <= score - end_bonus, else the local best (qle, tle, score);
+ *      this gives (qb, rb) and the left score;
+ *   3. right: the read bases after the seed against the following
+ *      (read bases + w) reference bases, from h0 = the left score;
+ *   4. the right end as in 2, giving (qe, re) and score;
+ *   each extension whose max_off reaches (w' >> 1) + (w' >> 2) for its band
+ *   w' runs again with twice the band, up to max_band_try runs (1..8), and
+ *   the last run counts;
+ *   5. in each read's seed order, a seed whose read and reference intervals
+ *   lie inside the alignment of an earlier kept seed is not kept.
+ * The extensions use the context's scoring, w, zdrop, end_bonus and plan.
+ *
+ * Host pointers: reads 2-bit packed, read r at base offset read_off[r]
+ * (a multiple of 4) with read_len[r] bases; seeds[n_seeds] with the seeds of
+ * one read consecutive, each inside its read and the reference; out[n_seeds]
+ * (caller-owned) receives the alignments; cells_out (nullable) the DP cells
+ * of all extensions.  The call returns when out is filled.
+ * Errors: BSW_EINVAL (bad argument, a seed outside its read or the
+ * reference, a read's seeds not consecutive), BSW_ESTATE (no reference, or
+ * submitted work pending), BSW_EBUDGET, BSW_ENOMEM, BSW_ECUDA.
+ */
+int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_t *read_off,
+                     const int32_t *read_len, int64_t n_seeds, const bsw_seed_t *seeds, int32_t max_band_try,
+                     bsw_aln_t *out, int64_t *cells_out);
+
 /* Library version string. */
 const char *bsw_version(void);
 

@@ -72,6 +72,22 @@ class bsw_plan_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bsw_seed_t(ctypes.Structure):
+    _fields_ = [("read_id", ctypes.c_int32), ("qbeg", ctypes.c_int32), ("len", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rbeg", ctypes.c_int64)]
+
+
+class bsw_aln_t(ctypes.Structure):
+    _fields_ = [("qb", ctypes.c_int32), ("qe", ctypes.c_int32), ("rb", ctypes.c_int64), ("re", ctypes.c_int64),
+                ("score", ctypes.c_int32), ("w_left", ctypes.c_int32), ("w_right", ctypes.c_int32),
+                ("kept", ctypes.c_int32)]
+
+
+SEED_DTYPE = np.dtype([("read_id", "<i4"), ("qbeg", "<i4"), ("len", "<i4"), ("reserved", "<i4"), ("rbeg", "<i8")])
+ALN_DTYPE = np.dtype([("qb", "<i4"), ("qe", "<i4"), ("rb", "<i8"), ("re", "<i8"), ("score", "<i4"),
+                      ("w_left", "<i4"), ("w_right", "<i4"), ("kept", "<i4")])
+
+
 class bsw_timing_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int32), ("class_ms", ctypes.c_float * 15)]
 
@@ -120,6 +136,10 @@ def lib():
             L.bsw_autotune.restype = ctypes.c_int
             L.bsw_kernel_times.argtypes = [vp, ctypes.POINTER(bsw_timing_t)]
             L.bsw_kernel_times.restype = ctypes.c_int
+            L.bsw_set_reference.argtypes = [vp, vp, i64]
+            L.bsw_set_reference.restype = ctypes.c_int
+            L.bsw_extend_seeds.argtypes = [vp, i64, vp, vp, vp, i64, vp, i32, vp, vp]
+            L.bsw_extend_seeds.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -213,6 +233,17 @@ def bsw_kernel_times(ctx: int) -> tuple[int, bsw_timing_t]:
     t = bsw_timing_t()
     rc = lib().bsw_kernel_times(ctx, ctypes.byref(t))
     return rc, t
+
+
+def bsw_set_reference(ctx: int, ref_packed: np.ndarray, ref_len: int) -> int:
+    return lib().bsw_set_reference(ctx, ref_packed.ctypes.data, int(ref_len))
+
+
+def bsw_extend_seeds(ctx: int, n_reads: int, reads, read_off, read_len, seeds, max_band_try: int, out,
+                     cells) -> int:
+    return lib().bsw_extend_seeds(ctx, int(n_reads), reads.ctypes.data, read_off.ctypes.data, read_len.ctypes.data,
+                                  int(seeds.shape[0]), seeds.ctypes.data, int(max_band_try), out.ctypes.data,
+                                  ctypes.addressof(cells))
 
 
 def make_plan(short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8, inter_warps=2) -> bsw_plan_t:
@@ -345,6 +376,28 @@ class Context:
         if rc != BSW_OK:
             raise BswError(rc, "bsw_kernel_times")
         return t.launches, list(t.class_ms)
+
+    def set_reference(self, ref_codes: np.ndarray) -> None:
+        """Upload a reference given as codes 0..3 (packed here)."""
+        self._ref_packed = bsw_pack_2bit(ref_codes)
+        rc = bsw_set_reference(self.handle, self._ref_packed, int(ref_codes.shape[0]))
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_set_reference")
+
+    def extend_seeds(self, sw, max_band_try: int = 2):
+        """The driver over a SeedWorkload (reads as codes; the reference set
+        with set_reference).  Returns (structured alignments, cells)."""
+        reads = bsw_pack_2bit(sw.reads)
+        read_off = np.ascontiguousarray(sw.read_off, np.int64)
+        read_len = np.ascontiguousarray(sw.read_len, np.int32)
+        seeds = np.zeros(sw.n_seeds, SEED_DTYPE)
+        seeds["read_id"], seeds["qbeg"], seeds["len"], seeds["rbeg"] = sw.seed_read, sw.qbeg, sw.slen, sw.rbeg
+        out = np.zeros(sw.n_seeds, ALN_DTYPE)
+        cells = ctypes.c_int64()
+        rc = bsw_extend_seeds(self.handle, sw.n_reads, reads, read_off, read_len, seeds, max_band_try, out, cells)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_extend_seeds")
+        return out, cells.value
 
     def band_width(self, qlen: int, w: int | None = None) -> int:
         return bsw_band_width(self.handle, qlen, self.params.w if w is None else w)

@@ -293,6 +293,11 @@ struct bsw_ctx {
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
     int last_launches = 0;
 
+    // seed-extension driver: the reference (bsw_set_reference) and the
+    // buffers of a bsw_extend_seeds call
+    DevBuf refbuf, drv;
+    int64_t ref_len = -1;
+
     struct GEntry {
         bsw_batch_t b;
         void *out, *cells;
@@ -1042,6 +1047,156 @@ int bsw_kernel_times(bsw_ctx_t *ctx, bsw_timing_t *out)
     return BSW_OK;
 }
 
+int bsw_set_reference(bsw_ctx_t *ctx, const uint8_t *ref, int64_t ref_len)
+{
+    if (!ctx || ref_len < 0 || (ref_len > 0 && !ref)) return BSW_EINVAL;
+    if (!serving_idle(ctx)) return BSW_ESTATE;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+    const size_t bytes = (size_t)((ref_len + 3) / 4);
+    ctx->ref_len = -1;
+    int rc = ctx->refbuf.reserve(bytes > 0 ? bytes : 1, ctx->budget);
+    if (rc != BSW_OK) return rc;
+    if (bytes) {
+        cudaError_t e = cudaMemcpy(ctx->refbuf.p, ref, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_rc(e);
+    }
+    ctx->ref_len = ref_len;
+    return BSW_OK;
+}
+
+int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_t *read_off,
+                     const int32_t *read_len, int64_t n_seeds, const bsw_seed_t *seeds, int32_t max_band_try,
+                     bsw_aln_t *out, int64_t *cells_out)
+{
+    if (!ctx || n_reads < 0 || n_seeds < 0 || n_seeds > INT32_MAX || max_band_try < 1 || max_band_try > 8)
+        return BSW_EINVAL;
+    if (n_seeds > 0 && (!reads || !read_off || !read_len || !seeds || !out)) return BSW_EINVAL;
+    if (ctx->ref_len < 0) return BSW_ESTATE;
+    if (!serving_idle(ctx)) return BSW_ESTATE;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+    if (cells_out) *cells_out = 0;
+    if (n_seeds == 0) return BSW_OK;
+    const int w = ctx->P.w;
+    if ((int64_t)w << (max_band_try - 1) > (1 << 20)) return BSW_EINVAL;
+
+    // Host checks: reads, seeds inside their read and the reference, each
+    // read's seeds consecutive.
+    int64_t read_bytes = 0;
+    int maxrl = 0;
+    for (int64_t r = 0; r < n_reads; ++r) {
+        if (read_off[r] < 0 || (read_off[r] & 3) || read_len[r] < 0 || read_len[r] > kLongMax) return BSW_EINVAL;
+        read_bytes = std::max(read_bytes, (read_off[r] + read_len[r] + 3) / 4);
+        maxrl = std::max(maxrl, (int)read_len[r]);
+    }
+    std::vector<uint8_t> seen((size_t)n_reads, 0);
+    for (int64_t k = 0; k < n_seeds; ++k) {
+        const bsw_seed_t &sd = seeds[k];
+        if (sd.read_id < 0 || sd.read_id >= n_reads || sd.qbeg < 0 || sd.len < 0 ||
+            (int64_t)sd.qbeg + sd.len > read_len[sd.read_id] || sd.rbeg < 0 || sd.rbeg + sd.len > ctx->ref_len)
+            return BSW_EINVAL;
+        if (k == 0 || seeds[k - 1].read_id != sd.read_id) {
+            if (seen[(size_t)sd.read_id]) return BSW_EINVAL;   // the read's seeds are not consecutive
+            seen[(size_t)sd.read_id] = 1;
+        }
+        // the score bound of the right side: h0 (at most the read length
+        // times match, plus the seed) and match per base
+        if ((int64_t)ctx->P.a * (2 * (int64_t)read_len[sd.read_id] + 1) >= (1ll << 30)) return BSW_EINVAL;
+    }
+
+    // Device layout: inputs, one side's pairs, the retry batch, the alignments.
+    const int64_t N = n_seeds;
+    const int qslot = (int)align_up((size_t)std::max(maxrl, 1), 16);
+    const int tslot = (int)align_up((size_t)maxrl + (size_t)w + 4, 16);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    const size_t o_reads = take((size_t)read_bytes), o_roff = take(8 * (size_t)n_reads),
+                 o_rlen = take(4 * (size_t)n_reads), o_seeds = take(sizeof(bsw_seed_t) * (size_t)N),
+                 o_q = take((size_t)N * qslot / 4), o_t = take((size_t)N * tslot / 4), o_qoff = take(8 * (size_t)N),
+                 o_toff = take(8 * (size_t)N), o_qlen = take(4 * (size_t)N), o_tlen = take(4 * (size_t)N),
+                 o_h0 = take(4 * (size_t)N), o_wcur = take(4 * (size_t)N), o_res = take(sizeof(bsw_result_t) * (size_t)N),
+                 o_list = take(4 * (size_t)N), o_count = take(4), o_cqoff = take(8 * (size_t)N),
+                 o_ctoff = take(8 * (size_t)N), o_cqlen = take(4 * (size_t)N), o_ctlen = take(4 * (size_t)N),
+                 o_ch0 = take(4 * (size_t)N), o_cw = take(4 * (size_t)N),
+                 o_cres = take(sizeof(bsw_result_t) * (size_t)N), o_aln = take(sizeof(bsw_aln_t) * (size_t)N),
+                 o_cells = take(8 * 2 * (size_t)max_band_try);
+    Lane &lane = ctx->sync;
+    bool moved = false;
+    int rc = ctx->drv.reserve(o, ctx->budget);
+    if (rc != BSW_OK) return rc;
+    if ((rc = lane.ensure_work(N, std::max(maxrl, kShortMax), ctx->sms, ctx->budget, &moved)) != BSW_OK) return rc;
+    if (moved) clear_graphs(ctx);
+    uint8_t *d = ctx->drv.p;
+    cudaStream_t st = lane.S.main;
+    cudaError_t e;
+    const struct { size_t off; const void *src; size_t bytes; } cps[] = {
+        {o_reads, reads, (size_t)read_bytes}, {o_roff, read_off, 8 * (size_t)n_reads},
+        {o_rlen, read_len, 4 * (size_t)n_reads}, {o_seeds, seeds, sizeof(bsw_seed_t) * (size_t)N}};
+    for (const auto &cp : cps)
+        if (cp.bytes && (e = cudaMemcpyAsync(d + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+    const DriverIn D{(const bsw_seed_t *)(d + o_seeds), d + o_reads, (const int64_t *)(d + o_roff),
+                     (const int32_t *)(d + o_rlen), ctx->refbuf.p, ctx->ref_len};
+    const DriverSide S{d + o_q, d + o_t, (int64_t *)(d + o_qoff), (int64_t *)(d + o_toff), (int32_t *)(d + o_qlen),
+                       (int32_t *)(d + o_tlen), (int32_t *)(d + o_h0), (int32_t *)(d + o_wcur),
+                       (bsw_result_t *)(d + o_res), qslot, tslot};
+    const DriverCompact C{(int64_t *)(d + o_cqoff), (int64_t *)(d + o_ctoff), (int32_t *)(d + o_cqlen),
+                          (int32_t *)(d + o_ctlen), (int32_t *)(d + o_ch0), (int32_t *)(d + o_cw),
+                          (bsw_result_t *)(d + o_cres)};
+    int32_t *list = (int32_t *)(d + o_list);
+    uint32_t *count = (uint32_t *)(d + o_count);
+    bsw_aln_t *aln = (bsw_aln_t *)(d + o_aln);
+    unsigned long long *cells = (unsigned long long *)(d + o_cells);
+    int n_runs = 0;
+    bool first = true;
+    auto extend = [&](const Batch &B) -> int {
+        Work W = make_work(lane.work.p, lane.wl);
+        W.cells = cells + n_runs++;
+        cudaError_t le = enqueue_launch(ctx, lane, lane.S, B, W, 0u, first, ctx->plan);
+        first = false;
+        if (le != cudaSuccess) {
+            lane.work_dirty = true;
+            return cuda_rc(le);
+        }
+        return BSW_OK;
+    };
+    for (int side = 0; side < 2; ++side) {
+        const bool left = side == 0;
+        if ((e = launch_side(left, D, S, N, w, ctx->P.a, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+        if ((rc = extend(Batch{N, S.q, S.q_off, S.q_len, S.t, S.t_off, S.t_len, S.h0, nullptr, S.res})) != BSW_OK)
+            return rc;
+        for (int t = 1; t < max_band_try; ++t) {
+            const int wt = w << (t - 1), wnext = w << t;
+            if ((e = cudaMemsetAsync(count, 0, 4, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = launch_retry_select(S, N, wt, list, count, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+            uint32_t cnt = 0;
+            if ((e = cudaMemcpyAsync(ctx->h_status, count, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return cuda_rc(e);
+            cnt = *ctx->h_status;
+            if (cnt == 0) break;
+            if ((e = launch_retry_gather(S, list, count, cnt, wnext, C, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+            if ((rc = extend(Batch{(int64_t)cnt, S.q, C.q_off, C.q_len, S.t, C.t_off, C.t_len, C.h0, C.w, C.res})) != BSW_OK)
+                return rc;
+            if ((e = launch_retry_scatter(S, list, count, cnt, wnext, C, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+        }
+        if ((e = launch_decide(left, D, S, N, ctx->P.end_bonus, aln, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+    }
+    if ((e = launch_filter(D, N, aln, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+    std::vector<unsigned long long> hc((size_t)n_runs);
+    Work W = make_work(lane.work.p, lane.wl);
+    if ((e = cudaMemcpyAsync(out, aln, sizeof(bsw_aln_t) * (size_t)N, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hc.data(), cells, 8 * (size_t)n_runs, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(ctx->h_status, W.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_rc(e);
+    if (cells_out) {
+        unsigned long long tot = 0;
+        for (unsigned long long c : hc) tot += c;
+        *cells_out = (int64_t)tot;
+    }
+    return status_to_rc(*ctx->h_status);
+}
+
 void bsw_destroy(bsw_ctx_t *ctx)
 {
     if (!ctx) return;
@@ -1056,6 +1211,8 @@ void bsw_destroy(bsw_ctx_t *ctx)
     for (int li = 0; li < kServeLanes; ++li)
         if (ctx->lane_created[li]) ctx->serve_lane[li].destroy(ctx->budget);
     ctx->sync.destroy(ctx->budget);
+    ctx->refbuf.release(ctx->budget);
+    ctx->drv.release(ctx->budget);
     if (ctx->timer_ready)
         for (int k = 0; k <= kNumClass; ++k) {
             cudaEventDestroy(ctx->timer.t0[k]);

@@ -77,4 +77,46 @@ cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W
 // Baseline: one pair per warp in input order.
 cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms);
 
+// ---------------------------------------------------- seed-extension driver
+
+// Device inputs of bsw_extend_seeds (packed reads and reference, seeds).
+struct DriverIn {
+    const bsw_seed_t *seeds;
+    const uint8_t *reads;
+    const int64_t *read_off;
+    const int32_t *read_len;
+    const uint8_t *ref;
+    int64_t ref_len;
+};
+
+// One side's pairs: packed sequences in fixed per-seed slots of qslot/tslot
+// bases, the pair arrays of a Batch, the band of each pair's last run and
+// the results.
+struct DriverSide {
+    uint8_t *q, *t;
+    int64_t *q_off, *t_off;
+    int32_t *q_len, *t_len, *h0, *w_cur;
+    bsw_result_t *res;
+    int qslot, tslot;
+};
+
+// The compact batch of a band retry (the sequences stay in DriverSide).
+struct DriverCompact {
+    int64_t *q_off, *t_off;
+    int32_t *q_len, *t_len, *h0, *w;
+    bsw_result_t *res;
+};
+
+cudaError_t launch_side(bool left, const DriverIn &D, const DriverSide &S, int64_t n, int w, int match,
+                        cudaStream_t st, int sms);
+cudaError_t launch_retry_select(const DriverSide &S, int64_t n, int wt, int32_t *list, uint32_t *count,
+                                cudaStream_t st, int sms);
+cudaError_t launch_retry_gather(const DriverSide &S, const int32_t *list, const uint32_t *count, int64_t n_max,
+                                int wnext, const DriverCompact &C, cudaStream_t st, int sms);
+cudaError_t launch_retry_scatter(const DriverSide &S, const int32_t *list, const uint32_t *count, int64_t n_max,
+                                 int wnext, const DriverCompact &C, cudaStream_t st, int sms);
+cudaError_t launch_decide(bool left, const DriverIn &D, const DriverSide &S, int64_t n, int end_bonus,
+                          bsw_aln_t *out, cudaStream_t st, int sms);
+cudaError_t launch_filter(const DriverIn &D, int64_t n, bsw_aln_t *out, cudaStream_t st, int sms);
+
 }  // namespace bsw
