@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default plan (no autotune)")
+    ap.add_argument("--no-driver", action="store_true", help="skip the seed-extension driver leg")
     ap.add_argument("--plan", default=None,
                     help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps (no autotune)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point")
@@ -289,6 +290,45 @@ def run_reference(args):
     return 0
 
 
+def driver_leg(bsw, args):
+    """The seed-extension driver (bsw_extend_seeds) on 500 000 151 bp reads
+    with 2 seeds each, end to end through the C ABI (host inputs, the copies
+    and both extension sides inside the timed call), its parity with the
+    driver oracle on the first 5 000 reads, and the oracle's rate there."""
+    from paper_1907_12931_gb300 import workload as W
+    from oracle import driver
+    sw = W.make_seeds("seeds151")
+    ctx = bsw.Context(sw.params, mem_budget_bytes=40 << 30)
+    ctx.set_reference(sw.ref)
+    prep = ctx.prepare_seeds(sw)
+    out = np.zeros(sw.n_seeds, bsw.ALN_DTYPE)
+    ctx.extend_prepared(prep, out=out)
+    times = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        _, cells = ctx.extend_prepared(prep, out=out)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    nsub = 50_000
+    sub = W.make_seeds("seeds151", n_reads=nsub)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref = driver.extend_seeds(sub, nthreads=cores)
+    tcpu = time.perf_counter() - t0
+    k = sub.n_seeds
+    mism = int(sum((out[f][:k] != ref[f]).sum() for f in ("qb", "qe", "rb", "re", "score", "w_left", "w_right", "kept")))
+    ctx.close()
+    return {"workload": "seeds151: 500,000 151 bp reads (read151 recipe) x 2 seeds of 19-50 bp, w 100, "
+                        "2 band tries", "seeds": sw.n_seeds, "ms": round(t * 1e3, 3),
+            "seeds_per_s": round(sw.n_seeds / t, 1), "gcups": round(cells / t / 1e9, 3), "cells": cells,
+            "kept_fraction": round(float(out["kept"].mean()), 4),
+            "retried_fraction": round(float(((out["w_left"] > 100) | (out["w_right"] > 100)).mean()), 5),
+            "timing": "median of 5 calls, wall clock around the synchronous C-ABI call",
+            "parity_sample": {"seeds_checked": k, "fields": 8, "mismatches": mism},
+            "cpu_oracle": {"seeds_per_s": round(k / tcpu, 1), "cores": cores,
+                           "sample": "the first %d reads (%d seeds), %.2f s" % (nsub, k, tcpu)}}
+
+
 def pinned_host_batch(bsw, hb):
     """Copy a HostBatch's arrays into pinned host memory (for the end-to-end leg)."""
     import torch
@@ -425,6 +465,10 @@ def run_gb300(args):
         mism = int((res != out_batched).any(axis=1).sum())
         parity = {"pairs_checked": int(res.shape[0]), "fields": 6, "mismatches": mism}
 
+    drv = None
+    if rank == 0 and not args.no_driver and args.config == "read151" and args.pairs is None:
+        drv = driver_leg(bsw, args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
@@ -452,6 +496,7 @@ def run_gb300(args):
                                        % (sms, f_mhz, LANE_OPS_PER_CLK_PER_SM)},
             "cpu_baseline": cpu,
             "parity_sample": parity,
+            "extension_driver": drv,
             "e2e": {"value": round(e2e, 3), "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(t_e2e * 1e3, 3), "bit_exact_vs_device": e2e_equal},
             "gpu_launches": launches_per_step * args.steps,

@@ -384,20 +384,29 @@ class Context:
         if rc != BSW_OK:
             raise BswError(rc, "bsw_set_reference")
 
-    def extend_seeds(self, sw, max_band_try: int = 2):
-        """The driver over a SeedWorkload (reads as codes; the reference set
-        with set_reference).  Returns (structured alignments, cells)."""
-        reads = bsw_pack_2bit(sw.reads)
-        read_off = np.ascontiguousarray(sw.read_off, np.int64)
-        read_len = np.ascontiguousarray(sw.read_len, np.int32)
+    @staticmethod
+    def prepare_seeds(sw):
+        """Packed reads, offsets, lengths and seed records of a SeedWorkload."""
         seeds = np.zeros(sw.n_seeds, SEED_DTYPE)
         seeds["read_id"], seeds["qbeg"], seeds["len"], seeds["rbeg"] = sw.seed_read, sw.qbeg, sw.slen, sw.rbeg
-        out = np.zeros(sw.n_seeds, ALN_DTYPE)
+        return (sw.n_reads, bsw_pack_2bit(sw.reads), np.ascontiguousarray(sw.read_off, np.int64),
+                np.ascontiguousarray(sw.read_len, np.int32), seeds)
+
+    def extend_prepared(self, prep, max_band_try: int = 2, out=None):
+        """bsw_extend_seeds on prepare_seeds' arrays.  Returns (alignments, cells)."""
+        n_reads, reads, read_off, read_len, seeds = prep
+        if out is None:
+            out = np.zeros(seeds.shape[0], ALN_DTYPE)
         cells = ctypes.c_int64()
-        rc = bsw_extend_seeds(self.handle, sw.n_reads, reads, read_off, read_len, seeds, max_band_try, out, cells)
+        rc = bsw_extend_seeds(self.handle, n_reads, reads, read_off, read_len, seeds, max_band_try, out, cells)
         if rc != BSW_OK:
             raise BswError(rc, "bsw_extend_seeds")
         return out, cells.value
+
+    def extend_seeds(self, sw, max_band_try: int = 2):
+        """The driver over a SeedWorkload (reads as codes; the reference set
+        with set_reference).  Returns (structured alignments, cells)."""
+        return self.extend_prepared(self.prepare_seeds(sw), max_band_try)
 
     def band_width(self, qlen: int, w: int | None = None) -> int:
         return bsw_band_width(self.handle, qlen, self.params.w if w is None else w)
