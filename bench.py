@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default plan (no autotune)")
     ap.add_argument("--no-driver", action="store_true", help="skip the seed-extension driver leg")
+    ap.add_argument("--no-sal", action="store_true", help="skip the suffix-array lookup leg")
     ap.add_argument("--plan", default=None,
                     help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps (no autotune)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point")
@@ -329,6 +330,64 @@ def driver_leg(bsw, args):
                            "sample": "the first %d reads (%d seeds), %.2f s" % (nsub, k, tcpu)}}
 
 
+def sal_leg(bsw, args, stream, hbm_peak):
+    """Suffix array lookup (Eq. 1) over 8,000,000 SA intervals of a 64 Mbp
+    reference prefix: the uncompressed suffix array (256 MB, larger than L2)
+    in HBM, intervals and output on the device, timed with CUDA events on the
+    stream; bandwidth against the measured copy peak."""
+    import torch
+    from paper_1907_12931_gb300 import workload as W
+    from oracle import sal as sal_oracle
+    ref = W.reference()[:64_000_000]
+    t0 = time.perf_counter()
+    sa = bsw.bsw_sa_build(ref)
+    t_build = time.perf_counter() - t0
+    n_sa = sa.shape[0]
+    rng = np.random.default_rng(77)
+    n_int = 8_000_000
+    cnt = np.minimum(rng.geometric(0.25, n_int), 500).astype(np.int32)
+    k = rng.integers(0, n_sa - cnt, dtype=np.int64)
+    off = np.zeros(n_int, np.int64)
+    np.cumsum(cnt[:-1], out=off[1:])
+    total = int(cnt.sum())
+    ctx = bsw.Context(W.Params(), mem_budget_bytes=8 << 30)
+    ctx.sal_set_index(sa)
+    dk, dc, do = (torch.from_numpy(x).cuda() for x in (k, cnt, off))
+    out = torch.empty(total, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        ctx.sal_lookup_device(dk, dc, do, out, stream.cuda_stream)
+    stream.synchronize()
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.sal_lookup_device(dk, dc, do, out, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.sync(stream.cuda_stream)
+    got = out.cpu().numpy()
+    ns = 200_000
+    want = sal_oracle.lookup(sa, k[:ns], cnt[:ns])
+    mism = int((got[:want.shape[0]] != want).sum())
+    t0 = time.perf_counter()
+    sal_oracle.lookup(sa, k[:ns], cnt[:ns])
+    tcpu = time.perf_counter() - t0
+    nbytes = n_int * (8 + 4 + 8) + total * (4 + 4)
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    ctx.close()
+    return {"workload": "64 Mbp reference prefix, suffix array of 64,000,001 int32 (256 MB); 8,000,000 intervals, "
+                        "counts geometric(0.25) capped at 500 (%d positions)" % total,
+            "ms": round(ms, 4), "positions_per_s": round(total / (ms * 1e-3), 1),
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(gbs / hbm_peak, 4) if hbm_peak else None,
+                         "bytes": "per interval k, count, offset (20 B) + per position S read and output write (8 B)"},
+            "index_build_s": round(t_build, 2),
+            "parity_sample": {"intervals_checked": ns, "mismatches": mism},
+            "cpu_oracle": {"positions_per_s": round(want.shape[0] / tcpu, 1), "cores": 1,
+                           "sample": "the first %d intervals, %.3f s" % (ns, tcpu)}}
+
+
 def pinned_host_batch(bsw, hb):
     """Copy a HostBatch's arrays into pinned host memory (for the end-to-end leg)."""
     import torch
@@ -468,6 +527,9 @@ def run_gb300(args):
     drv = None
     if rank == 0 and not args.no_driver and args.config == "read151" and args.pairs is None:
         drv = driver_leg(bsw, args)
+    sal_line = None
+    if rank == 0 and not args.no_sal and args.config == "read151" and args.pairs is None:
+        sal_line = sal_leg(bsw, args, stream, measured_peaks().get("hbm_gbs"))
 
     if rank == 0:
         line = {
@@ -497,6 +559,7 @@ def run_gb300(args):
             "cpu_baseline": cpu,
             "parity_sample": parity,
             "extension_driver": drv,
+            "suffix_array_lookup": sal_line,
             "e2e": {"value": round(e2e, 3), "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(t_e2e * 1e3, 3), "bit_exact_vs_device": e2e_equal},
             "gpu_launches": launches_per_step * args.steps,

@@ -361,6 +361,37 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
                      const int32_t *read_len, int64_t n_seeds, const bsw_seed_t *seeds, int32_t max_band_try,
                      bsw_aln_t *out, int64_t *cells_out);
 
+/*
+ * Suffix array lookup (Section IV-D, Eq. 1: j = S[i]).
+ *
+ * bsw_sa_build (host only, no context): the suffix array of codes[0..n)
+ * (bases 0..3) followed by a terminator smaller than every base, written to
+ * sa[0..n] (n + 1 entries; sa[0] = n).  Built by induced sorting in linear
+ * time; an index step, run once per reference.  n < 2^31 - 2.
+ * Errors: BSW_EINVAL (bad argument or a code > 3), BSW_ENOMEM.
+ */
+int bsw_sa_build(const uint8_t *codes, int64_t n, int32_t *sa);
+
+/*
+ * bsw_sal_set_index: upload a suffix array of sa_n entries (host pointer) to
+ * the context, uncompressed (4 bytes per entry, charged to the budget); it
+ * replaces any earlier one.  Errors: BSW_EINVAL, BSW_EBUDGET, BSW_ENOMEM,
+ * BSW_ECUDA, BSW_ESTATE (submitted work pending).
+ *
+ * bsw_sal_lookup: for each SA interval t, positions[off[t] + i] = S[k[t] + i]
+ * for 0 <= i < cnt[t] (the reference coordinates of the interval's matches).
+ * off[] is the caller's layout of the output (for example the exclusive
+ * prefix sum of cnt).  Host pointers (flags 0): the call checks every
+ * interval, stages, gathers on the GPU and returns with positions filled.
+ * BSW_DEVICE_PTRS: k, cnt, off, positions are device memory; the call only
+ * enqueues on cuda_stream (NULL: the context's stream), and an interval
+ * outside [0, sa_n) is skipped and reported by bsw_sync.
+ * Errors: BSW_EINVAL, BSW_ESTATE (no suffix array), BSW_EBUDGET, BSW_ECUDA.
+ */
+int bsw_sal_set_index(bsw_ctx_t *ctx, const int32_t *sa, int64_t sa_n);
+int bsw_sal_lookup(bsw_ctx_t *ctx, int64_t n_intervals, const int64_t *k, const int32_t *cnt, const int64_t *off,
+                   int32_t *positions, uint32_t flags, void *cuda_stream);
+
 /* Library version string. */
 const char *bsw_version(void);
 

@@ -136,6 +136,12 @@ def lib():
             L.bsw_autotune.restype = ctypes.c_int
             L.bsw_kernel_times.argtypes = [vp, ctypes.POINTER(bsw_timing_t)]
             L.bsw_kernel_times.restype = ctypes.c_int
+            L.bsw_sa_build.argtypes = [vp, i64, vp]
+            L.bsw_sa_build.restype = ctypes.c_int
+            L.bsw_sal_set_index.argtypes = [vp, vp, i64]
+            L.bsw_sal_set_index.restype = ctypes.c_int
+            L.bsw_sal_lookup.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.c_uint32, vp]
+            L.bsw_sal_lookup.restype = ctypes.c_int
             L.bsw_set_reference.argtypes = [vp, vp, i64]
             L.bsw_set_reference.restype = ctypes.c_int
             L.bsw_extend_seeds.argtypes = [vp, i64, vp, vp, vp, i64, vp, i32, vp, vp]
@@ -244,6 +250,16 @@ def bsw_extend_seeds(ctx: int, n_reads: int, reads, read_off, read_len, seeds, m
     return lib().bsw_extend_seeds(ctx, int(n_reads), reads.ctypes.data, read_off.ctypes.data, read_len.ctypes.data,
                                   int(seeds.shape[0]), seeds.ctypes.data, int(max_band_try), out.ctypes.data,
                                   ctypes.addressof(cells))
+
+
+def bsw_sa_build(codes: np.ndarray) -> np.ndarray:
+    """Suffix array of codes (0..3) + terminator: n + 1 int32 entries."""
+    codes = np.ascontiguousarray(codes, np.uint8)
+    sa = np.zeros(codes.shape[0] + 1, np.int32)
+    rc = lib().bsw_sa_build(codes.ctypes.data, codes.shape[0], sa.ctypes.data)
+    if rc != BSW_OK:
+        raise BswError(rc, "bsw_sa_build")
+    return sa
 
 
 def make_plan(short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8, inter_warps=2) -> bsw_plan_t:
@@ -376,6 +392,33 @@ class Context:
         if rc != BSW_OK:
             raise BswError(rc, "bsw_kernel_times")
         return t.launches, list(t.class_ms)
+
+    def sal_set_index(self, sa: np.ndarray) -> None:
+        sa = np.ascontiguousarray(sa, np.int32)
+        rc = lib().bsw_sal_set_index(self.handle, sa.ctypes.data, sa.shape[0])
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_sal_set_index")
+
+    def sal_lookup(self, k: np.ndarray, cnt: np.ndarray) -> np.ndarray:
+        """Host intervals -> the concatenated positions S[k[t] .. k[t] + cnt[t])."""
+        k = np.ascontiguousarray(k, np.int64)
+        cnt = np.ascontiguousarray(cnt, np.int32)
+        off = np.zeros(k.shape[0], np.int64)
+        if k.shape[0] > 1:
+            np.cumsum(cnt[:-1], out=off[1:])
+        out = np.zeros(int(cnt.sum()), np.int32)
+        rc = lib().bsw_sal_lookup(self.handle, k.shape[0], k.ctypes.data, cnt.ctypes.data, off.ctypes.data,
+                                  out.ctypes.data, 0, None)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_sal_lookup")
+        return out
+
+    def sal_lookup_device(self, k, cnt, off, out, stream: int | None = None) -> None:
+        """Device intervals (torch tensors): enqueue the gather into out."""
+        rc = lib().bsw_sal_lookup(self.handle, k.shape[0], k.data_ptr(), cnt.data_ptr(), off.data_ptr(),
+                                  out.data_ptr(), BSW_DEVICE_PTRS, stream)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_sal_lookup")
 
     def set_reference(self, ref_codes: np.ndarray) -> None:
         """Upload a reference given as codes 0..3 (packed here)."""

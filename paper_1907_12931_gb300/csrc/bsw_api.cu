@@ -298,6 +298,10 @@ struct bsw_ctx {
     DevBuf refbuf, drv;
     int64_t ref_len = -1;
 
+    // suffix array lookup: the uncompressed suffix array and staging
+    DevBuf sabuf, salio;
+    int64_t sa_n = -1;
+
     struct GEntry {
         bsw_batch_t b;
         void *out, *cells;
@@ -1197,6 +1201,74 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
     return status_to_rc(*ctx->h_status);
 }
 
+int bsw_sal_set_index(bsw_ctx_t *ctx, const int32_t *sa, int64_t sa_n)
+{
+    if (!ctx || sa_n < 0 || (sa_n > 0 && !sa)) return BSW_EINVAL;
+    if (!serving_idle(ctx)) return BSW_ESTATE;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+    ctx->sa_n = -1;
+    const size_t bytes = 4 * (size_t)sa_n;
+    int rc = ctx->sabuf.reserve(bytes > 0 ? bytes : 4, ctx->budget);
+    if (rc != BSW_OK) return rc;
+    if (bytes) {
+        cudaError_t e = cudaMemcpy(ctx->sabuf.p, sa, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_rc(e);
+    }
+    ctx->sa_n = sa_n;
+    return BSW_OK;
+}
+
+int bsw_sal_lookup(bsw_ctx_t *ctx, int64_t n_int, const int64_t *k, const int32_t *cnt, const int64_t *off,
+                   int32_t *positions, uint32_t flags, void *cuda_stream)
+{
+    if (!ctx || n_int < 0 || (flags & ~BSW_DEVICE_PTRS)) return BSW_EINVAL;
+    if (ctx->sa_n < 0) return BSW_ESTATE;
+    if (n_int == 0) return BSW_OK;
+    if (!k || !cnt || !off || !positions) return BSW_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+    const int32_t *sa = (const int32_t *)ctx->sabuf.p;
+    cudaError_t e;
+    if (flags & BSW_DEVICE_PTRS) {
+        // enqueue only; an interval outside the suffix array is reported by bsw_sync
+        Lane &lane = ctx->sync;
+        bool moved = false;
+        int rc = lane.ensure_work(1, kShortMax, ctx->sms, ctx->budget, &moved);
+        if (rc != BSW_OK) return rc;
+        if (moved) clear_graphs(ctx);
+        Work W = make_work(lane.work.p, lane.wl);
+        cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : lane.S.main;
+        return cuda_rc(launch_sal(sa, ctx->sa_n, k, cnt, off, n_int, positions, W.status, st, ctx->sms));
+    }
+    // host pointers: check, stage, gather, copy back
+    int64_t total = 0;
+    for (int64_t t = 0; t < n_int; ++t) {
+        if (k[t] < 0 || cnt[t] < 0 || k[t] + cnt[t] > ctx->sa_n || off[t] < 0) return BSW_EINVAL;
+        total = std::max(total, off[t] + cnt[t]);
+    }
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    const size_t o_k = take(8 * (size_t)n_int), o_c = take(4 * (size_t)n_int), o_o = take(8 * (size_t)n_int),
+                 o_p = take(4 * (size_t)total), o_st = take(4);
+    int rc = ctx->salio.reserve(o, ctx->budget);
+    if (rc != BSW_OK) return rc;
+    uint8_t *d = ctx->salio.p;
+    cudaStream_t st = ctx->sync.S.main;
+    if ((e = cudaMemcpyAsync(d + o_k, k, 8 * (size_t)n_int, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d + o_c, cnt, 4 * (size_t)n_int, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d + o_o, off, 8 * (size_t)n_int, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d + o_st, 0, 4, st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = launch_sal(sa, ctx->sa_n, (const int64_t *)(d + o_k), (const int32_t *)(d + o_c),
+                        (const int64_t *)(d + o_o), n_int, (int32_t *)(d + o_p), (uint32_t *)(d + o_st), st,
+                        ctx->sms)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((total && (e = cudaMemcpyAsync(positions, d + o_p, 4 * (size_t)total, cudaMemcpyDeviceToHost, st)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(ctx->h_status, d + o_st, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_rc(e);
+    return status_to_rc(*ctx->h_status);
+}
+
 void bsw_destroy(bsw_ctx_t *ctx)
 {
     if (!ctx) return;
@@ -1213,6 +1285,8 @@ void bsw_destroy(bsw_ctx_t *ctx)
     ctx->sync.destroy(ctx->budget);
     ctx->refbuf.release(ctx->budget);
     ctx->drv.release(ctx->budget);
+    ctx->sabuf.release(ctx->budget);
+    ctx->salio.release(ctx->budget);
     if (ctx->timer_ready)
         for (int k = 0; k <= kNumClass; ++k) {
             cudaEventDestroy(ctx->timer.t0[k]);

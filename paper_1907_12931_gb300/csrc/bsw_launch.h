@@ -119,4 +119,9 @@ cudaError_t launch_decide(bool left, const DriverIn &D, const DriverSide &S, int
                           bsw_aln_t *out, cudaStream_t st, int sms);
 cudaError_t launch_filter(const DriverIn &D, int64_t n, bsw_aln_t *out, cudaStream_t st, int sms);
 
+// Suffix array lookup: out[off[t] + i] = sa[k[t] + i] for i < cnt[t].
+// Intervals outside [0, sa_n) set kStInval in *status and write nothing.
+cudaError_t launch_sal(const int32_t *sa, int64_t sa_n, const int64_t *k, const int32_t *cnt, const int64_t *off,
+                       int64_t n_int, int32_t *out, uint32_t *status, cudaStream_t st, int sms);
+
 }  // namespace bsw
