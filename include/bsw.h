@@ -392,6 +392,43 @@ int bsw_sal_set_index(bsw_ctx_t *ctx, const int32_t *sa, int64_t sa_n);
 int bsw_sal_lookup(bsw_ctx_t *ctx, int64_t n_intervals, const int64_t *k, const int32_t *cnt, const int64_t *off,
                    int32_t *positions, uint32_t flags, void *cuda_stream);
 
+/*
+ * Super-maximal exact matches (Section IV; Li 2012).
+ *
+ * bsw_fm_build: index the reference for SMEM search.  The text is
+ * T = ref + its reverse complement (the SMEM search covers both strands);
+ * the call builds, on the host, the FM-indexes of T and of reverse(T)
+ * (suffix arrays by induced sorting, occurrence tables in buckets of 32 BWT
+ * positions) and uploads them (about 2 bytes per reference base; the
+ * suffix arrays are not kept).  ref: codes 0..3, n bases, n < 2^30.
+ * Errors: BSW_EINVAL, BSW_ENOMEM, BSW_EBUDGET, BSW_ECUDA, BSW_ESTATE
+ * (submitted work pending).
+ *
+ * bsw_smem: for each read X (2-bit packed at base offset read_off[r], a
+ * multiple of 4, with read_len[r] bases), with e(i) the end of the longest
+ * prefix of X[i:] occurring in T, the SMEMs are the intervals [i, e(i)) with
+ * i = 0 or e(i-1) < e(i) (no longer exact match contains them); those of at
+ * least min_len bases are written to out, grouped by read in read order and
+ * by qbeg within a read, with [k, k + s) the interval of X[i, e(i)) in the
+ * suffix array of T.  first[r] (n_reads + 1 entries, nullable) receives the
+ * index of read r's first record.  *n_out receives the number of records;
+ * if it exceeds out_cap nothing is written to out and BSW_EBUDGET is
+ * returned (call again with a larger out).  Device memory: about
+ * 4 * n_reads * max(read_len) bytes besides the reads.
+ * Errors: BSW_EINVAL, BSW_ESTATE (no index), BSW_EBUDGET, BSW_ECUDA.
+ */
+typedef struct {
+    int32_t read_id;   /* the read                                              */
+    int32_t qbeg, len; /* the match: read bases [qbeg, qbeg + len)              */
+    int32_t reserved;
+    int64_t k, s;      /* its suffix-array interval [k, k + s) in T (s = count) */
+} bsw_smem_t;
+
+int bsw_fm_build(bsw_ctx_t *ctx, const uint8_t *ref, int64_t n);
+int bsw_smem(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_t *read_off,
+             const int32_t *read_len, int32_t min_len, bsw_smem_t *out, int64_t out_cap, int64_t *n_out,
+             int64_t *first);
+
 /* Library version string. */
 const char *bsw_version(void);
 

@@ -83,6 +83,8 @@ class bsw_aln_t(ctypes.Structure):
                 ("kept", ctypes.c_int32)]
 
 
+SMEM_DTYPE = np.dtype([("read_id", "<i4"), ("qbeg", "<i4"), ("len", "<i4"), ("reserved", "<i4"), ("k", "<i8"),
+                       ("s", "<i8")])
 SEED_DTYPE = np.dtype([("read_id", "<i4"), ("qbeg", "<i4"), ("len", "<i4"), ("reserved", "<i4"), ("rbeg", "<i8")])
 ALN_DTYPE = np.dtype([("qb", "<i4"), ("qe", "<i4"), ("rb", "<i8"), ("re", "<i8"), ("score", "<i4"),
                       ("w_left", "<i4"), ("w_right", "<i4"), ("kept", "<i4")])
@@ -142,6 +144,10 @@ def lib():
             L.bsw_sal_set_index.restype = ctypes.c_int
             L.bsw_sal_lookup.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.c_uint32, vp]
             L.bsw_sal_lookup.restype = ctypes.c_int
+            L.bsw_fm_build.argtypes = [vp, vp, i64]
+            L.bsw_fm_build.restype = ctypes.c_int
+            L.bsw_smem.argtypes = [vp, i64, vp, vp, vp, i32, vp, i64, vp, vp]
+            L.bsw_smem.restype = ctypes.c_int
             L.bsw_set_reference.argtypes = [vp, vp, i64]
             L.bsw_set_reference.restype = ctypes.c_int
             L.bsw_extend_seeds.argtypes = [vp, i64, vp, vp, vp, i64, vp, i32, vp, vp]
@@ -392,6 +398,31 @@ class Context:
         if rc != BSW_OK:
             raise BswError(rc, "bsw_kernel_times")
         return t.launches, list(t.class_ms)
+
+    def fm_build(self, ref_codes: np.ndarray) -> None:
+        ref = np.ascontiguousarray(ref_codes, np.uint8)
+        rc = lib().bsw_fm_build(self.handle, ref.ctypes.data, ref.shape[0])
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_fm_build")
+
+    def smem(self, reads_packed, read_off, read_len, min_len: int = 19, cap: int | None = None):
+        """SMEMs of packed reads.  Returns (structured records, first[n_reads + 1])."""
+        read_off = np.ascontiguousarray(read_off, np.int64)
+        read_len = np.ascontiguousarray(read_len, np.int32)
+        n = read_len.shape[0]
+        first = np.zeros(n + 1, np.int64)
+        n_out = ctypes.c_int64()
+        cap = 4 * n + 16 if cap is None else cap
+        while True:
+            out = np.zeros(cap, SMEM_DTYPE)
+            rc = lib().bsw_smem(self.handle, n, reads_packed.ctypes.data, read_off.ctypes.data, read_len.ctypes.data,
+                                int(min_len), out.ctypes.data, cap, ctypes.addressof(n_out), first.ctypes.data)
+            if rc == BSW_EBUDGET and n_out.value > cap:
+                cap = int(n_out.value)
+                continue
+            if rc != BSW_OK:
+                raise BswError(rc, "bsw_smem")
+            return out[:n_out.value], first
 
     def sal_set_index(self, sa: np.ndarray) -> None:
         sa = np.ascontiguousarray(sa, np.int32)

@@ -26,6 +26,8 @@
 #include "bsw_device.cuh"
 #include "bsw_launch.h"
 
+extern "C" int bsw_sa_build(const uint8_t *codes, int64_t n, int32_t *sa);
+
 using namespace bsw;
 
 namespace {
@@ -301,6 +303,11 @@ struct bsw_ctx {
     // suffix array lookup: the uncompressed suffix array and staging
     DevBuf sabuf, salio;
     int64_t sa_n = -1;
+
+    // SMEM search: the FM-indexes of T = ref + revcomp(ref) and of reverse(T)
+    DevBuf fmbuf, smemio;
+    FmDev fm_t{}, fm_r{};
+    bool fm_ready = false;
 
     struct GEntry {
         bsw_batch_t b;
@@ -1269,6 +1276,103 @@ int bsw_sal_lookup(bsw_ctx_t *ctx, int64_t n_int, const int64_t *k, const int32_
     return status_to_rc(*ctx->h_status);
 }
 
+int bsw_fm_build(bsw_ctx_t *ctx, const uint8_t *ref, int64_t n)
+{
+    if (!ctx || n < 1 || n >= (1ll << 30) || !ref) return BSW_EINVAL;
+    if (!serving_idle(ctx)) return BSW_ESTATE;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+    ctx->fm_ready = false;
+    FmHost ft, fr;
+    try {
+        std::vector<uint8_t> T((size_t)(2 * n));
+        for (int64_t i = 0; i < n; ++i) {
+            if (ref[i] > 3) return BSW_EINVAL;
+            T[(size_t)i] = ref[i];
+            T[(size_t)(2 * n - 1 - i)] = (uint8_t)(3 - ref[i]);   // reverse complement
+        }
+        std::vector<int32_t> sa((size_t)(2 * n + 1));
+        int rc = bsw_sa_build(T.data(), 2 * n, sa.data());
+        if (rc != BSW_OK) return rc;
+        fm_from_sa(T.data(), 2 * n, sa.data(), ft);
+        std::reverse(T.begin(), T.end());
+        if ((rc = bsw_sa_build(T.data(), 2 * n, sa.data())) != BSW_OK) return rc;
+        fm_from_sa(T.data(), 2 * n, sa.data(), fr);
+    } catch (const std::bad_alloc &) {
+        return BSW_ENOMEM;
+    }
+    const size_t bt = sizeof(FmEntry) * ft.occ.size(), br = sizeof(FmEntry) * fr.occ.size();
+    int rc = ctx->fmbuf.reserve(bt + br, ctx->budget);
+    if (rc != BSW_OK) return rc;
+    cudaError_t e;
+    if ((e = cudaMemcpy(ctx->fmbuf.p, ft.occ.data(), bt, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(ctx->fmbuf.p + bt, fr.occ.data(), br, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_rc(e);
+    ctx->fm_t = FmDev{(const FmEntry *)ctx->fmbuf.p, ft.n, ft.primary, {ft.C[0], ft.C[1], ft.C[2], ft.C[3], ft.C[4]}};
+    ctx->fm_r = FmDev{(const FmEntry *)(ctx->fmbuf.p + bt), fr.n, fr.primary,
+                      {fr.C[0], fr.C[1], fr.C[2], fr.C[3], fr.C[4]}};
+    ctx->fm_ready = true;
+    return BSW_OK;
+}
+
+int bsw_smem(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_t *read_off,
+             const int32_t *read_len, int32_t min_len, bsw_smem_t *out, int64_t out_cap, int64_t *n_out,
+             int64_t *first)
+{
+    if (!ctx || n_reads < 0 || min_len < 1 || out_cap < 0 || !n_out) return BSW_EINVAL;
+    if (n_reads > 0 && (!reads || !read_off || !read_len)) return BSW_EINVAL;
+    if (!ctx->fm_ready) return BSW_ESTATE;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+    *n_out = 0;
+    if (first) first[0] = 0;
+    if (n_reads == 0) return BSW_OK;
+    int64_t read_bytes = 0;
+    int lmax = 0;
+    for (int64_t r = 0; r < n_reads; ++r) {
+        if (read_off[r] < 0 || (read_off[r] & 3) || read_len[r] < 0 || read_len[r] > kLongMax) return BSW_EINVAL;
+        read_bytes = std::max(read_bytes, (read_off[r] + read_len[r] + 3) / 4);
+        lmax = std::max(lmax, (int)read_len[r]);
+    }
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    const size_t o_reads = take((size_t)read_bytes), o_roff = take(8 * (size_t)n_reads),
+                 o_rlen = take(4 * (size_t)n_reads), o_end = take(4 * (size_t)n_reads * (size_t)lmax),
+                 o_cnt = take(8 * (size_t)n_reads), o_first = take(8 * (size_t)n_reads),
+                 o_out = take(sizeof(bsw_smem_t) * (size_t)std::max<int64_t>(out_cap, 1));
+    int rc = ctx->smemio.reserve(o, ctx->budget);
+    if (rc != BSW_OK) return rc;
+    uint8_t *d = ctx->smemio.p;
+    cudaStream_t st = ctx->sync.S.main;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d + o_reads, reads, (size_t)read_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d + o_roff, read_off, 8 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d + o_rlen, read_len, 4 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_rc(e);
+    const SmemIn R{d + o_reads, (const int64_t *)(d + o_roff), (const int32_t *)(d + o_rlen), n_reads, lmax};
+    int32_t *end = (int32_t *)(d + o_end);
+    int64_t *cnt = (int64_t *)(d + o_cnt), *dfirst = (int64_t *)(d + o_first);
+    if ((e = launch_match_end(R, ctx->fm_r, end, st, ctx->sms)) != cudaSuccess ||
+        (e = launch_smem(false, R, ctx->fm_t, end, min_len, cnt, nullptr, nullptr, st, ctx->sms)) != cudaSuccess)
+        return cuda_rc(e);
+    std::vector<int64_t> hc((size_t)n_reads), hf((size_t)n_reads + 1);
+    if ((e = cudaMemcpyAsync(hc.data(), cnt, 8 * (size_t)n_reads, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_rc(e);
+    hf[0] = 0;
+    for (int64_t r = 0; r < n_reads; ++r) hf[(size_t)r + 1] = hf[(size_t)r] + hc[(size_t)r];
+    const int64_t total = hf[(size_t)n_reads];
+    *n_out = total;
+    if (first) std::memcpy(first, hf.data(), 8 * ((size_t)n_reads + 1));
+    if (total > out_cap) return BSW_EBUDGET;
+    if (total == 0) return BSW_OK;
+    bsw_smem_t *dout = (bsw_smem_t *)(d + o_out);
+    if ((e = cudaMemcpyAsync(dfirst, hf.data(), 8 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = launch_smem(true, R, ctx->fm_t, end, min_len, nullptr, dfirst, dout, st, ctx->sms)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out, dout, sizeof(bsw_smem_t) * (size_t)total, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_rc(e);
+    return BSW_OK;
+}
+
 void bsw_destroy(bsw_ctx_t *ctx)
 {
     if (!ctx) return;
@@ -1287,6 +1391,8 @@ void bsw_destroy(bsw_ctx_t *ctx)
     ctx->drv.release(ctx->budget);
     ctx->sabuf.release(ctx->budget);
     ctx->salio.release(ctx->budget);
+    ctx->fmbuf.release(ctx->budget);
+    ctx->smemio.release(ctx->budget);
     if (ctx->timer_ready)
         for (int k = 0; k <= kNumClass; ++k) {
             cudaEventDestroy(ctx->timer.t0[k]);

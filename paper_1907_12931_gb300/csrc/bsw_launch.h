@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <vector>
 #include "bsw_device.cuh"
 
 namespace bsw {
@@ -118,6 +119,50 @@ cudaError_t launch_retry_scatter(const DriverSide &S, const int32_t *list, const
 cudaError_t launch_decide(bool left, const DriverIn &D, const DriverSide &S, int64_t n, int end_bonus,
                           bsw_aln_t *out, cudaStream_t st, int sms);
 cudaError_t launch_filter(const DriverIn &D, int64_t n, bsw_aln_t *out, cudaStream_t st, int sms);
+
+// ----------------------------------------------------- FM-index and SMEMs
+
+// One bucket of the occurrence table: counts of each base in BWT[0, 32t)
+// and the bucket's 32 BWT bases, 2-bit packed (32 bytes, one DRAM sector).
+struct FmEntry {
+    uint32_t cnt[4];
+    uint64_t bwt;
+    uint64_t pad;
+};
+
+// Host copy of one FM-index: n = text length + 1 BWT rows, the $ row, the
+// first row of each base's block (C[0] = 1 for $, C[4] = n).
+struct FmHost {
+    int64_t n = 0, primary = -1;
+    int64_t C[5] = {0, 0, 0, 0, 0};
+    std::vector<FmEntry> occ;
+};
+
+struct FmDev {
+    const FmEntry *occ;
+    int64_t n, primary;
+    int64_t C[5];
+};
+
+// Reads of an SMEM search: packed 2-bit, read r at base offset read_off[r]
+// with read_len[r] <= lmax bases.
+struct SmemIn {
+    const uint8_t *reads;
+    const int64_t *read_off;
+    const int32_t *read_len;
+    int64_t n_reads;
+    int lmax;
+};
+
+// The index of text[0..n) from its suffix array sa[0..n] (host).
+void fm_from_sa(const uint8_t *text, int64_t n, const int32_t *sa, FmHost &out);
+// end[r * lmax + i] = the end of the longest prefix of read r from i that
+// occurs in the text of Frev's reverse.
+cudaError_t launch_match_end(const SmemIn &R, const FmDev &Frev, int32_t *end, cudaStream_t st, int sms);
+// Per read, its SMEMs of at least min_len bases: counts (write = false) or
+// the records at first[r] (write = true) with SA intervals in F.
+cudaError_t launch_smem(bool write, const SmemIn &R, const FmDev &F, const int32_t *end, int min_len, int64_t *count,
+                        const int64_t *first, bsw_smem_t *out, cudaStream_t st, int sms);
 
 // Suffix array lookup: out[off[t] + i] = sa[k[t] + i] for i < cnt[t].
 // Intervals outside [0, sa_n) set kStInval in *status and write nothing.

@@ -54,6 +54,8 @@ def _load():
             lib.bswgen_ref_copy.restype = ctypes.c_int
             lib.bswgen_ref_len.argtypes = []
             lib.bswgen_ref_len.restype = i64
+            lib.bswgen_reads.argtypes = [u64, i64, i32, i64, vp, vp]
+            lib.bswgen_reads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -285,3 +287,20 @@ def seeds_from_lists(reads, ref, seeds, params: Params | None = None, name: str 
     return SeedWorkload(name, params or Params(), packed, roff, rlen, np.asarray(ref, np.uint8), sr,
                         np.array([s[1] for s in seeds], np.int32), np.array([s[2] for s in seeds], np.int32),
                         np.array([s[3] for s in seeds], np.int64))
+
+
+def make_reads(n_reads: int, read_len: int = 151, ref_limit: int = 48_000_000, seed: int = 21):
+    """Reads for the SMEM search copied from the reference's first ref_limit
+    bases (read151 or read250 recipe), odd-numbered ones reverse-complemented.
+    Returns (reads as codes laid out at read_off, read_off (multiples of 4),
+    read_len, reference start of each read)."""
+    reads = np.zeros(n_reads * read_len, np.uint8)
+    pos = np.zeros(n_reads, np.int64)
+    rc = _load().bswgen_reads(seed, n_reads, read_len, ref_limit, reads.ctypes.data, pos.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("bswgen_reads failed: %d" % rc)
+    rl = np.full(n_reads, read_len, np.int32)
+    off, total = layout(rl, 4)
+    codes = np.zeros(total, np.uint8)
+    codes[np.repeat(off, read_len) + np.tile(np.arange(read_len), n_reads)] = reads
+    return codes, off, rl, pos

@@ -405,3 +405,50 @@ int bswgen_ref_copy(int64_t start, int64_t n, uint8_t *out)
 }
 
 int64_t bswgen_ref_len(void) { return REF_LEN_LARGE; }
+
+/*
+ * Reads for the SMEM search: n_reads reads of read_len bases copied from
+ * reference positions [400, ref_limit - read_len - 400) with the recipe of
+ * workload 1 (read_len 151: donor SNPs, 1% substitutions) or 2 (2%
+ * divergence with indels); odd-numbered reads are reverse-complemented (the
+ * other strand).  pos[r] receives the reference start of read r.
+ */
+int bswgen_reads(uint64_t seed, int64_t n_reads, int32_t read_len, int64_t ref_limit, uint8_t *reads, int64_t *pos)
+{
+    const uint8_t *ref = get_ref(1);
+    if (!ref || n_reads < 0 || read_len < 1 || read_len > 10000 || ref_limit > REF_LEN_LARGE ||
+        ref_limit < 2 * (int64_t)read_len + 1000)
+        return -1;
+    mut_t mu;
+    if (read_len == 151) { mu.thr_indel = 0; mu.thr_sub = ppm_thr(10000); mu.indel_max = 1; }
+    else { mu.thr_indel = ppm_thr(2000); mu.thr_sub = ppm_thr(18000); mu.indel_max = 10; }
+    const uint64_t snp_thr = ppm_thr(1000);
+    const uint64_t donor_seed = sm_hash(REF_SEED, 0xD0D0);
+    uint8_t *tmp = (uint8_t *)malloc((size_t)read_len);
+    if (!tmp) return -2;
+    for (int64_t r = 0; r < n_reads; ++r) {
+        uint64_t rng = sm_hash(seed ^ 0x5E1EC7ULL, (uint64_t)r);
+        const int64_t r0 = 400 + (int64_t)uni(&rng, (uint32_t)(ref_limit - 2 * (int64_t)read_len - 800));
+        pos[r] = r0;
+        if (read_len == 151) {
+            for (int32_t k = 0; k < read_len; ++k) {
+                int64_t p = r0 + k;
+                uint8_t b = ref[p];
+                uint64_t hv = sm_hash(donor_seed, (uint64_t)p);
+                if (hv < snp_thr) b = (uint8_t)((b + 1 + (uint32_t)((hv >> 8) % 3)) & 3);
+                if (sm_next(&rng) < mu.thr_sub) b = (uint8_t)((b + 1 + uni(&rng, 3)) & 3);
+                tmp[k] = b;
+            }
+        } else {
+            mutate_copy(ref, ref_limit, r0, read_len, &rng, &mu, tmp, NULL);
+        }
+        uint8_t *out = reads + r * (int64_t)read_len;
+        if (r & 1) {
+            for (int32_t k = 0; k < read_len; ++k) out[k] = (uint8_t)(3 - tmp[read_len - 1 - k]);
+        } else {
+            memcpy(out, tmp, (size_t)read_len);
+        }
+    }
+    free(tmp);
+    return 0;
+}

@@ -1,0 +1,71 @@
+"""SMEM search on the GPU (bsw_fm_build + bsw_smem) against the oracle
+(oracle/smem.py), needs a GPU: every record (read, start, length, SA
+interval) must match."""
+import numpy as np
+import pytest
+
+from oracle import smem
+from paper_1907_12931_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bsw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_12931_gb300 import bsw as _b
+    _b.lib()
+    return _b
+
+
+def pack(reads):
+    rl = np.array([len(r) for r in reads], np.int32)
+    off, total = W.layout(rl, 4)
+    codes = np.zeros(total, np.uint8)
+    for o, r in zip(off, reads):
+        codes[o:o + len(r)] = r
+    from paper_1907_12931_gb300 import bsw as b
+    return b.bsw_pack_2bit(codes), off, rl
+
+
+def check(bsw, ref, reads, min_len):
+    want = smem.smems(ref, reads, min_len)
+    packed, off, rl = pack(reads)
+    with bsw.Context(W.Params()) as ctx:
+        ctx.fm_build(ref)
+        got, first = ctx.smem(packed, off, rl, min_len=min_len, cap=1)   # cap 1: exercises the retry
+    for r, w in enumerate(want):
+        g = got[first[r]:first[r + 1]]
+        assert np.all(g["read_id"] == r)
+        assert [tuple(int(v) for v in x) for x in g[["qbeg", "len", "k", "s"]]] == [tuple(x) for x in w], r
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_small_references(bsw, seed):
+    rng = np.random.default_rng(100 + seed)
+    ref = rng.integers(0, 4, 500 + 300 * seed).astype(np.uint8)
+    reads = []
+    for _ in range(40):
+        L = int(rng.integers(0, 60))
+        if rng.random() < 0.7 and L:
+            p = int(rng.integers(0, ref.shape[0] - L))
+            x = ref[p:p + L].copy()
+            if rng.random() < 0.5:
+                x = (3 - x[::-1]).astype(np.uint8)
+            flips = rng.random(L) < 0.05
+            x[flips] = (x[flips] + 1) % 4
+        else:
+            x = rng.integers(0, 4, L).astype(np.uint8)
+        reads.append(x)
+    for min_len in (1, 5, 19):
+        check(bsw, ref, reads, min_len)
+
+
+def test_generated_reads(bsw):
+    """151 bp reads from both strands of a 60 kbp reference prefix."""
+    ref = W.reference()[:60_000]
+    codes, off, rl, _ = W.make_reads(120, 151, ref_limit=60_000)
+    reads = [codes[o:o + n] for o, n in zip(off, rl)]
+    check(bsw, ref, reads, 19)
