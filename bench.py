@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the default plan (no autotune)")
     ap.add_argument("--no-driver", action="store_true", help="skip the seed-extension driver leg")
     ap.add_argument("--no-sal", action="store_true", help="skip the suffix-array lookup leg")
+    ap.add_argument("--no-smem", action="store_true", help="skip the SMEM search leg")
     ap.add_argument("--plan", default=None,
                     help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps (no autotune)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point")
@@ -388,6 +389,65 @@ def sal_leg(bsw, args, stream, hbm_peak):
                            "sample": "the first %d intervals, %.3f s" % (ns, tcpu)}}
 
 
+def _occurrences(T, p):
+    """Occurrences of pattern p in text T (numpy, candidate filtering)."""
+    idx = np.nonzero(T[:T.shape[0] - p.shape[0] + 1] == p[0])[0]
+    for d in range(1, p.shape[0]):
+        idx = idx[T[idx + d] == p[d]]
+    return idx.shape[0]
+
+
+def smem_leg(bsw, args):
+    """SMEM search over 200,000 151 bp reads (both strands) of a 48 Mbp
+    reference prefix: the FM-indexes of ref + revcomp(ref) and its reverse
+    (occurrence tables of 192 MB, larger than L2), the search end to end
+    through the C ABI; sampled records checked against the definition."""
+    from paper_1907_12931_gb300 import workload as W
+    n_ref = 48_000_000
+    ref = W.reference()[:n_ref]
+    ctx = bsw.Context(W.Params(), mem_budget_bytes=16 << 30)
+    t0 = time.perf_counter()
+    ctx.fm_build(ref)
+    t_build = time.perf_counter() - t0
+    codes, off, rl, _ = W.make_reads(200_000, 151, ref_limit=n_ref)
+    packed = bsw.bsw_pack_2bit(codes)
+    recs, first = ctx.smem(packed, off, rl, min_len=19)
+    cap = recs.shape[0] + 16
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        recs, first = ctx.smem(packed, off, rl, min_len=19, cap=cap)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    ctx.close()
+    T = np.concatenate([ref, (3 - ref[::-1]).astype(np.uint8)])
+    rng = np.random.default_rng(5)
+    bad = 0
+    pick = rng.choice(recs.shape[0], size=min(20, recs.shape[0]), replace=False)
+    for j in pick:
+        r, q, ln, cnt = int(recs["read_id"][j]), int(recs["qbeg"][j]), int(recs["len"][j]), int(recs["s"][j])
+        x = codes[off[r]:off[r] + rl[r]]
+        ok = _occurrences(T, x[q:q + ln]) == cnt
+        if q + ln < rl[r]:
+            ok &= _occurrences(T, x[q:q + ln + 1]) == 0     # not extendable to the right
+        if q > 0:
+            ok &= _occurrences(T, x[q - 1:q + ln]) == 0     # not extendable to the left
+        bad += 0 if ok else 1
+    return {"workload": "200,000 151 bp reads (read151 recipe, every other read from the reverse strand) of a "
+                        "48 Mbp reference prefix; min_len 19",
+            "ms": round(t * 1e3, 3), "reads_per_s": round(rl.shape[0] / t, 1),
+            "smems": int(recs.shape[0]), "smems_per_s": round(recs.shape[0] / t, 1),
+            "timing": "median of 3 calls, wall clock around the synchronous C-ABI call (reads copied in, "
+                      "records copied out)",
+            "index_build_s": round(t_build, 2), "index_bytes": int(4 * n_ref),
+            "property_check": {"records_checked": int(pick.shape[0]), "failures": bad,
+                               "checks": "occurrence count in ref + revcomp(ref), no extension by one base "
+                                         "to the right or to the left"},
+            "cpu_oracle": None, "cpu_oracle_note": "the oracle's suffix array of a 96 Mbp text by prefix "
+                                                   "doubling does not fit a bench run; parity is tested on "
+                                                   "small references in tests/test_gpu_smem.py"}
+
+
 def pinned_host_batch(bsw, hb):
     """Copy a HostBatch's arrays into pinned host memory (for the end-to-end leg)."""
     import torch
@@ -530,6 +590,9 @@ def run_gb300(args):
     sal_line = None
     if rank == 0 and not args.no_sal and args.config == "read151" and args.pairs is None:
         sal_line = sal_leg(bsw, args, stream, measured_peaks().get("hbm_gbs"))
+    smem_line = None
+    if rank == 0 and not args.no_smem and args.config == "read151" and args.pairs is None:
+        smem_line = smem_leg(bsw, args)
 
     if rank == 0:
         line = {
@@ -560,6 +623,7 @@ def run_gb300(args):
             "parity_sample": parity,
             "extension_driver": drv,
             "suffix_array_lookup": sal_line,
+            "smem_search": smem_line,
             "e2e": {"value": round(e2e, 3), "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(t_e2e * 1e3, 3), "bit_exact_vs_device": e2e_equal},
             "gpu_launches": launches_per_step * args.steps,
