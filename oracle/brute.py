@@ -8,7 +8,8 @@ Eq. 3, so the index bookkeeping of the one-row form is not shared.
 
 ``extend_full`` implements:
   * Eq. 2 with the readings R2 (zero diagonal -> M = 0) and R3 (E and F open
-    from M with cost o + e) of the oracle's header;
+    from M with cost o + e) of the oracle's header, and R11 (N, code 4,
+    scores -1 against any base);
   * Eq. 3 boundaries: H[-1,-1] = h0, first row max(0, h0 - o_ins - (j+1) e_ins),
     first column max(0, h0 - o_del - (i+1) e_del), E = F = 0 on entry;
   * optionally the static diagonal band (rule a, band width clipped by R1),
@@ -91,7 +92,7 @@ def extend_full(params, Q: np.ndarray, T: np.ndarray, H0: np.ndarray, band: bool
                 d = left(i - 1)
             else:
                 d = H[i - 1, j - 1] if in_band(i - 1, j - 1) else np.zeros(B, np.int64)
-            sc = np.where(Q[:, j] == T[:, i], s.match, -s.mismatch)
+            sc = np.where((Q[:, j] > 3) | (T[:, i] > 3), -1, np.where(Q[:, j] == T[:, i], s.match, -s.mismatch))
             M = np.where(d > 0, d + sc, 0)
             e = E[i, j] if (i == 0 or in_band(i - 1, j)) else np.zeros(B, np.int64)
             h = np.maximum(M, np.maximum(e, F))
@@ -225,7 +226,7 @@ def extend_trimmed(params, Q: np.ndarray, T: np.ndarray, H0: np.ndarray, zdrop: 
             hv, ev = slot(rr, j)
             d = np.where(never, top_slot(j), hv)
             e = np.where(never, 0, ev)
-            sc = np.where(Q[:, j] == T[:, i], s.match, -s.mismatch)
+            sc = np.where((Q[:, j] > 3) | (T[:, i] > 3), -1, np.where(Q[:, j] == T[:, i], s.match, -s.mismatch))
             M = np.where(d > 0, d + sc, 0)
             h = np.maximum(M, np.maximum(e, F))
             H[i, j] = np.where(inb, h, 0)

@@ -30,7 +30,9 @@
  *   R5 z-drop with the diagonal-offset gap correction;
  *   R6 band growth of +2 reads row entries written by earlier rows;
  *   R7 empty query -> {h0, 0, 0, 0, h0, 0}; empty target -> {h0, 0, 0, 0, -1, 0};
- *   R8 rows walk the target, columns walk the query.
+ *   R8 rows walk the target, columns walk the query;
+ *   R11 an N (code 4; the paper's alphabet has four bases) scores -1 against
+ *       any base, N included, as BWA-MEM scores it.
  * Rows are target positions i (deletion penalties on vertical moves), columns
  * are query positions j (insertion penalties on horizontal moves).
  *
@@ -85,7 +87,8 @@ int orc_band_width(const orc_params_t *P, int32_t n, int32_t w)
 }
 
 /*
- * One extension.  q: query codes (n), t: target codes (m), both 0..3.
+ * One extension.  q: query codes (n), t: target codes (m), both 0..3 (A, C, G, T)
+ * or 4 (N, R11).
  * Returns 0, or -1 if memory runs out.  cells counts the (i, j) updates made;
  * stale_nz counts reads of row entries that the previous row did not write
  * and that hold a non-zero value (R6).
@@ -146,7 +149,9 @@ int orc_extend_one(const orc_params_t *P, int32_t n, const uint8_t *q, int32_t m
             if (i > 0 && j > prev_hi && (d != 0 || e != 0)) ++nstale;
             Hp[j] = hl;                               /* H(i, j-1), for row i+1 */
             /* Eq. 2 with R2: a zero diagonal is unreached. */
-            int32_t M = d > 0 ? d + (q[j] == ti ? a : -b) : 0;
+            /* R11: N (code 4) scores -1 against any base, N included. */
+            const int32_t sc = (q[j] > 3 || ti > 3) ? -1 : (q[j] == ti ? a : -b);
+            int32_t M = d > 0 ? d + sc : 0;
             int32_t h = imax(M, imax(e, f));
             hl = h;
             if (h >= rm) rj = j;                      /* R4: ties -> larger j */

@@ -344,3 +344,45 @@ def test_generator_deterministic():
     for k in ("q", "q_off", "q_len", "t", "t_off", "t_len", "h0"):
         np.testing.assert_array_equal(getattr(a, k), getattr(b, k))
     assert a.q.max() <= 3 and a.t.max() <= 3
+
+
+def test_n_scores_minus_one():
+    """R11 by hand: one cell, h0 = 10.  Against N (either side, or both) the
+    cell gets M = 10 - 1 = 9 < h0, so the best stays h0 at (0, 0) and the
+    query end is reached with 9 at row 0: {10, 0, 0, 1, 9, 0}.  A match
+    gives 11 instead."""
+    for q, t in ((4, 4), (4, 0), (0, 4), (2, 4)):
+        got, _, _ = _oracle_grid([[q]], [[t]], [10], oracle.NO_BAND | oracle.NO_TRIM | oracle.NO_ZDROP)
+        assert got[0].tolist() == [10, 0, 0, 1, 9, 0], (q, t, got[0])
+    got, _, _ = _oracle_grid([[2]], [[2]], [10], 0)
+    assert got[0].tolist() == [11, 1, 1, 1, 11, 0]
+
+
+def test_all_n_diagonal():
+    """A query of n N's against a target of N's: along the diagonal H drops by
+    1 per cell (the gaps cost more), so the best stays h0 and the query end is
+    first reached at row n - 1 with h0 - n."""
+    n, h0 = 6, 20
+    got, _, _ = _oracle_grid([[4] * n], [[4] * (n + 4)], [h0], 0)
+    assert got[0][0] == h0 and got[0][1] == 0
+    assert got[0][4] == h0 - n and got[0][3] >= n
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (3, 5), (5, 3), (6, 8), (8, 8)])
+def test_brute_random_small_with_n(n, m):
+    """Codes 0..4 (N) on both sides: the one-row sweep equals the full-matrix
+    DP, each applying R11 on its own."""
+    rng = np.random.default_rng(n * 53 + m)
+    B = 3000
+    Q = rng.integers(0, 4, (B, n))
+    T = rng.integers(0, 4, (B, m))
+    half = B // 2
+    k = min(n, m)
+    T[:half, :k] = Q[:half, :k]
+    Q = np.where(rng.random((B, n)) < 0.15, 4, Q)
+    T = np.where(rng.random((B, m)) < 0.15, 4, T)
+    H0 = rng.integers(0, 20, B)
+    got, _, _ = _oracle_grid(Q, T, H0, oracle.NO_BAND | oracle.NO_TRIM | oracle.NO_ZDROP)
+    np.testing.assert_array_equal(got, brute.extend_full(P, Q, T, H0))
+    got, _, _ = _oracle_grid(Q, T, H0, 0)
+    np.testing.assert_array_equal(got, brute.extend_trimmed(P, Q, T, H0))
