@@ -97,7 +97,19 @@ typedef struct {
     const int32_t *h0;         /* [n_pairs] seed score, >= 0                      */
     const int32_t *w_override; /* [n_pairs] per-pair band, or NULL for the ctx w  */
     uint32_t flags;            /* BSW_* flags above                               */
+    const uint8_t *q_n;        /* N bitmap of q, or NULL (no N): bit p & 7 of     */
+    const uint8_t *t_n;        /* byte p >> 3 marks base p as N (see below)       */
 } bsw_batch_t;
+
+/*
+ * N bases: the 2-bit codes hold A, C, G, T only.  q_n / t_n (nullable, same
+ * pointer kind as q / t) mark bases as N; an N scores -1 against any base, N
+ * included (BWA-MEM's rule; the paper's alphabet has four bases), and the
+ * base's 2-bit code is ignored.  Pairs with an N run in the 8-bit per-thread
+ * kernels when their scores fit, else in the 32-bit warp-per-pair kernel.
+ * bsw_pack_2bit_n packs text with N.  The serving calls (bsw_stream_submit)
+ * take no N bitmaps.
+ */
 
 /*
  * Create a context.  sc: scoring (copied); w >= 0: band half-width before the
@@ -177,6 +189,13 @@ void bsw_destroy(bsw_ctx_t *ctx);
  * byte (out is then unspecified).
  */
 int bsw_pack_2bit(const uint8_t *in, int64_t n, uint8_t *out);
+
+/*
+ * As bsw_pack_2bit, also accepting N (code 4 or the letters N/n): N is
+ * packed as code 0 and marked in out_n[(n + 7) / 8] (bit p & 7 of byte
+ * p >> 3 for base p; other bits 0).  Returns BSW_OK or BSW_EINVAL.
+ */
+int bsw_pack_2bit_n(const uint8_t *in, int64_t n, uint8_t *out, uint8_t *out_n);
 
 /*
  * The band half-width after the gap-limit clip for a query of qlen bases:

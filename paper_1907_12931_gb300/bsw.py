@@ -60,7 +60,8 @@ class bsw_batch_t(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64),
                 ("q", ctypes.c_void_p), ("q_off", ctypes.c_void_p), ("q_len", ctypes.c_void_p),
                 ("t", ctypes.c_void_p), ("t_off", ctypes.c_void_p), ("t_len", ctypes.c_void_p),
-                ("h0", ctypes.c_void_p), ("w_override", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+                ("h0", ctypes.c_void_p), ("w_override", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+                ("q_n", ctypes.c_void_p), ("t_n", ctypes.c_void_p)]
 
 
 class bsw_plan_t(ctypes.Structure):
@@ -123,6 +124,8 @@ def lib():
             L.bsw_destroy.restype = None
             L.bsw_pack_2bit.argtypes = [vp, i64, vp]
             L.bsw_pack_2bit.restype = ctypes.c_int
+            L.bsw_pack_2bit_n.argtypes = [vp, i64, vp, vp]
+            L.bsw_pack_2bit_n.restype = ctypes.c_int
             L.bsw_band_width.argtypes = [vp, i32, i32]
             L.bsw_band_width.restype = i32
             L.bsw_extend_batch_noalloc.argtypes = [ctypes.POINTER(bsw_scoring_t), i32, i32, i32,
@@ -219,6 +222,25 @@ def bsw_pack_2bit(codes: np.ndarray) -> np.ndarray:
     return out
 
 
+def bsw_pack_2bit_n(codes: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Codes 0..4 (4 = N): the 2-bit packing and the N bitmap."""
+    codes = np.ascontiguousarray(codes, np.uint8)
+    out = np.zeros((codes.shape[0] + 3) // 4, np.uint8)
+    nm = np.zeros((codes.shape[0] + 7) // 8, np.uint8)
+    rc = lib().bsw_pack_2bit_n(codes.ctypes.data, codes.shape[0], out.ctypes.data, nm.ctypes.data)
+    if rc != BSW_OK:
+        raise BswError(rc, "bsw_pack_2bit_n")
+    return out, nm
+
+
+def _pack(codes: np.ndarray):
+    """Packed codes and an N bitmap, or None when there is no N."""
+    codes = np.ascontiguousarray(codes, np.uint8)
+    if codes.size and int(codes.max()) > 3:
+        return bsw_pack_2bit_n(codes)
+    return bsw_pack_2bit(codes), None
+
+
 def bsw_band_width(ctx: int, qlen: int, w: int) -> int:
     return int(lib().bsw_band_width(ctx, int(qlen), int(w)))
 
@@ -278,8 +300,8 @@ class HostBatch:
     """Packed, host-resident inputs of a workload (numpy arrays kept alive)."""
 
     def __init__(self, wl, w_override=None, flags: int = 0):
-        self.q = bsw_pack_2bit(wl.q)
-        self.t = bsw_pack_2bit(wl.t)
+        self.q, self.q_n = _pack(wl.q)
+        self.t, self.t_n = _pack(wl.t)
         # own copies: the caller's arrays are never aliased
         self.q_off = np.array(wl.q_off, np.int64, copy=True, order="C")
         self.q_len = np.array(wl.q_len, np.int32, copy=True, order="C")
@@ -294,10 +316,13 @@ class HostBatch:
         f = self.flags if flags is None else flags
         return bsw_batch_t(self.n, self.q.ctypes.data, self.q_off.ctypes.data, self.q_len.ctypes.data,
                            self.t.ctypes.data, self.t_off.ctypes.data, self.t_len.ctypes.data,
-                           self.h0.ctypes.data, None if self.w is None else self.w.ctypes.data, f)
+                           self.h0.ctypes.data, None if self.w is None else self.w.ctypes.data, f,
+                           None if self.q_n is None else self.q_n.ctypes.data,
+                           None if self.t_n is None else self.t_n.ctypes.data)
 
     def nbytes(self) -> int:
-        return sum(a.nbytes for a in (self.q, self.t, self.q_off, self.q_len, self.t_off, self.t_len, self.h0))
+        return sum(a.nbytes for a in (self.q, self.t, self.q_off, self.q_len, self.t_off, self.t_len, self.h0,
+                                      self.q_n, self.t_n) if a is not None)
 
 
 class DeviceBatch:
@@ -314,13 +339,17 @@ class DeviceBatch:
         self.t_len = torch.from_numpy(hb.t_len).to(device)
         self.h0 = torch.from_numpy(hb.h0).to(device)
         self.w = None if hb.w is None else torch.from_numpy(hb.w).to(device)
+        self.q_n = None if hb.q_n is None else torch.from_numpy(hb.q_n).to(device)
+        self.t_n = None if hb.t_n is None else torch.from_numpy(hb.t_n).to(device)
         self.out = torch.zeros((self.n, 6), dtype=torch.int32, device=device)
         self.cells = torch.zeros(1, dtype=torch.int64, device=device)
 
     def struct(self, flags: int = 0) -> bsw_batch_t:
         return bsw_batch_t(self.n, self.q.data_ptr(), self.q_off.data_ptr(), self.q_len.data_ptr(),
                            self.t.data_ptr(), self.t_off.data_ptr(), self.t_len.data_ptr(), self.h0.data_ptr(),
-                           None if self.w is None else self.w.data_ptr(), flags | BSW_DEVICE_PTRS)
+                           None if self.w is None else self.w.data_ptr(), flags | BSW_DEVICE_PTRS,
+                           None if self.q_n is None else self.q_n.data_ptr(),
+                           None if self.t_n is None else self.t_n.data_ptr())
 
 
 class Context:

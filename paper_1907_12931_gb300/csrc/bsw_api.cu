@@ -231,14 +231,21 @@ int check_host_batch(const bsw_batch_t *b, const Params &P, Extents *x)
 
 // Device layout of a staged batch.
 struct IoLayout {
-    size_t q, t, q_off, q_len, t_off, t_len, h0, w, out, cells, status, in_end, total;
+    size_t q, t, q_off, q_len, t_off, t_len, h0, w, out, cells, status, in_end, total, qn, tn;
 };
 
-IoLayout io_layout(int64_t N, int64_t qbytes, int64_t tbytes)
+// N bitmap bytes staged for packed bytes [lo, hi) (two packed bytes per
+// bitmap byte; the first bitmap byte holds packed byte lo's bases).
+inline int64_t nmask_lo(int64_t lo) { return lo / 2; }
+inline int64_t nmask_bytes(int64_t lo, int64_t hi) { return hi > lo ? (hi + 1) / 2 - lo / 2 : 0; }
+
+IoLayout io_layout(int64_t N, int64_t qbytes, int64_t tbytes, int64_t qnbytes = 0, int64_t tnbytes = 0)
 {
     IoLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    L.qn = take((size_t)qnbytes);
+    L.tn = take((size_t)tnbytes);
     L.q = take((size_t)qbytes);
     L.t = take((size_t)tbytes);
     L.q_off = take(8 * (size_t)N);
@@ -347,7 +354,7 @@ bool same_batch(const bsw_batch_t &a, const bsw_batch_t &b)
 {
     return a.n_pairs == b.n_pairs && a.q == b.q && a.q_off == b.q_off && a.q_len == b.q_len && a.t == b.t &&
            a.t_off == b.t_off && a.t_len == b.t_len && a.h0 == b.h0 && a.w_override == b.w_override &&
-           a.flags == b.flags;
+           a.flags == b.flags && a.q_n == b.q_n && a.t_n == b.t_n;
 }
 
 // Enqueue one launch of a device-resident batch on the lane's streams (S.main
@@ -399,7 +406,8 @@ int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B
     if (rc != BSW_OK) return rc;
     const int64_t N = b->n_pairs;
     const int64_t qbytes = x.q_hi - x.q_lo, tbytes = x.t_hi - x.t_lo;
-    IoLayout L = io_layout(N, qbytes, tbytes);
+    const int64_t qnb = b->q_n ? nmask_bytes(x.q_lo, x.q_hi) : 0, tnb = b->t_n ? nmask_bytes(x.t_lo, x.t_hi) : 0;
+    IoLayout L = io_layout(N, qbytes, tbytes, qnb, tnb);
     Lane &lane = c->sync;
     bool moved = false;
     if ((rc = lane.io.reserve(L.total, c->budget, &moved)) != BSW_OK) return rc;
@@ -416,14 +424,17 @@ int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B
         {L.q, b->q + x.q_lo, (size_t)qbytes}, {L.t, b->t + x.t_lo, (size_t)tbytes},
         {L.q_off, b->q_off, 8 * (size_t)N}, {L.q_len, b->q_len, 4 * (size_t)N},
         {L.t_off, b->t_off, 8 * (size_t)N}, {L.t_len, b->t_len, 4 * (size_t)N},
-        {L.h0, b->h0, 4 * (size_t)N}, {L.w, b->w_override, b->w_override ? 4 * (size_t)N : 0}};
+        {L.h0, b->h0, 4 * (size_t)N}, {L.w, b->w_override, b->w_override ? 4 * (size_t)N : 0},
+        {L.qn, b->q_n ? b->q_n + nmask_lo(x.q_lo) : nullptr, (size_t)qnb},
+        {L.tn, b->t_n ? b->t_n + nmask_lo(x.t_lo) : nullptr, (size_t)tnb}};
     for (const Cp &cp : cps)
         if (cp.bytes && (e = cudaMemcpyAsync(d + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_rc(e);
     *out_B = Batch{N, d + L.q - x.q_lo, (const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len),
                    d + L.t - x.t_lo, (const int64_t *)(d + L.t_off), (const int32_t *)(d + L.t_len),
                    (const int32_t *)(d + L.h0), b->w_override ? (const int32_t *)(d + L.w) : nullptr,
-                   (bsw_result_t *)(d + L.out)};
+                   (bsw_result_t *)(d + L.out), b->q_n ? d + L.qn - nmask_lo(x.q_lo) : nullptr,
+                   b->t_n ? d + L.tn - nmask_lo(x.t_lo) : nullptr};
     *out_L = L;
     return BSW_OK;
 }
@@ -462,7 +473,7 @@ int extend_device(bsw_ctx *c, const bsw_batch_t *b, bsw_result_t *out, int64_t *
     if (rc != BSW_OK) return rc;
     if (moved) clear_graphs(c);
     cudaStream_t st = user ? user : lane.S.main;
-    Batch B{N, b->q, b->q_off, b->q_len, b->t, b->t_off, b->t_len, b->h0, b->w_override, out};
+    Batch B{N, b->q, b->q_off, b->q_len, b->t, b->t_off, b->t_len, b->h0, b->w_override, out, b->q_n, b->t_n};
     Work W = make_work(lane.work.p, lane.wl);
     if (cells_out) W.cells = (unsigned long long *)cells_out;
     cudaError_t e;
@@ -703,6 +714,26 @@ int bsw_pack_2bit(const uint8_t *in, int64_t n, uint8_t *out)
     return BSW_OK;
 }
 
+int bsw_pack_2bit_n(const uint8_t *in, int64_t n, uint8_t *out, uint8_t *out_n)
+{
+    if (n < 0 || (n > 0 && (!in || !out || !out_n))) return BSW_EINVAL;
+    for (int64_t k = 0; k < (n + 3) / 4; ++k) out[k] = 0;
+    for (int64_t k = 0; k < (n + 7) / 8; ++k) out_n[k] = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int v;
+        switch (in[k]) {
+        case 0: case 'A': case 'a': v = 0; break;
+        case 1: case 'C': case 'c': v = 1; break;
+        case 2: case 'G': case 'g': v = 2; break;
+        case 3: case 'T': case 't': v = 3; break;
+        case 4: case 'N': case 'n': v = 0; out_n[k >> 3] |= (uint8_t)(1u << (k & 7)); break;
+        default: return BSW_EINVAL;
+        }
+        out[k >> 2] |= (uint8_t)(v << (2 * (k & 3)));
+    }
+    return BSW_OK;
+}
+
 int32_t bsw_band_width(const bsw_ctx_t *ctx, int32_t qlen, int32_t w)
 {
     if (!ctx || qlen < 0 || w < 0) return -1;
@@ -793,6 +824,7 @@ int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, u
     if (b->flags & (BSW_DEVICE_PTRS | BSW_PLAIN_KERNEL | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32 |
                     BSW_TIME_KERNELS))
         return BSW_EINVAL;   // the serving loop runs the context's batched plan on host inputs
+    if (b->q_n || b->t_n) return BSW_EINVAL;   // no N bitmaps in the serving loop
     if (b->n_pairs > 0 && (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out))
         return BSW_EINVAL;
     Request *r = new (std::nothrow) Request();
@@ -925,7 +957,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         if (moved) clear_graphs(ctx);
         if ((rc = lane.io.reserve(sizeof(bsw_result_t) * (size_t)ns, ctx->budget)) != BSW_OK) return rc;
         B = Batch{ns, sb.q, sb.q_off, sb.q_len, sb.t, sb.t_off, sb.t_len, sb.h0, sb.w_override,
-                  (bsw_result_t *)lane.io.p};
+                  (bsw_result_t *)lane.io.p, sb.q_n, sb.t_n};
     } else {
         IoLayout L;
         if ((rc = stage_host(ctx, &sb, nullptr, &B, &L)) != BSW_OK) return rc;

@@ -62,6 +62,9 @@ struct Batch {
     const int32_t *h0;
     const int32_t *w_override;
     bsw_result_t *out;
+    // N bitmaps (nullable): bit (p & 7) of byte p >> 3 marks base p of q / t
+    // as N, which scores -1 against any base
+    const uint8_t *q_n, *t_n;
 };
 
 // Device scratch for one batch launch (allocated and owned by the host runtime).

@@ -62,11 +62,18 @@ __device__ __forceinline__ void store_result(bsw_result_t *out, int score, int q
 
 // ------------------------------------------------------------------ bucketing
 
-__device__ __forceinline__ int pick_bin(int n, long long bound, uint32_t flags, int short_max, int h0)
+__device__ __forceinline__ int pick_bin(int n, long long bound, uint32_t flags, int short_max, int h0, bool has_n)
 {
     const int u8 = kBinU8 + (kShortMax - n) * kU8H0Buckets + (kU8H0Buckets - 1 - min(h0 >> 4, kU8H0Buckets - 1));
     const int rank = 639 - min(n >> 6, 639);
     if (flags & BSW_FORCE_I32) return kBinW32 + rank;
+    // Pairs with an N base: the 8-bit per-thread kernels score N, the 32-bit
+    // warp kernel does; the 16-bit and packed kernels do not take them.
+    if (has_n) {
+        const bool f8 = (flags & BSW_FORCE_I8) != 0;
+        if (!(flags & BSW_FORCE_I16) && n <= (f8 ? kShortMax : short_max) && (f8 || bound <= 255)) return u8;
+        return kBinW32 + rank;
+    }
     // The forced lane widths are test modes: they keep every query up to
     // kShortMax on the per-thread kernels whatever the plan says.
     if (n <= ((flags & (BSW_FORCE_I8 | BSW_FORCE_I16)) ? kShortMax : short_max)) {
@@ -77,6 +84,30 @@ __device__ __forceinline__ int pick_bin(int n, long long bound, uint32_t flags, 
         return kBinW32 + rank;
     }
     return bound <= 32767 ? kBinW16 + rank : kBinW32 + rank;
+}
+
+// Whether bases [off, off + len) of an N bitmap hold an N.
+__device__ __forceinline__ bool range_has_n(const uint8_t *nm, int64_t off, int len)
+{
+    if (!nm || len <= 0) return false;
+    const int64_t a = off, b = off + len;                 // bits [a, b)
+    for (int64_t byte = a >> 3; byte <= (b - 1) >> 3; ++byte) {
+        uint32_t v = __ldg(nm + byte);
+        if (byte == (a >> 3)) v &= 0xffu << (a & 7);
+        if (byte == ((b - 1) >> 3)) v &= 0xffu >> (7 - ((b - 1) & 7));
+        if (v) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool pair_has_n(const Batch &B, int64_t qo, int n, int64_t to, int m)
+{
+    return range_has_n(B.q_n, qo, n) || range_has_n(B.t_n, to, m);
+}
+
+__device__ __forceinline__ int n_bit(const uint8_t *nm, int64_t pos)
+{
+    return (__ldg(nm + (pos >> 3)) >> (pos & 7)) & 1;
 }
 
 // Validate each pair, answer the empty ones, and histogram the rest by bin.
@@ -101,7 +132,7 @@ __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
             const long long bound = (long long)h0 + (long long)P.a * min(n, m);
             if (bound >= (1ll << 30)) atomicOr(W.status, kStInval);
             else if (n > P.max_qlen) atomicOr(W.status, kStTooLong);
-            else key = pick_bin(n, bound, P.flags, P.short_max, h0);
+            else key = pick_bin(n, bound, P.flags, P.short_max, h0, pair_has_n(B, qo, n, to, m));
         }
         W.key[p] = key;
         if (key >= 0) atomicAdd(&sh[key], 1u);
@@ -238,18 +269,23 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
     }
 
     // Eq. 3, first row: H = h0 at column 0, max(0, h0 - o_ins - c*e_ins) after.
-    const uint8_t *qp = B.q + (B.q_off[p] >> 2);
+    // 8-bit lanes: an N column gets the selector of byte 4 (the -1 profile).
+    const int64_t q_off = B.q_off[p];
+    const uint8_t *qp = B.q + (q_off >> 2);
     for (int c = 0; c <= n; c += 4) {
         const uint32_t byte = c < n ? __ldg(qp + (c >> 2)) : 0u;
+        const uint32_t nb = (U8 && B.q_n && c < n) ? (uint32_t)__ldg(B.q_n + ((q_off + c) >> 3)) >> ((q_off + c) & 7) : 0u;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int j = c + k;
             if (j <= n) {
                 const int hv = j == 0 ? h0 : max(0, h0 - P.o_ins - j * e_ins);
-                S[j * 32] = slot_init<U8>((byte >> (2 * k)) & 3, hv);
+                S[j * 32] = slot_init<U8>((nb >> k) & 1 ? 4 : (byte >> (2 * k)) & 3, hv);
             }
         }
     }
+    const uint8_t *tn = U8 ? B.t_n : nullptr;
+    const int64_t t_off = B.t_off[p];
 
     const uint8_t *tp = B.t + (B.t_off[p] >> 2);
     const uint32_t mb8 = (uint32_t)(-P.b) & 0xffu;
@@ -268,7 +304,8 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
         int hl = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
         int f = 0, key = 0;   // key = H*256 + j (j < 256): its max is the row max, ties to larger j
         if (U8) {
-            const uint32_t prof = mis4 ^ (flip << (8 * tb));   // byte c: score of (t_i, c)
+            // byte c: score of (t_i, c); all -1 for an N row (byte 4, N columns, is -1 too)
+            const uint32_t prof = (tn && n_bit(tn, t_off + i)) ? 0xffffffffu : mis4 ^ (flip << (8 * tb));
             const uint32_t k8 = P.k8;
             // E is loaded as a byte before the word: a byte load issued after
             // the word load would be folded into a shift and mask of the word
@@ -280,7 +317,7 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
                 for (int j = lo; j < hi; ++j) {
                     const int e = SE[j * 128];                                 // E(i, j)
                     const uint32_t wv = S[j * 32];
-                    const int sc = (int)prmt(prof, 0u, wv);
+                    const int sc = (int)prmt(prof, 0xffffffffu, wv);
                     const int d = (int)(wv >> 24);                             // H(i-1, j-1)
                     const int M = __viaddmin_s32(d, sc, (int)((uint32_t)d * k8));   // d > 0 ? d + sc : <= 0
                     const int h = __vimax3_s32(M, e, f);                       // Eq. 2
@@ -296,7 +333,7 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
                 for (int j = lo; j < hi; ++j) {
                     const int e = SE[j * 128];
                     const uint32_t wv = S[j * 32];
-                    const int sc = (int)prmt(prof, 0u, wv);
+                    const int sc = (int)prmt(prof, 0xffffffffu, wv);
                     const int d = (int)(wv >> 24);
                     const int M = __viaddmin_s32(d, sc, (int)((uint32_t)d * k8));
                     const int h = __vimax3_s32(M, e, f);
@@ -727,7 +764,8 @@ template <> struct SlotIO<false> {
 // can still be read, including the band-regrowth reads of earlier rows'
 // values.  Columns never written before get their first-row value of Eq. 3
 // when the band first reaches them (hw is the highest column set so far).
-template <int C, bool S16, bool RING>
+// NM: the batch has N bitmaps; an N on either side scores -1.
+template <int C, bool S16, bool RING, bool NM = false>
 __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, uint8_t *slots, int mask)
 {
     using IO = SlotIO<S16>;
@@ -753,6 +791,7 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
     unsigned long long ncell = 0;
     for (int i = 0; i < m; ++i) {
         const int tb = (__ldg(tp + (i >> 2)) >> (2 * (i & 3))) & 3;
+        const bool tn = NM && B.t_n && n_bit(B.t_n, B.t_off[p] + i);
         lo = max(lo, i - wb);
         hi = min(min(hi, i + wb + 1), n);
         if (RING && hi - 1 > hw) {             // first visit of columns (hw, hi-1]
@@ -769,7 +808,7 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
             int M[C], E0[C], Fl[C], H[C];
             bool act[C];
             int cnt = 0, floc = 0;
-            uint32_t qbits = 0;
+            uint32_t qbits = 0, nq = 0;
             if (j0 < hi && j0 + C > lo) {
 #pragma unroll
                 for (int k = 0; k < C; k += 4) {
@@ -777,6 +816,16 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
                     if (j0 + k < n) qbits |= (uint32_t)__ldg(B.q + (pos >> 2)) << (2 * k);
                 }
                 if (C < 4) qbits >>= 2 * ((qoff + j0) & 3);
+                if (NM && B.q_n) {                       // N bits of the lane's columns
+                    const int64_t pos = qoff + j0;
+                    const int bits = (int)(pos & 7) + min(C, n - j0);   // bitmap bits up to the last column
+                    const uint8_t *src = B.q_n + (pos >> 3);
+                    uint32_t w = __ldg(src);
+#pragma unroll
+                    for (int b = 1; b <= (C + 7) / 8; ++b)
+                        if (8 * b < bits) w |= (uint32_t)__ldg(src + b) << (8 * b);
+                    nq = w >> (pos & 7);
+                }
             }
 #pragma unroll
             for (int k = 0; k < C; ++k) {
@@ -784,7 +833,8 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
                 act[k] = j >= lo && j < hi;
                 int d = 0, e = 0;
                 if (act[k]) IO::load(slots, at(j), d, e);
-                const int sc = (int)((qbits >> (2 * k)) & 3u) == tb ? a : mb;
+                int sc = (int)((qbits >> (2 * k)) & 3u) == tb ? a : mb;
+                if (NM && (tn || ((nq >> k) & 1u))) sc = -1;
                 M[k] = d > 0 ? d + sc : 0;
                 E0[k] = e;
                 Fl[k] = floc;
@@ -1159,8 +1209,11 @@ __global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2) k_warp(B
                     cells += P.o_del == P.o_ins && P.e_del == P.e_ins
                                  ? warp_pair_ring16<C, true>(B, P, p, RH, RE, need - 1)
                                  : warp_pair_ring16<C, false>(B, P, p, RH, RE, need - 1);
+                } else if (B.q_n || B.t_n) {
+                    cells += warp_pair<C, false, true, true>(B, P, p, ring, need - 1);
+                } else {
+                    cells += warp_pair<C, false, true, false>(B, P, p, ring, need - 1);
                 }
-                else cells += warp_pair<C, S16, true>(B, P, p, ring, need - 1);
                 continue;
             }
         }
@@ -1168,7 +1221,8 @@ __global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2) k_warp(B
             if (lane == 0) atomicOr(W.status, kStTooLong);
             continue;
         }
-        cells += warp_pair<C, S16, false>(B, P, p, slots, 0);
+        if (!S16 && (B.q_n || B.t_n)) cells += warp_pair<C, S16, false, true>(B, P, p, slots, 0);
+        else cells += warp_pair<C, S16, false, false>(B, P, p, slots, 0);
     }
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
@@ -1204,7 +1258,11 @@ __global__ void __launch_bounds__(256) k_plain(Batch B, Params P, Work W)
             if (lane == 0) atomicOr(W.status, kStTooLong);
             continue;
         }
-        cells += s16 ? warp_pair<1, true, false>(B, P, (int)p, slots, 0) : warp_pair<1, false, false>(B, P, (int)p, slots, 0);
+        if (B.q_n || B.t_n)
+            cells += s16 ? warp_pair<1, true, false, true>(B, P, (int)p, slots, 0)
+                         : warp_pair<1, false, false, true>(B, P, (int)p, slots, 0);
+        else
+            cells += s16 ? warp_pair<1, true, false>(B, P, (int)p, slots, 0) : warp_pair<1, false, false>(B, P, (int)p, slots, 0);
     }
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
@@ -1326,7 +1384,7 @@ template <int NMAX>
 cudaError_t launch_u8(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms, const Plan &L)
 {
     constexpr int N2 = NMAX > 64 ? 128 : NMAX > 32 ? 64 : 32;   // the packed kernel's sizes
-    if (NMAX <= 128 && (L.packed || (P.flags & BSW_PACKED_PAIRS)) && inter2_scoring_ok(P)) {
+    if (NMAX <= 128 && (L.packed || (P.flags & BSW_PACKED_PAIRS)) && inter2_scoring_ok(P) && !B.q_n && !B.t_n) {
         const int blocks = sms * g_inter2_blocks[inter2_index<N2>()];
         k_inter2<N2><<<blocks, inter2_warps<N2>() * 32, inter2_smem<N2>(), st>>>(B, P, W, cls);
         return cudaGetLastError();

@@ -127,7 +127,8 @@ extern "C" int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int3
 
     Params P{sc->match, sc->mismatch, sc->o_del, sc->e_del, sc->o_ins, sc->e_ins, w, zdrop, end_bonus, b->flags,
              kNaMaxQlen, 1u << 8, 1u << 16, 1u << 24, kShortMax};
-    Batch B{b->n_pairs, b->q, b->q_off, b->q_len, b->t, b->t_off, b->t_len, b->h0, b->w_override, out};
+    Batch B{b->n_pairs, b->q, b->q_off, b->q_len, b->t, b->t_off, b->t_len, b->h0, b->w_override, out,
+            b->q_n, b->t_n};
     // The histogram, the cell count and the status word must start at zero;
     // the array keeps whatever the previous call left.
     if (cudaMemsetAsync(W.hist, 0, 4 * kNumBins, st) != cudaSuccess || cudaMemsetAsync(W.cells, 0, 8, st) != cudaSuccess ||

@@ -87,7 +87,7 @@ class Workload:
     """A batch of extension pairs.  Sequence k of q is q[q_off[k] : q_off[k] + q_len[k]]."""
     name: str
     params: Params
-    q: np.ndarray       # uint8 codes 0..3
+    q: np.ndarray       # uint8 codes 0..3 (4 = N)
     q_off: np.ndarray   # int64, in bases
     q_len: np.ndarray   # int32
     t: np.ndarray
@@ -192,9 +192,36 @@ def from_lists(queries, targets, h0s, params: Params | None = None, align: int =
 
 
 def encode(s: str) -> np.ndarray:
-    """ACGT string -> codes 0..3."""
-    lut = {"A": 0, "C": 1, "G": 2, "T": 3}
+    """ACGTN string -> codes 0..4 (4 = N)."""
+    lut = {"A": 0, "C": 1, "G": 2, "T": 3, "N": 4}
     return np.array([lut[ch] for ch in s.upper()], np.uint8)
+
+
+def inject_n(wl: Workload, q_rate: float, t_runs: float, seed: int, run_max: int = 40) -> Workload:
+    """A copy of wl with N bases (code 4): each query base becomes N with
+    probability q_rate (sequencer no-calls, scattered), and each target base
+    starts a run of 1..run_max N's with probability t_runs (assembly gaps in
+    the reference).  Padding between sequences is left as it was."""
+    rng = np.random.default_rng(seed)
+    q, t = wl.q.copy(), wl.t.copy()
+
+    def inside(off, ln, total):
+        m = np.zeros(total + 1, np.int64)
+        np.add.at(m, off, 1)
+        np.add.at(m, off + ln, -1)
+        return np.cumsum(m)[:total] > 0
+
+    qin = inside(wl.q_off, wl.q_len.astype(np.int64), q.shape[0])
+    q[qin & (rng.random(q.shape[0]) < q_rate)] = 4
+    tin = inside(wl.t_off, wl.t_len.astype(np.int64), t.shape[0])
+    starts = np.nonzero(tin & (rng.random(t.shape[0]) < t_runs))[0]
+    if starts.size:
+        lens = rng.integers(1, run_max + 1, starts.size)
+        cover = np.zeros(t.shape[0] + run_max + 1, np.int64)
+        np.add.at(cover, starts, 1)
+        np.add.at(cover, starts + lens, -1)
+        t[(np.cumsum(cover)[:t.shape[0]] > 0) & tin] = 4
+    return Workload(wl.name + "+N", wl.params, q, wl.q_off, wl.q_len, t, wl.t_off, wl.t_len, wl.h0)
 
 
 # ------------------------------------------------------------ seeds on reads

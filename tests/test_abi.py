@@ -53,6 +53,60 @@ def test_pack_2bit(lib):
     assert e.value.code == lib.BSW_EINVAL
 
 
+def test_pack_2bit_n(lib):
+    """N (code 4 or the letter) sets its bit in the bitmap and packs as 0;
+    the other codes pack as bsw_pack_2bit does."""
+    codes = np.array([0, 4, 2, 3, 4, 2, 1, 0, 4], np.uint8)
+    packed, nm = lib.bsw_pack_2bit_n(codes)
+    assert packed.tolist() == [0b11100000, 0b00011000, 0]
+    assert nm.tolist() == [0b00010010, 0b1]
+    p2, n2 = lib.bsw_pack_2bit_n(np.frombuffer(b"ANGTnGCAN", np.uint8))
+    np.testing.assert_array_equal(p2, packed)
+    np.testing.assert_array_equal(n2, nm)
+    rng = np.random.default_rng(1)
+    x = rng.integers(0, 5, 1003).astype(np.uint8)
+    p, m = lib.bsw_pack_2bit_n(x)
+    k = np.arange(1003)
+    back = (p[k // 4] >> (2 * (k % 4))) & 3
+    isn = (m[k // 8] >> (k % 8)) & 1
+    np.testing.assert_array_equal(isn, (x == 4).astype(np.uint8))
+    np.testing.assert_array_equal(back, np.where(x == 4, 0, x))
+    with pytest.raises(lib.BswError) as e:
+        lib.bsw_pack_2bit_n(np.array([0, 5], np.uint8))
+    assert e.value.code == lib.BSW_EINVAL
+
+
+def test_host_batch_carries_n_bitmaps(lib):
+    from paper_1907_12931_gb300 import workload as W
+    wl = W.from_lists([W.encode("ACGTN"), W.encode("ACGT")], [W.encode("ACGT"), W.encode("NNAC")], [5, 5], align=4)
+    hb = lib.HostBatch(wl)
+    assert hb.q_n is not None and hb.t_n is not None
+    s = hb.struct()
+    assert s.q_n == hb.q_n.ctypes.data and s.t_n == hb.t_n.ctypes.data
+    assert hb.q_n.tolist() == [0b10000, 0]                      # queries at 0 and 8, 16 bases in all
+    assert hb.t_n.tolist() == [0b110000, 0]                     # targets at 0 and 4, 12 bases
+    plain = lib.HostBatch(W.from_lists([W.encode("ACGT")], [W.encode("ACGT")], [5], align=4))
+    assert plain.q_n is None and plain.struct().q_n is None and plain.struct().t_n is None
+
+
+def test_inject_n_keeps_padding_and_rates():
+    from paper_1907_12931_gb300 import workload as W
+    wl = W.make("plain10k", n_pairs=2000)
+    nw = W.inject_n(wl, 0.01, 0.001, seed=3)
+    qin = np.zeros(wl.q.shape[0], bool)
+    for o, n in zip(wl.q_off, wl.q_len):
+        qin[o:o + n] = True
+    tin = np.zeros(wl.t.shape[0], bool)
+    for o, n in zip(wl.t_off, wl.t_len):
+        tin[o:o + n] = True
+    assert not (nw.q[~qin] == 4).any() and not (nw.t[~tin] == 4).any()
+    changed = nw.q != wl.q
+    assert (nw.q[changed] == 4).all() and (nw.t[nw.t != wl.t] == 4).all()
+    rate = (nw.q[qin] == 4).mean()
+    assert 0.007 < rate < 0.013
+    assert (nw.t[tin] == 4).mean() > 0.005
+
+
 def test_strerror_and_version(lib):
     assert lib.bsw_strerror(0) == "ok"
     assert "budget" in lib.bsw_strerror(lib.BSW_EBUDGET)
