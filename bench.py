@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--no-driver", action="store_true", help="skip the seed-extension driver leg")
     ap.add_argument("--no-sal", action="store_true", help="skip the suffix-array lookup leg")
     ap.add_argument("--no-smem", action="store_true", help="skip the SMEM search leg")
+    ap.add_argument("--no-nbases", action="store_true", help="skip the N-bases leg")
     ap.add_argument("--plan", default=None,
                     help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps (no autotune)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point")
@@ -331,6 +332,58 @@ def driver_leg(bsw, args):
                            "sample": "the first %d reads (%d seeds), %.2f s" % (nsub, k, tcpu)}}
 
 
+def n_bases_leg(bsw, wl, plan, gcups_no_n, stream):
+    """The headline workload with N bases: each query base an N with
+    probability 0.1 % (sequencer no-calls), each target base the start of a
+    run of 1-40 N's with probability 0.02 % (reference gaps).  Device inputs,
+    the same plan, timed with CUDA events on the stream; every pair checked
+    against the oracle, whose run on the host cores is also timed."""
+    import torch
+    from paper_1907_12931_gb300 import workload as W
+    import oracle
+    nw = W.inject_n(wl, 0.001, 0.0002, seed=77)
+    qn = np.concatenate([[0], np.cumsum(nw.q == 4)])
+    tn = np.concatenate([[0], np.cumsum(nw.t == 4)])
+    has_n = ((qn[nw.q_off + nw.q_len] - qn[nw.q_off]) > 0) | ((tn[nw.t_off + nw.t_len] - tn[nw.t_off]) > 0)
+    ctx = bsw.Context(nw.params, mem_budget_bytes=40 << 30)
+    ctx.set_plan(plan)
+    db = bsw.DeviceBatch(bsw.HostBatch(nw))
+    for _ in range(3):
+        ctx.extend_device(db, 0, stream.cuda_stream)
+    stream.synchronize()
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.extend_device(db, 0, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.sync(stream.cuda_stream)
+    cells = int(db.cells.item())
+    got = db.out.cpu().numpy()
+    ctx.extend_device(db, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH, stream.cuda_stream)
+    _, class_ms = ctx.kernel_times()
+    ctx.sync(stream.cuda_stream)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res, ocells, _ = oracle.extend_batch(nw, nthreads=cores)
+    tcpu = time.perf_counter() - t0
+    mism = int((res != got).any(axis=1).sum())
+    ctx.close()
+    gcups = cells / (ms * 1e-3) / 1e9
+    return {"workload": "%s with N: query bases N with p 0.001, target N runs of 1-40 starting with p 0.0002"
+                        % wl.name,
+            "pairs": nw.n_pairs, "pairs_with_n": int(has_n.sum()), "ms": round(ms, 4), "gcups": round(gcups, 3),
+            "vs_without_n": round(gcups / gcups_no_n, 4) if gcups_no_n else None,
+            "timing": "CUDA events on the stream, mean of %d calls, device inputs" % reps,
+            "class_ms_in_step": {bsw.CLASS_NAMES[c]: round(t, 4) for c, t in enumerate(class_ms) if t > 0},
+            "parity": {"pairs_checked": nw.n_pairs, "fields": 6, "mismatches": mism,
+                       "cells_equal": cells == int(ocells.sum())},
+            "cpu_oracle": {"gcups": round(int(ocells.sum()) / tcpu / 1e9, 4), "cores": cores,
+                           "sample": "all pairs once, %.2f s" % tcpu}}
+
+
 def sal_leg(bsw, args, stream, hbm_peak):
     """Suffix array lookup (Eq. 1) over 8,000,000 SA intervals of a 64 Mbp
     reference prefix: the uncompressed suffix array (256 MB, larger than L2)
@@ -584,6 +637,9 @@ def run_gb300(args):
         mism = int((res != out_batched).any(axis=1).sum())
         parity = {"pairs_checked": int(res.shape[0]), "fields": 6, "mismatches": mism}
 
+    nb_line = None
+    if rank == 0 and not args.no_nbases and args.config in ("read151", "read250") and args.pairs is None:
+        nb_line = n_bases_leg(bsw, wl, plan, gcups / world, stream)
     drv = None
     if rank == 0 and not args.no_driver and args.config == "read151" and args.pairs is None:
         drv = driver_leg(bsw, args)
@@ -621,6 +677,7 @@ def run_gb300(args):
                                        % (sms, f_mhz, LANE_OPS_PER_CLK_PER_SM)},
             "cpu_baseline": cpu,
             "parity_sample": parity,
+            "n_bases": nb_line,
             "extension_driver": drv,
             "suffix_array_lookup": sal_line,
             "smem_search": smem_line,

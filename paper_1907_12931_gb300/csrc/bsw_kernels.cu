@@ -91,12 +91,20 @@ __device__ __forceinline__ bool range_has_n(const uint8_t *nm, int64_t off, int 
 {
     if (!nm || len <= 0) return false;
     const int64_t a = off, b = off + len;                 // bits [a, b)
-    for (int64_t byte = a >> 3; byte <= (b - 1) >> 3; ++byte) {
-        uint32_t v = __ldg(nm + byte);
-        if (byte == (a >> 3)) v &= 0xffu << (a & 7);
-        if (byte == ((b - 1) >> 3)) v &= 0xffu >> (7 - ((b - 1) & 7));
-        if (v) return true;
-    }
+    const int64_t b0 = a >> 3, b1 = (b - 1) >> 3;         // first and last byte
+    auto masked = [&](int64_t byte, uint32_t v) {
+        if (byte == b0) v &= 0xffu << (a & 7);
+        if (byte == b1) v &= 0xffu >> (7 - ((b - 1) & 7));
+        return v;
+    };
+    if (masked(b0, __ldg(nm + b0))) return true;
+    int64_t byte = b0 + 1;
+    for (; byte <= b1 && (reinterpret_cast<uintptr_t>(nm + byte) & 7); ++byte)   // up to an 8-byte boundary
+        if (masked(byte, __ldg(nm + byte))) return true;
+    for (; byte + 8 <= b1; byte += 8)                    // 8 whole bytes strictly between b0 and b1
+        if (__ldg(reinterpret_cast<const unsigned long long *>(nm + byte)) != 0ull) return true;
+    for (; byte <= b1; ++byte)
+        if (masked(byte, __ldg(nm + byte))) return true;
     return false;
 }
 
@@ -108,6 +116,23 @@ __device__ __forceinline__ bool pair_has_n(const Batch &B, int64_t qo, int n, in
 __device__ __forceinline__ int n_bit(const uint8_t *nm, int64_t pos)
 {
     return (__ldg(nm + (pos >> 3)) >> (pos & 7)) & 1;
+}
+
+// The first i in [from, len) whose base off + i is marked in the N bitmap, or
+// len if none.
+__device__ __forceinline__ int next_n(const uint8_t *nm, int64_t off, int from, int len)
+{
+    if (!nm || from >= len) return len;
+    const int64_t a = off + from, b = off + len;          // bits [a, b)
+    for (int64_t byte = a >> 3; byte <= (b - 1) >> 3; ++byte) {
+        uint32_t v = __ldg(nm + byte);
+        if (byte == (a >> 3)) v &= 0xffu << (a & 7);
+        if (v) {
+            const int64_t pos = byte * 8 + __ffs(v) - 1;
+            return pos < b ? (int)(pos - off) : len;
+        }
+    }
+    return len;
 }
 
 // Validate each pair, answer the empty ones, and histogram the rest by bin.
@@ -132,7 +157,14 @@ __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
             const long long bound = (long long)h0 + (long long)P.a * min(n, m);
             if (bound >= (1ll << 30)) atomicOr(W.status, kStInval);
             else if (n > P.max_qlen) atomicOr(W.status, kStTooLong);
-            else key = pick_bin(n, bound, P.flags, P.short_max, h0, pair_has_n(B, qo, n, to, m));
+            else {
+                // an 8-bit pair stays in its bin with or without N: scan the
+                // N bitmaps only for the others
+                key = pick_bin(n, bound, P.flags, P.short_max, h0, false);
+                const bool u8 = key < kBinI16 && !(P.flags & BSW_FORCE_I16);
+                if (!u8 && (B.q_n || B.t_n) && pair_has_n(B, qo, n, to, m))
+                    key = pick_bin(n, bound, P.flags, P.short_max, h0, true);
+            }
         }
         W.key[p] = key;
         if (key >= 0) atomicAdd(&sh[key], 1u);
@@ -254,7 +286,9 @@ __device__ __forceinline__ bool slot_nonzero(uint32_t w)
 // Extend pair p; the calling thread owns the slot column S[0], S[32], ...
 // Returns the cells computed, or 0 after queueing the pair for the 32-bit
 // re-run when a score leaves the lane range.
-template <int NMAX, bool U8>
+// NM: the batch has N bitmaps (8-bit lanes only); kernels of batches without
+// them carry no N code.
+template <int NMAX, bool U8, bool NM>
 __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const Params &P, const Work &W,
                                                          int p, uint32_t *S)
 {
@@ -274,7 +308,7 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
     const uint8_t *qp = B.q + (q_off >> 2);
     for (int c = 0; c <= n; c += 4) {
         const uint32_t byte = c < n ? __ldg(qp + (c >> 2)) : 0u;
-        const uint32_t nb = (U8 && B.q_n && c < n) ? (uint32_t)__ldg(B.q_n + ((q_off + c) >> 3)) >> ((q_off + c) & 7) : 0u;
+        const uint32_t nb = (NM && B.q_n && c < n) ? (uint32_t)__ldg(B.q_n + ((q_off + c) >> 3)) >> ((q_off + c) & 7) : 0u;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int j = c + k;
@@ -284,7 +318,7 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
             }
         }
     }
-    const uint8_t *tn = U8 ? B.t_n : nullptr;
+    const uint8_t *tn = NM ? B.t_n : nullptr;
     const int64_t t_off = B.t_off[p];
 
     const uint8_t *tp = B.t + (B.t_off[p] >> 2);
@@ -296,7 +330,10 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
     unsigned long long ncell = 0;
     uint32_t tbyte = 0;
     for (int i = 0; i < m; ++i) {
-        if ((i & 3) == 0) tbyte = __ldg(tp + (i >> 2));
+        if ((i & 3) == 0) {
+            tbyte = __ldg(tp + (i >> 2));
+            if (NM && tn) tbyte |= (((uint32_t)__ldg(tn + ((t_off + i) >> 3)) >> ((t_off + i) & 7)) & 15u) << 8;
+        }
         const int tb = (tbyte >> (2 * (i & 3))) & 3;
         lo = max(lo, i - wb);
         hi = min(min(hi, i + wb + 1), n);
@@ -305,7 +342,8 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
         int f = 0, key = 0;   // key = H*256 + j (j < 256): its max is the row max, ties to larger j
         if (U8) {
             // byte c: score of (t_i, c); all -1 for an N row (byte 4, N columns, is -1 too)
-            const uint32_t prof = (tn && n_bit(tn, t_off + i)) ? 0xffffffffu : mis4 ^ (flip << (8 * tb));
+            uint32_t prof = mis4 ^ (flip << (8 * tb));
+            if (NM && ((tbyte >> (8 + (i & 3))) & 1u)) prof = 0xffffffffu;
             const uint32_t k8 = P.k8;
             // E is loaded as a byte before the word: a byte load issued after
             // the word load would be folded into a shift and mask of the word
@@ -394,7 +432,7 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
     return ncell;
 }
 
-template <int NMAX, bool U8>
+template <int NMAX, bool U8, bool NM = false>
 __global__ void __launch_bounds__(256) k_inter(Batch B, Params P, Work W, int cls)
 {
     extern __shared__ uint32_t smem[];
@@ -409,7 +447,7 @@ __global__ void __launch_bounds__(256) k_inter(Batch B, Params P, Work W, int cl
         g = __shfl_sync(kFull, g, 0);
         if (g >= ngroups) break;
         const int idx = (g << 5) + lane;
-        if (idx < count) cells += inter_pair<NMAX, U8>(B, P, W, W.order[start + idx], S);
+        if (idx < count) cells += inter_pair<NMAX, U8, NM>(B, P, W, W.order[start + idx], S);
         __syncwarp();
     }
     for (int d = 16; d > 0; d >>= 1) cells += __shfl_xor_sync(kFull, cells, d);
@@ -1312,6 +1350,7 @@ constexpr size_t kRingSmemMax = 96 * 1024;
 // Resident blocks per SM of each k_inter instantiation with 1, 2 and 4 warps
 // per block, set by prepare_kernels.
 int g_inter_blocks[12][3];
+int g_inter_blocks_n[8][3];     // the N-aware 8-bit instantiations
 
 int warps_index(int warps) { return warps <= 1 ? 0 : warps == 2 ? 1 : 2; }
 
@@ -1323,27 +1362,41 @@ template <int NMAX, bool U8> constexpr int inter_index()
               : 8 + (NMAX >= 256 ? 0 : NMAX >= 128 ? 1 : NMAX >= 64 ? 2 : 3);
 }
 
-template <int NMAX, bool U8>
-cudaError_t prepare_inter()
+template <int NMAX, bool U8, bool NM>
+cudaError_t prepare_inter_one(int *blocks)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_inter<NMAX, U8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_inter<NMAX, U8, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)inter_smem<NMAX, U8>(4));
     if (e != cudaSuccess) return e;
     for (int wi = 0; wi < 3; ++wi) {
         const int warps = 1 << wi;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inter<NMAX, U8>, warps * 32, inter_smem<NMAX, U8>(warps));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inter<NMAX, U8, NM>, warps * 32,
+                                                          inter_smem<NMAX, U8>(warps));
         if (e != cudaSuccess) return e;
-        g_inter_blocks[inter_index<NMAX, U8>()][wi] = nb > 0 ? nb : 1;
+        blocks[wi] = nb > 0 ? nb : 1;
     }
     return cudaSuccess;
 }
 
 template <int NMAX, bool U8>
+cudaError_t prepare_inter()
+{
+    cudaError_t e = prepare_inter_one<NMAX, U8, false>(g_inter_blocks[inter_index<NMAX, U8>()]);
+    if (e != cudaSuccess || !U8) return e;
+    return prepare_inter_one<NMAX, true, true>(g_inter_blocks_n[inter_index<NMAX, U8>()]);
+}
+
+template <int NMAX, bool U8>
 cudaError_t launch_inter(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms, int warps)
 {
-    const int blocks = sms * g_inter_blocks[inter_index<NMAX, U8>()][warps_index(warps)];
-    k_inter<NMAX, U8><<<blocks, warps * 32, inter_smem<NMAX, U8>(warps), st>>>(B, P, W, cls);
+    if (U8 && (B.q_n || B.t_n)) {
+        const int blocks = sms * g_inter_blocks_n[inter_index<NMAX, U8>()][warps_index(warps)];
+        k_inter<NMAX, true, true><<<blocks, warps * 32, inter_smem<NMAX, U8>(warps), st>>>(B, P, W, cls);
+    } else {
+        const int blocks = sms * g_inter_blocks[inter_index<NMAX, U8>()][warps_index(warps)];
+        k_inter<NMAX, U8, false><<<blocks, warps * 32, inter_smem<NMAX, U8>(warps), st>>>(B, P, W, cls);
+    }
     return cudaGetLastError();
 }
 

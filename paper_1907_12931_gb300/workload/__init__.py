@@ -197,30 +197,37 @@ def encode(s: str) -> np.ndarray:
     return np.array([lut[ch] for ch in s.upper()], np.uint8)
 
 
+def _draw_positions(off, ln, k, rng):
+    """k positions drawn uniformly, with replacement, from the bases of the
+    sequences [off, off + ln); also the sequence of each."""
+    ln = np.asarray(ln, np.int64)
+    cum = np.cumsum(ln)
+    total = int(cum[-1]) if cum.size else 0
+    if total == 0 or k == 0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    r = rng.integers(0, total, k)
+    i = np.searchsorted(cum, r, side="right")
+    return np.asarray(off, np.int64)[i] + r - (cum[i] - ln[i]), i
+
+
 def inject_n(wl: Workload, q_rate: float, t_runs: float, seed: int, run_max: int = 40) -> Workload:
-    """A copy of wl with N bases (code 4): each query base becomes N with
-    probability q_rate (sequencer no-calls, scattered), and each target base
-    starts a run of 1..run_max N's with probability t_runs (assembly gaps in
-    the reference).  Padding between sequences is left as it was."""
+    """A copy of wl with N bases (code 4): about a q_rate fraction of the
+    query bases become N, scattered (sequencer no-calls), and about a t_runs
+    fraction of the target bases start a run of 1..run_max N's, cut at the
+    target's end (assembly gaps in the reference).  Positions are drawn with
+    replacement; padding between sequences is left as it was."""
     rng = np.random.default_rng(seed)
     q, t = wl.q.copy(), wl.t.copy()
-
-    def inside(off, ln, total):
-        m = np.zeros(total + 1, np.int64)
-        np.add.at(m, off, 1)
-        np.add.at(m, off + ln, -1)
-        return np.cumsum(m)[:total] > 0
-
-    qin = inside(wl.q_off, wl.q_len.astype(np.int64), q.shape[0])
-    q[qin & (rng.random(q.shape[0]) < q_rate)] = 4
-    tin = inside(wl.t_off, wl.t_len.astype(np.int64), t.shape[0])
-    starts = np.nonzero(tin & (rng.random(t.shape[0]) < t_runs))[0]
-    if starts.size:
-        lens = rng.integers(1, run_max + 1, starts.size)
-        cover = np.zeros(t.shape[0] + run_max + 1, np.int64)
-        np.add.at(cover, starts, 1)
-        np.add.at(cover, starts + lens, -1)
-        t[(np.cumsum(cover)[:t.shape[0]] > 0) & tin] = 4
+    kq = rng.binomial(int(wl.q_len.sum()), q_rate)
+    pos, _ = _draw_positions(wl.q_off, wl.q_len, kq, rng)
+    q[pos] = 4
+    kt = rng.binomial(int(wl.t_len.sum()), t_runs)
+    start, i = _draw_positions(wl.t_off, wl.t_len, kt, rng)
+    if start.size:
+        end = np.minimum(start + rng.integers(1, run_max + 1, start.size), wl.t_off[i] + wl.t_len[i])
+        lens = end - start
+        first = np.cumsum(lens) - lens
+        t[np.repeat(start, lens) + np.arange(int(lens.sum())) - np.repeat(first, lens)] = 4
     return Workload(wl.name + "+N", wl.params, q, wl.q_off, wl.q_len, t, wl.t_off, wl.t_len, wl.h0)
 
 
