@@ -376,9 +376,14 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def extend_host(self, hb: HostBatch, flags: int = 0, stream: int | None = None):
-        """Host inputs -> (results int32 [N, 6], cells)."""
-        out = np.zeros((hb.n, 6), np.int32)
+    def extend_host(self, hb: HostBatch, flags: int = 0, stream: int | None = None, out: np.ndarray | None = None):
+        """Host inputs -> (results int32 [N, 6], cells).  `out`, if given, is a
+        C-contiguous int32 [N, 6] array that receives the results (pinned
+        memory makes the copy back faster)."""
+        if out is None:
+            out = np.zeros((hb.n, 6), np.int32)
+        elif out.dtype != np.int32 or out.shape != (hb.n, 6) or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous int32 array of shape (%d, 6)" % hb.n)
         cells = ctypes.c_int64()
         rc = bsw_extend_batch(self.handle, hb.struct(hb.flags | flags), out.ctypes.data,
                               ctypes.addressof(cells), stream)

@@ -132,7 +132,7 @@ int64_t slot_bytes_for(int maxn) { return (int64_t)align_up((size_t)(maxn + 1 + 
 struct Lane {
     Streams S{};
     cudaEvent_t done = nullptr;
-    DevBuf work, io;
+    DevBuf work, io, seq;       // seq: sequences of a staged host batch
     WorkLayout wl{};
     bool work_dirty = true;     // histogram must be zeroed before the next launch
     uint8_t *pinned = nullptr;  // host staging (serving lanes)
@@ -161,6 +161,7 @@ struct Lane {
         if (S.main) cudaStreamDestroy(S.main);
         work.release(B);
         io.release(B);
+        seq.release(B);
         if (pinned) cudaFreeHost(pinned);
         pinned = nullptr;
     }
@@ -198,7 +199,9 @@ struct Lane {
     }
 };
 
-// Host-side check of one batch; fills the packed-byte extents and max query length.
+// Host-side check of one serving request (small batches; a synchronous host
+// batch is checked on the device by stage_host); fills the packed-byte
+// extents, the longest query and a bound on the band area.
 struct Extents {
     int64_t q_lo = INT64_MAX, q_hi = 0, t_lo = INT64_MAX, t_hi = 0;
     int maxn = 0;
@@ -229,9 +232,10 @@ int check_host_batch(const bsw_batch_t *b, const Params &P, Extents *x)
     return BSW_OK;
 }
 
-// Device layout of a staged batch.
+// Device layout of a staged serving batch (one contiguous copy from the lane's
+// pinned staging).
 struct IoLayout {
-    size_t q, t, q_off, q_len, t_off, t_len, h0, w, out, cells, status, in_end, total, qn, tn;
+    size_t q, t, q_off, q_len, t_off, t_len, h0, w, out, cells, status, in_end, total;
 };
 
 // N bitmap bytes staged for packed bytes [lo, hi) (two packed bytes per
@@ -239,13 +243,11 @@ struct IoLayout {
 inline int64_t nmask_lo(int64_t lo) { return lo / 2; }
 inline int64_t nmask_bytes(int64_t lo, int64_t hi) { return hi > lo ? (hi + 1) / 2 - lo / 2 : 0; }
 
-IoLayout io_layout(int64_t N, int64_t qbytes, int64_t tbytes, int64_t qnbytes = 0, int64_t tnbytes = 0)
+IoLayout io_layout(int64_t N, int64_t qbytes, int64_t tbytes)
 {
     IoLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
-    L.qn = take((size_t)qnbytes);
-    L.tn = take((size_t)tnbytes);
     L.q = take((size_t)qbytes);
     L.t = take((size_t)tbytes);
     L.q_off = take(8 * (size_t)N);
@@ -293,6 +295,7 @@ struct bsw_ctx {
     Lane sync;
     uint32_t *h_status = nullptr;     // pinned
     unsigned long long *h_cells = nullptr;
+    Extents32 *h_ext = nullptr;
 
     // execution plan (bsw_set_plan / bsw_autotune) and kernel timing
     Plan plan = default_plan();
@@ -394,25 +397,56 @@ ClassTimer *timer_for(bsw_ctx *c, uint32_t flags)
     return &c->timer;
 }
 
-// Copy a host batch's inputs into the sync lane's staging buffer (only the
-// packed bytes its pairs use; the device base pointers are shifted back by the
-// first used byte so the caller's offsets stay valid) and describe it as a
-// device Batch whose results go to the staging buffer.  Enqueued on the lane's
-// stream after `user` (nullable) reaches this point.
-int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B, IoLayout *out_L)
+// Device layout of a host batch staged by stage_host: the per-pair arrays, the
+// results and the extents record in the lane's io buffer; the sequences and N
+// bitmaps in its seq buffer, sized once the extents are known.
+struct StageLayout {
+    size_t q_off, q_len, t_off, t_len, h0, w, out, ext, total;
+    size_t q, t, qn, tn, seq_total;
+};
+
+StageLayout stage_layout(int64_t N, bool has_w)
 {
-    Extents x;
-    int rc = check_host_batch(b, c->P, &x);
-    if (rc != BSW_OK) return rc;
+    StageLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    L.q_off = take(8 * (size_t)N);
+    L.q_len = take(4 * (size_t)N);
+    L.t_off = take(8 * (size_t)N);
+    L.t_len = take(4 * (size_t)N);
+    L.h0 = take(4 * (size_t)N);
+    L.w = take(has_w ? 4 * (size_t)N : 0);
+    L.out = take(sizeof(bsw_result_t) * (size_t)N);
+    L.ext = take(sizeof(Extents32));
+    L.total = o;
+    return L;
+}
+
+void stage_seq_layout(StageLayout &L, int64_t qbytes, int64_t tbytes, int64_t qnbytes, int64_t tnbytes)
+{
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    L.qn = take((size_t)qnbytes);
+    L.tn = take((size_t)tnbytes);
+    L.q = take((size_t)qbytes);
+    L.t = take((size_t)tbytes);
+    L.seq_total = o;
+}
+
+// Stage a host batch on the sync lane (enqueued after `user`, nullable,
+// reaches this point): copy the per-pair arrays, check them and reduce their
+// extents on the device (one small read-back), then copy only the packed
+// sequence bytes the pairs use; the device base pointers are shifted back by
+// the first used byte so the caller's offsets stay valid.  Describes the
+// staged batch as a device Batch whose results go to the io buffer.
+int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B, StageLayout *out_L)
+{
     const int64_t N = b->n_pairs;
-    const int64_t qbytes = x.q_hi - x.q_lo, tbytes = x.t_hi - x.t_lo;
-    const int64_t qnb = b->q_n ? nmask_bytes(x.q_lo, x.q_hi) : 0, tnb = b->t_n ? nmask_bytes(x.t_lo, x.t_hi) : 0;
-    IoLayout L = io_layout(N, qbytes, tbytes, qnb, tnb);
     Lane &lane = c->sync;
+    StageLayout L = stage_layout(N, b->w_override != nullptr);
     bool moved = false;
+    int rc;
     if ((rc = lane.io.reserve(L.total, c->budget, &moved)) != BSW_OK) return rc;
-    if ((rc = lane.ensure_work(N, std::max(x.maxn, kShortMax), c->sms, c->budget, &moved)) != BSW_OK) return rc;
-    if (moved) clear_graphs(c);
     uint8_t *d = lane.io.p;
     cudaStream_t st = lane.S.main;
     cudaError_t e;
@@ -420,21 +454,46 @@ int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B
         if ((e = cudaEventRecord(lane.done, user)) != cudaSuccess) return cuda_rc(e);
         if ((e = cudaStreamWaitEvent(st, lane.done, 0)) != cudaSuccess) return cuda_rc(e);
     }
-    struct Cp { size_t off; const void *src; size_t bytes; } cps[] = {
-        {L.q, b->q + x.q_lo, (size_t)qbytes}, {L.t, b->t + x.t_lo, (size_t)tbytes},
+    struct Cp { size_t off; const void *src; size_t bytes; };
+    const Cp meta[] = {
         {L.q_off, b->q_off, 8 * (size_t)N}, {L.q_len, b->q_len, 4 * (size_t)N},
         {L.t_off, b->t_off, 8 * (size_t)N}, {L.t_len, b->t_len, 4 * (size_t)N},
-        {L.h0, b->h0, 4 * (size_t)N}, {L.w, b->w_override, b->w_override ? 4 * (size_t)N : 0},
-        {L.qn, b->q_n ? b->q_n + nmask_lo(x.q_lo) : nullptr, (size_t)qnb},
-        {L.tn, b->t_n ? b->t_n + nmask_lo(x.t_lo) : nullptr, (size_t)tnb}};
-    for (const Cp &cp : cps)
+        {L.h0, b->h0, 4 * (size_t)N}, {L.w, b->w_override, b->w_override ? 4 * (size_t)N : 0}};
+    for (const Cp &cp : meta)
         if (cp.bytes && (e = cudaMemcpyAsync(d + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_rc(e);
-    *out_B = Batch{N, d + L.q - x.q_lo, (const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len),
-                   d + L.t - x.t_lo, (const int64_t *)(d + L.t_off), (const int32_t *)(d + L.t_len),
-                   (const int32_t *)(d + L.h0), b->w_override ? (const int32_t *)(d + L.w) : nullptr,
-                   (bsw_result_t *)(d + L.out), b->q_n ? d + L.qn - nmask_lo(x.q_lo) : nullptr,
-                   b->t_n ? d + L.tn - nmask_lo(x.t_lo) : nullptr};
+    Extents32 *X = reinterpret_cast<Extents32 *>(d + L.ext);
+    if ((e = cudaMemsetAsync(X, 0xff, 16, st)) != cudaSuccess) return cuda_rc(e);                 // q_lo, t_lo
+    if ((e = cudaMemsetAsync(reinterpret_cast<uint8_t *>(X) + 16, 0, sizeof(Extents32) - 16, st)) != cudaSuccess)
+        return cuda_rc(e);
+    const PairMeta M{(const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len), (const int64_t *)(d + L.t_off),
+                     (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
+                     b->w_override ? (const int32_t *)(d + L.w) : nullptr};
+    if ((e = launch_extents(M, N, c->P, X, st, c->sms)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaMemcpyAsync(c->h_ext, X, sizeof(Extents32), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+    const Extents32 x = *c->h_ext;
+    if (x.inval) return BSW_EINVAL;
+    int64_t q_lo = (int64_t)x.q_lo, q_hi = (int64_t)x.q_hi, t_lo = (int64_t)x.t_lo, t_hi = (int64_t)x.t_hi;
+    if (x.q_lo > x.q_hi) q_lo = q_hi = 0;                 // no pair with both sides non-empty
+    if (x.t_lo > x.t_hi) t_lo = t_hi = 0;
+    const int64_t qnb = b->q_n ? nmask_bytes(q_lo, q_hi) : 0, tnb = b->t_n ? nmask_bytes(t_lo, t_hi) : 0;
+    stage_seq_layout(L, q_hi - q_lo, t_hi - t_lo, qnb, tnb);
+    if ((rc = lane.seq.reserve(L.seq_total, c->budget, &moved)) != BSW_OK) return rc;
+    if ((rc = lane.ensure_work(N, std::max((int)x.maxn, kShortMax), c->sms, c->budget, &moved)) != BSW_OK) return rc;
+    if (moved) clear_graphs(c);
+    uint8_t *sq = lane.seq.p;
+    const Cp seqs[] = {
+        {L.q, b->q + q_lo, (size_t)(q_hi - q_lo)}, {L.t, b->t + t_lo, (size_t)(t_hi - t_lo)},
+        {L.qn, b->q_n ? b->q_n + nmask_lo(q_lo) : nullptr, (size_t)qnb},
+        {L.tn, b->t_n ? b->t_n + nmask_lo(t_lo) : nullptr, (size_t)tnb}};
+    for (const Cp &cp : seqs)
+        if (cp.bytes && (e = cudaMemcpyAsync(sq + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+    *out_B = Batch{N, sq + L.q - q_lo, M.q_off, M.q_len, sq + L.t - t_lo, M.t_off, M.t_len, M.h0, M.w,
+                   (bsw_result_t *)(d + L.out), b->q_n ? sq + L.qn - nmask_lo(q_lo) : nullptr,
+                   b->t_n ? sq + L.tn - nmask_lo(t_lo) : nullptr};
     *out_L = L;
     return BSW_OK;
 }
@@ -442,7 +501,7 @@ int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B
 int extend_host(bsw_ctx *c, const bsw_batch_t *b, bsw_result_t *out, int64_t *cells_out, cudaStream_t user)
 {
     Batch B;
-    IoLayout L;
+    StageLayout L;
     int rc = stage_host(c, b, user, &B, &L);
     if (rc != BSW_OK) return rc;
     const int64_t N = b->n_pairs;
@@ -769,7 +828,8 @@ int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonu
     if (rc == BSW_OK) rc = c->sync.create();
     if (rc == BSW_OK && prepare_kernels(c->sms) != cudaSuccess) rc = BSW_ECUDA;
     if (rc == BSW_OK && (cudaMallocHost(&c->h_status, 4) != cudaSuccess ||
-                         cudaMallocHost(&c->h_cells, 8) != cudaSuccess))
+                         cudaMallocHost(&c->h_cells, 8) != cudaSuccess ||
+                         cudaMallocHost(&c->h_ext, sizeof(Extents32)) != cudaSuccess))
         rc = BSW_ENOMEM;
     if (rc == BSW_OK && (cudaEventCreate(&c->tune_ev[0]) != cudaSuccess || cudaEventCreate(&c->tune_ev[1]) != cudaSuccess))
         rc = BSW_ECUDA;
@@ -959,7 +1019,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         B = Batch{ns, sb.q, sb.q_off, sb.q_len, sb.t, sb.t_off, sb.t_len, sb.h0, sb.w_override,
                   (bsw_result_t *)lane.io.p, sb.q_n, sb.t_n};
     } else {
-        IoLayout L;
+        StageLayout L;
         if ((rc = stage_host(ctx, &sb, nullptr, &B, &L)) != BSW_OK) return rc;
     }
     const Work W = make_work(lane.work.p, lane.wl);
@@ -1435,6 +1495,7 @@ void bsw_destroy(bsw_ctx_t *ctx)
     for (auto &kv : ctx->tickets) delete kv.second;
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_cells) cudaFreeHost(ctx->h_cells);
+    if (ctx->h_ext) cudaFreeHost(ctx->h_ext);
     delete ctx;
 }
 

@@ -260,6 +260,65 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(int64_t n, Work W)
     }
 }
 
+// Checks and packed-byte extents of a batch's pairs (block reduction, then one
+// atomic per field and block).
+__global__ void __launch_bounds__(256) k_extents(PairMeta M, int64_t n, Params P, Extents32 *X)
+{
+    unsigned long long qlo = ~0ull, qhi = 0, tlo = ~0ull, thi = 0;
+    int maxn = 0;
+    uint32_t bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const int32_t ql = M.q_len[k], tl = M.t_len[k], h0 = M.h0[k];
+        const int64_t qo = M.q_off[k], to = M.t_off[k];
+        const int32_t w = M.w ? M.w[k] : P.w;
+        if (ql < 0 || tl < 0 || h0 < 0 || w < 0 || qo < 0 || to < 0 || (qo & 3) || (to & 3)) {
+            bad = 1;
+            continue;
+        }
+        if (ql > 0 && tl > 0) {
+            if ((long long)h0 + (long long)P.a * min(ql, tl) >= (1ll << 30) || ql > kLongMax) bad = 1;
+            qlo = min(qlo, (unsigned long long)(qo >> 2));
+            qhi = max(qhi, (unsigned long long)((qo + ql + 3) >> 2));
+            tlo = min(tlo, (unsigned long long)(to >> 2));
+            thi = max(thi, (unsigned long long)((to + tl + 3) >> 2));
+            maxn = max(maxn, ql);
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        qlo = min(qlo, __shfl_xor_sync(kFull, qlo, d));
+        qhi = max(qhi, __shfl_xor_sync(kFull, qhi, d));
+        tlo = min(tlo, __shfl_xor_sync(kFull, tlo, d));
+        thi = max(thi, __shfl_xor_sync(kFull, thi, d));
+        maxn = max(maxn, __shfl_xor_sync(kFull, maxn, d));
+        bad |= __shfl_xor_sync(kFull, bad, d);
+    }
+    __shared__ unsigned long long s[8][4];
+    __shared__ int sm[8];
+    __shared__ uint32_t sb[8];
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s[wid][0] = qlo; s[wid][1] = qhi; s[wid][2] = tlo; s[wid][3] = thi;
+        sm[wid] = maxn;
+        sb[wid] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int u = 1; u < (int)(blockDim.x >> 5); ++u) {
+            qlo = min(qlo, s[u][0]); qhi = max(qhi, s[u][1]);
+            tlo = min(tlo, s[u][2]); thi = max(thi, s[u][3]);
+            maxn = max(maxn, sm[u]);
+            bad |= sb[u];
+        }
+        atomicMin(&X->q_lo, qlo);
+        atomicMax(&X->q_hi, qhi);
+        atomicMin(&X->t_lo, tlo);
+        atomicMax(&X->t_hi, thi);
+        atomicMax(&X->maxn, maxn);
+        if (bad) atomicOr(&X->inval, 1u);
+    }
+}
+
 // ------------------------------------------------------- one pair per thread
 
 // Slot word layouts (32 bits per column, column j of lane L at S[j*32 + L]):
@@ -1550,6 +1609,14 @@ cudaError_t launch_prepass(const Batch &B, const Params &P, const Work &W, cudaS
 }
 
 }  // namespace
+
+cudaError_t launch_extents(const PairMeta &M, int64_t n, const Params &P, Extents32 *X, cudaStream_t st, int sms)
+{
+    const int64_t b = (n + 255) / 256;
+    const int blocks = (int)(b < (int64_t)sms * 4 ? (b > 0 ? b : 1) : (int64_t)sms * 4);
+    k_extents<<<blocks, 256, 0, st>>>(M, n, P, X);
+    return cudaGetLastError();
+}
 
 bool packed_scoring_ok(const Params &P) { return inter2_scoring_ok(P); }
 

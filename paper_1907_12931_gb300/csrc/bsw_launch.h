@@ -78,6 +78,26 @@ cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W
 // Baseline: one pair per warp in input order.
 cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms);
 
+// Per-pair arrays of a host batch already on the device, checked and reduced
+// there: whether any pair is invalid (the checks of bsw_extend_batch) and, over
+// the pairs with both sides non-empty, the packed-byte extents of q and t and
+// the longest query.
+struct PairMeta {
+    const int64_t *q_off;
+    const int32_t *q_len;
+    const int64_t *t_off;
+    const int32_t *t_len;
+    const int32_t *h0;
+    const int32_t *w;   // nullable
+};
+struct Extents32 {
+    unsigned long long q_lo, t_lo;   // start at ~0
+    unsigned long long q_hi, t_hi;   // the rest start at 0
+    int32_t maxn;
+    uint32_t inval;
+};
+cudaError_t launch_extents(const PairMeta &M, int64_t n, const Params &P, Extents32 *X, cudaStream_t st, int sms);
+
 // ---------------------------------------------------- seed-extension driver
 
 // Device inputs of bsw_extend_seeds (packed reads and reference, seeds).
