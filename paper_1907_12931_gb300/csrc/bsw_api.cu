@@ -296,6 +296,7 @@ struct bsw_ctx {
     uint32_t *h_status = nullptr;     // pinned
     unsigned long long *h_cells = nullptr;
     Extents32 *h_ext = nullptr;
+    DriverCheck *h_chk = nullptr;
 
     // execution plan (bsw_set_plan / bsw_autotune) and kernel timing
     Plan plan = default_plan();
@@ -307,7 +308,7 @@ struct bsw_ctx {
 
     // seed-extension driver: the reference (bsw_set_reference) and the
     // buffers of a bsw_extend_seeds call
-    DevBuf refbuf, drv;
+    DevBuf refbuf, drv, drvmeta;     // drvmeta: reads' offsets and lengths, seeds, checks
     int64_t ref_len = -1;
 
     // suffix array lookup: the uncompressed suffix array and staging
@@ -829,7 +830,8 @@ int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonu
     if (rc == BSW_OK && prepare_kernels(c->sms) != cudaSuccess) rc = BSW_ECUDA;
     if (rc == BSW_OK && (cudaMallocHost(&c->h_status, 4) != cudaSuccess ||
                          cudaMallocHost(&c->h_cells, 8) != cudaSuccess ||
-                         cudaMallocHost(&c->h_ext, sizeof(Extents32)) != cudaSuccess))
+                         cudaMallocHost(&c->h_ext, sizeof(Extents32)) != cudaSuccess ||
+                         cudaMallocHost(&c->h_chk, sizeof(DriverCheck)) != cudaSuccess))
         rc = BSW_ENOMEM;
     if (rc == BSW_OK && (cudaEventCreate(&c->tune_ev[0]) != cudaSuccess || cudaEventCreate(&c->tune_ev[1]) != cudaSuccess))
         rc = BSW_ECUDA;
@@ -1182,38 +1184,46 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
     const int w = ctx->P.w;
     if ((int64_t)w << (max_band_try - 1) > (1 << 20)) return BSW_EINVAL;
 
-    // Host checks: reads, seeds inside their read and the reference, each
-    // read's seeds consecutive.
-    int64_t read_bytes = 0;
-    int maxrl = 0;
-    for (int64_t r = 0; r < n_reads; ++r) {
-        if (read_off[r] < 0 || (read_off[r] & 3) || read_len[r] < 0 || read_len[r] > kLongMax) return BSW_EINVAL;
-        read_bytes = std::max(read_bytes, (read_off[r] + read_len[r] + 3) / 4);
-        maxrl = std::max(maxrl, (int)read_len[r]);
-    }
-    std::vector<uint8_t> seen((size_t)n_reads, 0);
-    for (int64_t k = 0; k < n_seeds; ++k) {
-        const bsw_seed_t &sd = seeds[k];
-        if (sd.read_id < 0 || sd.read_id >= n_reads || sd.qbeg < 0 || sd.len < 0 ||
-            (int64_t)sd.qbeg + sd.len > read_len[sd.read_id] || sd.rbeg < 0 || sd.rbeg + sd.len > ctx->ref_len)
-            return BSW_EINVAL;
-        if (k == 0 || seeds[k - 1].read_id != sd.read_id) {
-            if (seen[(size_t)sd.read_id]) return BSW_EINVAL;   // the read's seeds are not consecutive
-            seen[(size_t)sd.read_id] = 1;
-        }
-        // the score bound of the right side: h0 (at most the read length
-        // times match, plus the seed) and match per base
-        if ((int64_t)ctx->P.a * (2 * (int64_t)read_len[sd.read_id] + 1) >= (1ll << 30)) return BSW_EINVAL;
-    }
-
-    // Device layout: inputs, one side's pairs, the retry batch, the alignments.
+    // Checks on the device (launch_driver_check): reads, seeds inside their
+    // read and the reference, each read's seeds consecutive, the score bound;
+    // they also give the packed-read extent and the longest read.
     const int64_t N = n_seeds;
+    Lane &lane = ctx->sync;
+    cudaStream_t st = lane.S.main;
+    cudaError_t e;
+    size_t om = 0;
+    auto take_m = [&](size_t bytes) { size_t r = om; om = align_up(om + bytes, 256); return r; };
+    const size_t o_roff = take_m(8 * (size_t)n_reads), o_rlen = take_m(4 * (size_t)n_reads),
+                 o_seeds = take_m(sizeof(bsw_seed_t) * (size_t)N), o_runs = take_m(4 * (size_t)n_reads),
+                 o_chk = take_m(sizeof(DriverCheck));
+    int rc = ctx->drvmeta.reserve(om, ctx->budget);
+    if (rc != BSW_OK) return rc;
+    uint8_t *dm = ctx->drvmeta.p;
+    const struct { size_t off; const void *src; size_t bytes; } meta[] = {
+        {o_roff, read_off, 8 * (size_t)n_reads}, {o_rlen, read_len, 4 * (size_t)n_reads},
+        {o_seeds, seeds, sizeof(bsw_seed_t) * (size_t)N}};
+    for (const auto &cp : meta)
+        if (cp.bytes && (e = cudaMemcpyAsync(dm + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+    if ((e = cudaMemsetAsync(dm + o_runs, 0, om - o_runs, st)) != cudaSuccess) return cuda_rc(e);   // runs, check
+    DriverCheck *chk = (DriverCheck *)(dm + o_chk);
+    const DriverIn Dm{(const bsw_seed_t *)(dm + o_seeds), nullptr, (const int64_t *)(dm + o_roff),
+                      (const int32_t *)(dm + o_rlen), ctx->refbuf.p, ctx->ref_len};
+    if ((e = launch_driver_check(Dm, n_reads, N, ctx->P.a, (uint32_t *)(dm + o_runs), chk, st, ctx->sms)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaMemcpyAsync(ctx->h_chk, chk, sizeof(DriverCheck), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_rc(e);
+    if (ctx->h_chk->inval) return BSW_EINVAL;
+    const int64_t read_bytes = (int64_t)ctx->h_chk->read_bytes;
+    const int maxrl = ctx->h_chk->maxrl;
+
+    // Device layout: the reads, one side's pairs, the retry batch, the alignments.
     const int qslot = (int)align_up((size_t)std::max(maxrl, 1), 16);
     const int tslot = (int)align_up((size_t)maxrl + (size_t)w + 4, 16);
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
-    const size_t o_reads = take((size_t)read_bytes), o_roff = take(8 * (size_t)n_reads),
-                 o_rlen = take(4 * (size_t)n_reads), o_seeds = take(sizeof(bsw_seed_t) * (size_t)N),
+    const size_t o_reads = take((size_t)read_bytes),
                  o_q = take((size_t)N * qslot / 4), o_t = take((size_t)N * tslot / 4), o_qoff = take(8 * (size_t)N),
                  o_toff = take(8 * (size_t)N), o_qlen = take(4 * (size_t)N), o_tlen = take(4 * (size_t)N),
                  o_h0 = take(4 * (size_t)N), o_wcur = take(4 * (size_t)N), o_res = take(sizeof(bsw_result_t) * (size_t)N),
@@ -1222,23 +1232,14 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
                  o_ch0 = take(4 * (size_t)N), o_cw = take(4 * (size_t)N),
                  o_cres = take(sizeof(bsw_result_t) * (size_t)N), o_aln = take(sizeof(bsw_aln_t) * (size_t)N),
                  o_cells = take(8 * 2 * (size_t)max_band_try);
-    Lane &lane = ctx->sync;
     bool moved = false;
-    int rc = ctx->drv.reserve(o, ctx->budget);
-    if (rc != BSW_OK) return rc;
+    if ((rc = ctx->drv.reserve(o, ctx->budget)) != BSW_OK) return rc;
     if ((rc = lane.ensure_work(N, std::max(maxrl, kShortMax), ctx->sms, ctx->budget, &moved)) != BSW_OK) return rc;
     if (moved) clear_graphs(ctx);
     uint8_t *d = ctx->drv.p;
-    cudaStream_t st = lane.S.main;
-    cudaError_t e;
-    const struct { size_t off; const void *src; size_t bytes; } cps[] = {
-        {o_reads, reads, (size_t)read_bytes}, {o_roff, read_off, 8 * (size_t)n_reads},
-        {o_rlen, read_len, 4 * (size_t)n_reads}, {o_seeds, seeds, sizeof(bsw_seed_t) * (size_t)N}};
-    for (const auto &cp : cps)
-        if (cp.bytes && (e = cudaMemcpyAsync(d + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_rc(e);
-    const DriverIn D{(const bsw_seed_t *)(d + o_seeds), d + o_reads, (const int64_t *)(d + o_roff),
-                     (const int32_t *)(d + o_rlen), ctx->refbuf.p, ctx->ref_len};
+    if (read_bytes && (e = cudaMemcpyAsync(d + o_reads, reads, (size_t)read_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_rc(e);
+    const DriverIn D{Dm.seeds, d + o_reads, Dm.read_off, Dm.read_len, ctx->refbuf.p, ctx->ref_len};
     const DriverSide S{d + o_q, d + o_t, (int64_t *)(d + o_qoff), (int64_t *)(d + o_toff), (int32_t *)(d + o_qlen),
                        (int32_t *)(d + o_tlen), (int32_t *)(d + o_h0), (int32_t *)(d + o_wcur),
                        (bsw_result_t *)(d + o_res), qslot, tslot};
@@ -1481,6 +1482,7 @@ void bsw_destroy(bsw_ctx_t *ctx)
     ctx->sync.destroy(ctx->budget);
     ctx->refbuf.release(ctx->budget);
     ctx->drv.release(ctx->budget);
+    ctx->drvmeta.release(ctx->budget);
     ctx->sabuf.release(ctx->budget);
     ctx->salio.release(ctx->budget);
     ctx->fmbuf.release(ctx->budget);
@@ -1496,6 +1498,7 @@ void bsw_destroy(bsw_ctx_t *ctx)
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_cells) cudaFreeHost(ctx->h_cells);
     if (ctx->h_ext) cudaFreeHost(ctx->h_ext);
+    if (ctx->h_chk) cudaFreeHost(ctx->h_chk);
     delete ctx;
 }
 

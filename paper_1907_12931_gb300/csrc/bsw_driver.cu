@@ -175,6 +175,54 @@ __global__ void k_filter(DriverIn D, int64_t n, bsw_aln_t *out)
     }
 }
 
+// Reads: offsets on a base multiple of 4, lengths in [0, kLongMax]; the
+// packed extent and the longest read.
+__global__ void __launch_bounds__(256) k_check_reads(DriverIn D, int64_t n_reads, DriverCheck *X)
+{
+    unsigned long long rb = 0;
+    int mx = 0;
+    uint32_t bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_reads; r += stride) {
+        const int64_t o = D.read_off[r];
+        const int32_t l = D.read_len[r];
+        if (o < 0 || (o & 3) || l < 0 || l > kLongMax) { bad = 1; continue; }
+        rb = max(rb, (unsigned long long)((o + l + 3) >> 2));
+        mx = max(mx, l);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        rb = max(rb, __shfl_xor_sync(0xffffffffu, rb, d));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&X->read_bytes, rb);
+        atomicMax(&X->maxrl, mx);
+        if (bad) atomicOr(&X->inval, 1u);
+    }
+}
+
+// Seeds: inside their read and the reference, the right side's score bound
+// within 2^30, and each read's seeds one consecutive run.  Reads are checked
+// by k_check_reads in the same stream before this kernel's results are used;
+// a seed of an invalid read only reads that read's length.
+__global__ void __launch_bounds__(256) k_check_seeds(DriverIn D, int64_t n_reads, int64_t n_seeds, int match,
+                                                     uint32_t *runs, DriverCheck *X)
+{
+    uint32_t bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_seeds; k += stride) {
+        const bsw_seed_t sd = D.seeds[k];
+        if (sd.read_id < 0 || sd.read_id >= n_reads) { bad = 1; continue; }
+        const int32_t rl = D.read_len[sd.read_id];
+        if (sd.qbeg < 0 || sd.len < 0 || (int64_t)sd.qbeg + sd.len > rl || sd.rbeg < 0 || sd.rbeg + sd.len > D.ref_len ||
+            (long long)match * (2 * (long long)rl + 1) >= (1ll << 30))
+            bad = 1;
+        if ((k == 0 || D.seeds[k - 1].read_id != sd.read_id) && atomicAdd(&runs[sd.read_id], 1u) != 0u) bad = 1;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&X->inval, 1u);
+}
+
 int grid_for(int64_t n, int per_block, int sms)
 {
     const int64_t b = (n + per_block - 1) / per_block;
@@ -218,6 +266,14 @@ cudaError_t launch_decide(bool left, const DriverIn &D, const DriverSide &S, int
 {
     if (left) k_decide<true><<<grid_for(n, 256, sms), 256, 0, st>>>(D, S, n, end_bonus, out);
     else k_decide<false><<<grid_for(n, 256, sms), 256, 0, st>>>(D, S, n, end_bonus, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_driver_check(const DriverIn &D, int64_t n_reads, int64_t n_seeds, int match, uint32_t *runs,
+                                DriverCheck *X, cudaStream_t st, int sms)
+{
+    if (n_reads > 0) k_check_reads<<<grid_for(n_reads, 256, sms), 256, 0, st>>>(D, n_reads, X);
+    if (n_seeds > 0) k_check_seeds<<<grid_for(n_seeds, 256, sms), 256, 0, st>>>(D, n_reads, n_seeds, match, runs, X);
     return cudaGetLastError();
 }
 

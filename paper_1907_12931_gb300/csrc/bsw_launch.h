@@ -121,6 +121,19 @@ struct DriverSide {
     int qslot, tslot;
 };
 
+// Checks of bsw_extend_seeds' inputs, on the device: every read's offset and
+// length, every seed inside its read and the reference, each read's seeds
+// consecutive (runs[r] counts the runs of read r's seeds; zeroed by the
+// caller), the right side's score bound.  Also the packed-read extent and the
+// longest read.  read_bytes and maxrl start at 0, inval at 0.
+struct DriverCheck {
+    unsigned long long read_bytes;
+    int32_t maxrl;
+    uint32_t inval;
+};
+cudaError_t launch_driver_check(const DriverIn &D, int64_t n_reads, int64_t n_seeds, int match, uint32_t *runs,
+                                DriverCheck *X, cudaStream_t st, int sms);
+
 // The compact batch of a band retry (the sequences stay in DriverSide).
 struct DriverCompact {
     int64_t *q_off, *t_off;
