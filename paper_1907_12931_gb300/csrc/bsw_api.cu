@@ -315,9 +315,10 @@ struct bsw_ctx {
     DevBuf sabuf, salio;
     int64_t sa_n = -1;
 
-    // SMEM search: the FM-indexes of T = ref + revcomp(ref) and of reverse(T)
-    DevBuf fmbuf, smemio;
-    FmDev fm_t{}, fm_r{};
+    // SMEM search: the FM-index of T = ref + revcomp(ref); staging, and the
+    // global lists of reads whose lists overflow shared memory
+    DevBuf fmbuf, smemio, smemscratch;
+    FmDev fm_t{};
     bool fm_ready = false;
 
     struct GEntry {
@@ -1375,7 +1376,7 @@ int bsw_fm_build(bsw_ctx_t *ctx, const uint8_t *ref, int64_t n)
     if (!serving_idle(ctx)) return BSW_ESTATE;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
     ctx->fm_ready = false;
-    FmHost ft, fr;
+    FmHost ft;
     try {
         std::vector<uint8_t> T((size_t)(2 * n));
         for (int64_t i = 0; i < n; ++i) {
@@ -1387,22 +1388,15 @@ int bsw_fm_build(bsw_ctx_t *ctx, const uint8_t *ref, int64_t n)
         int rc = bsw_sa_build(T.data(), 2 * n, sa.data());
         if (rc != BSW_OK) return rc;
         fm_from_sa(T.data(), 2 * n, sa.data(), ft);
-        std::reverse(T.begin(), T.end());
-        if ((rc = bsw_sa_build(T.data(), 2 * n, sa.data())) != BSW_OK) return rc;
-        fm_from_sa(T.data(), 2 * n, sa.data(), fr);
     } catch (const std::bad_alloc &) {
         return BSW_ENOMEM;
     }
-    const size_t bt = sizeof(FmEntry) * ft.occ.size(), br = sizeof(FmEntry) * fr.occ.size();
-    int rc = ctx->fmbuf.reserve(bt + br, ctx->budget);
+    const size_t bt = sizeof(FmEntry) * ft.occ.size();
+    int rc = ctx->fmbuf.reserve(bt, ctx->budget);
     if (rc != BSW_OK) return rc;
     cudaError_t e;
-    if ((e = cudaMemcpy(ctx->fmbuf.p, ft.occ.data(), bt, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(ctx->fmbuf.p + bt, fr.occ.data(), br, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return cuda_rc(e);
+    if ((e = cudaMemcpy(ctx->fmbuf.p, ft.occ.data(), bt, cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_rc(e);
     ctx->fm_t = FmDev{(const FmEntry *)ctx->fmbuf.p, ft.n, ft.primary, {ft.C[0], ft.C[1], ft.C[2], ft.C[3], ft.C[4]}};
-    ctx->fm_r = FmDev{(const FmEntry *)(ctx->fmbuf.p + bt), fr.n, fr.primary,
-                      {fr.C[0], fr.C[1], fr.C[2], fr.C[3], fr.C[4]}};
     ctx->fm_ready = true;
     return BSW_OK;
 }
@@ -1428,8 +1422,9 @@ int bsw_smem(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
     const size_t o_reads = take((size_t)read_bytes), o_roff = take(8 * (size_t)n_reads),
-                 o_rlen = take(4 * (size_t)n_reads), o_end = take(4 * (size_t)n_reads * (size_t)lmax),
-                 o_cnt = take(8 * (size_t)n_reads), o_first = take(8 * (size_t)n_reads),
+                 o_rlen = take(4 * (size_t)n_reads), o_cnt = take(8 * (size_t)n_reads),
+                 o_first = take(8 * (size_t)n_reads), o_ids = take(4 * (size_t)n_reads), o_nids = take(4),
+                 o_next = take(4), o_keep = take(sizeof(bsw_smem_t) * kSmemKeep * (size_t)n_reads),
                  o_out = take(sizeof(bsw_smem_t) * (size_t)std::max<int64_t>(out_cap, 1));
     int rc = ctx->smemio.reserve(o, ctx->budget);
     if (rc != BSW_OK) return rc;
@@ -1438,29 +1433,62 @@ int bsw_smem(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_
     cudaError_t e;
     if ((e = cudaMemcpyAsync(d + o_reads, reads, (size_t)read_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d + o_roff, read_off, 8 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d + o_rlen, read_len, 4 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        (e = cudaMemcpyAsync(d + o_rlen, read_len, 4 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d + o_nids, 0, 4, st)) != cudaSuccess)
         return cuda_rc(e);
     const SmemIn R{d + o_reads, (const int64_t *)(d + o_roff), (const int32_t *)(d + o_rlen), n_reads, lmax};
-    int32_t *end = (int32_t *)(d + o_end);
-    int64_t *cnt = (int64_t *)(d + o_cnt), *dfirst = (int64_t *)(d + o_first);
-    if ((e = launch_match_end(R, ctx->fm_r, end, st, ctx->sms)) != cudaSuccess ||
-        (e = launch_smem(false, R, ctx->fm_t, end, min_len, cnt, nullptr, nullptr, st, ctx->sms)) != cudaSuccess)
+    int32_t *ids = (int32_t *)(d + o_ids);
+    uint32_t *nids = (uint32_t *)(d + o_nids);
+    int64_t *dfirst = (int64_t *)(d + o_first);
+    const SmemWork W{(int64_t *)(d + o_cnt), (bsw_smem_t *)(d + o_keep), dfirst, (bsw_smem_t *)(d + o_out),
+                     (uint32_t *)(d + o_next), nids, ids};
+    auto global_lists = [&](int64_t n_ids, BiIv **lists) -> int {      // lmax + 1 entries hold any list
+        const int r2 = ctx->smemscratch.reserve(sizeof(BiIv) * (size_t)n_ids * (size_t)(lmax + 1), ctx->budget);
+        *lists = (BiIv *)ctx->smemscratch.p;
+        return r2;
+    };
+
+    // One search pass: counts, and the records of reads with few; reads whose
+    // lists overflow shared memory are searched with lists in global memory.
+    if ((e = launch_smem_store(R, ctx->fm_t, min_len, W, st, ctx->sms)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(ctx->h_status, nids, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_rc(e);
+    const int64_t n_ovf = *ctx->h_status;
+    if (n_ovf > 0) {
+        BiIv *lists = nullptr;
+        if ((rc = global_lists(n_ovf, &lists)) != BSW_OK) return rc;
+        if ((e = launch_smem_global(false, R, ctx->fm_t, min_len, W, ids, n_ovf, lists, lmax + 1, st, ctx->sms)) !=
+            cudaSuccess)
+            return cuda_rc(e);
+    }
     std::vector<int64_t> hc((size_t)n_reads), hf((size_t)n_reads + 1);
-    if ((e = cudaMemcpyAsync(hc.data(), cnt, 8 * (size_t)n_reads, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+    if ((e = cudaMemcpyAsync(hc.data(), W.count, 8 * (size_t)n_reads, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_rc(e);
     hf[0] = 0;
-    for (int64_t r = 0; r < n_reads; ++r) hf[(size_t)r + 1] = hf[(size_t)r] + hc[(size_t)r];
+    std::vector<int32_t> many;                                        // reads with more records than were kept
+    for (int64_t r = 0; r < n_reads; ++r) {
+        hf[(size_t)r + 1] = hf[(size_t)r] + hc[(size_t)r];
+        if (hc[(size_t)r] > kSmemKeep) many.push_back((int32_t)r);
+    }
     const int64_t total = hf[(size_t)n_reads];
     *n_out = total;
     if (first) std::memcpy(first, hf.data(), 8 * ((size_t)n_reads + 1));
     if (total > out_cap) return BSW_EBUDGET;
     if (total == 0) return BSW_OK;
-    bsw_smem_t *dout = (bsw_smem_t *)(d + o_out);
     if ((e = cudaMemcpyAsync(dfirst, hf.data(), 8 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = launch_smem(true, R, ctx->fm_t, end, min_len, nullptr, dfirst, dout, st, ctx->sms)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(out, dout, sizeof(bsw_smem_t) * (size_t)total, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = launch_smem_gather(n_reads, W, st, ctx->sms)) != cudaSuccess)
+        return cuda_rc(e);
+    if (!many.empty()) {
+        BiIv *lists = nullptr;
+        if ((rc = global_lists((int64_t)many.size(), &lists)) != BSW_OK) return rc;
+        if ((e = cudaMemcpyAsync(ids, many.data(), 4 * many.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = launch_smem_global(true, R, ctx->fm_t, min_len, W, ids, (int64_t)many.size(), lists, lmax + 1, st,
+                                    ctx->sms)) != cudaSuccess)
+            return cuda_rc(e);
+    }
+    if ((e = cudaMemcpyAsync(out, W.out, sizeof(bsw_smem_t) * (size_t)total, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_rc(e);
     return BSW_OK;
@@ -1487,6 +1515,7 @@ void bsw_destroy(bsw_ctx_t *ctx)
     ctx->salio.release(ctx->budget);
     ctx->fmbuf.release(ctx->budget);
     ctx->smemio.release(ctx->budget);
+    ctx->smemscratch.release(ctx->budget);
     if (ctx->timer_ready)
         for (int k = 0; k <= kNumClass; ++k) {
             cudaEventDestroy(ctx->timer.t0[k]);

@@ -191,11 +191,34 @@ struct SmemIn {
 void fm_from_sa(const uint8_t *text, int64_t n, const int32_t *sa, FmHost &out);
 // end[r * lmax + i] = the end of the longest prefix of read r from i that
 // occurs in the text of Frev's reverse.
-cudaError_t launch_match_end(const SmemIn &R, const FmDev &Frev, int32_t *end, cudaStream_t st, int sms);
-// Per read, its SMEMs of at least min_len bases: counts (write = false) or
-// the records at first[r] (write = true) with SA intervals in F.
-cudaError_t launch_smem(bool write, const SmemIn &R, const FmDev &F, const int32_t *end, int min_len, int64_t *count,
-                        const int64_t *first, bsw_smem_t *out, cudaStream_t st, int sms);
+// One bi-interval (Algorithm 2): [k, k + s) the suffix-array interval of a
+// match P in T, [l, l + s) that of revcomp(P), e the match's end in the read.
+struct BiIv {
+    uint32_t k, l, s;
+    int32_t e;
+};
+constexpr int kSmemThreads = 128, kListCap = 20, kSmemBlocksPerSm = 5, kSmemKeep = 8;
+
+// Buffers of one SMEM search.  Store mode: count[r] (-1 and r appended to
+// ovf_list[atomicAdd(ovf_n)] when the read's list exceeds kListCap) and up to
+// kSmemKeep records at scratch[r * kSmemKeep].  Write mode: records at
+// out[first[r]].  next: the launch's read counter (zeroed by the launchers).
+struct SmemWork {
+    int64_t *count;
+    bsw_smem_t *scratch;
+    const int64_t *first;
+    bsw_smem_t *out;
+    uint32_t *next;
+    uint32_t *ovf_n;
+    int32_t *ovf_list;
+};
+cudaError_t launch_smem_store(const SmemIn &R, const FmDev &F, int min_len, const SmemWork &W, cudaStream_t st, int sms);
+// The reads ids[0..n_ids) in store or write mode with lists in `lists` (cap
+// entries per lane, n_ids lanes at most).
+cudaError_t launch_smem_global(bool write, const SmemIn &R, const FmDev &F, int min_len, const SmemWork &W,
+                               const int32_t *ids, int64_t n_ids, BiIv *lists, int cap, cudaStream_t st, int sms);
+// Records of reads with count <= kSmemKeep from the scratch to out[first[r]].
+cudaError_t launch_smem_gather(int64_t n_reads, const SmemWork &W, cudaStream_t st, int sms);
 
 // Suffix array lookup: out[off[t] + i] = sa[k[t] + i] for i < cnt[t].
 // Intervals outside [0, sa_n) set kStInval in *status and write nothing.

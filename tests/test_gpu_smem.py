@@ -69,3 +69,28 @@ def test_generated_reads(bsw):
     codes, off, rl, _ = W.make_reads(120, 151, ref_limit=60_000)
     reads = [codes[o:o + n] for o, n in zip(off, rl)]
     check(bsw, ref, reads, 19)
+
+
+@pytest.mark.parametrize("period", [1, 2, 3, 7])
+def test_repetitive_reference(bsw, period):
+    """A tandem repeat with a few point changes: the forward pass shrinks the
+    occurrence count by a little per base, so the lists of many reads exceed
+    the shared-memory capacity and those reads take the global-list launch."""
+    rng = np.random.default_rng(200 + period)
+    unit = rng.integers(0, 4, period).astype(np.uint8)
+    n = 3000
+    ref = np.tile(unit, n // period + 1)[:n]
+    ref = np.where(rng.random(n) < 0.01, rng.integers(0, 4, n), ref).astype(np.uint8)
+    reads = []
+    for _ in range(30):
+        L = int(rng.integers(20, 80))
+        p = int(rng.integers(0, n - L))
+        x = ref[p:p + L].copy()
+        if rng.random() < 0.5:
+            x = (3 - x[::-1]).astype(np.uint8)
+        flips = rng.random(L) < 0.02
+        x[flips] = (x[flips] + 1) % 4
+        reads.append(x)
+    reads.append(np.tile(unit, 100 // period + 1)[:100].astype(np.uint8))   # the pure repeat
+    for min_len in (1, 19):
+        check(bsw, ref, reads, min_len)
