@@ -435,12 +435,17 @@ void stage_seq_layout(StageLayout &L, int64_t qbytes, int64_t tbytes, int64_t qn
     L.seq_total = o;
 }
 
+// Batches up to this many pairs are checked on the host: below it the host
+// loop costs less than the device check's round trip.
+constexpr int64_t kHostCheckMax = 32768;
+
 // Stage a host batch on the sync lane (enqueued after `user`, nullable,
 // reaches this point): copy the per-pair arrays, check them and reduce their
-// extents on the device (one small read-back), then copy only the packed
-// sequence bytes the pairs use; the device base pointers are shifted back by
-// the first used byte so the caller's offsets stay valid.  Describes the
-// staged batch as a device Batch whose results go to the io buffer.
+// extents (on the device with one small read-back, or on the host for small
+// batches), then copy only the packed sequence bytes the pairs use; the
+// device base pointers are shifted back by the first used byte so the
+// caller's offsets stay valid.  Describes the staged batch as a device Batch
+// whose results go to the io buffer.
 int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B, StageLayout *out_L)
 {
     const int64_t N = b->n_pairs;
@@ -464,19 +469,27 @@ int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B
     for (const Cp &cp : meta)
         if (cp.bytes && (e = cudaMemcpyAsync(d + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_rc(e);
-    Extents32 *X = reinterpret_cast<Extents32 *>(d + L.ext);
-    if ((e = cudaMemsetAsync(X, 0xff, 16, st)) != cudaSuccess) return cuda_rc(e);                 // q_lo, t_lo
-    if ((e = cudaMemsetAsync(reinterpret_cast<uint8_t *>(X) + 16, 0, sizeof(Extents32) - 16, st)) != cudaSuccess)
-        return cuda_rc(e);
     const PairMeta M{(const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len), (const int64_t *)(d + L.t_off),
                      (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
                      b->w_override ? (const int32_t *)(d + L.w) : nullptr};
-    if ((e = launch_extents(M, N, c->P, X, st, c->sms)) != cudaSuccess) return cuda_rc(e);
-    if ((e = cudaMemcpyAsync(c->h_ext, X, sizeof(Extents32), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        return cuda_rc(e);
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
-    const Extents32 x = *c->h_ext;
-    if (x.inval) return BSW_EINVAL;
+    Extents32 x;
+    if (N <= kHostCheckMax) {
+        Extents hx;
+        if ((rc = check_host_batch(b, c->P, &hx)) != BSW_OK) return rc;
+        x = Extents32{(unsigned long long)hx.q_lo, (unsigned long long)hx.t_lo, (unsigned long long)hx.q_hi,
+                      (unsigned long long)hx.t_hi, hx.maxn, 0u};
+    } else {
+        Extents32 *X = reinterpret_cast<Extents32 *>(d + L.ext);
+        if ((e = cudaMemsetAsync(X, 0xff, 16, st)) != cudaSuccess) return cuda_rc(e);             // q_lo, t_lo
+        if ((e = cudaMemsetAsync(reinterpret_cast<uint8_t *>(X) + 16, 0, sizeof(Extents32) - 16, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = launch_extents(M, N, c->P, X, st, c->sms)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaMemcpyAsync(c->h_ext, X, sizeof(Extents32), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+        x = *c->h_ext;
+        if (x.inval) return BSW_EINVAL;
+    }
     int64_t q_lo = (int64_t)x.q_lo, q_hi = (int64_t)x.q_hi, t_lo = (int64_t)x.t_lo, t_hi = (int64_t)x.t_hi;
     if (x.q_lo > x.q_hi) q_lo = q_hi = 0;                 // no pair with both sides non-empty
     if (x.t_lo > x.t_hi) t_lo = t_hi = 0;

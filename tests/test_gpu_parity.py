@@ -239,6 +239,26 @@ def test_invalid_inputs_and_recovery(bsw):
         assert_same(got, ref, "after errors")
 
 
+def test_invalid_inputs_large_batch(bsw):
+    """Batches above the host-check size are checked on the device before any
+    sequence is copied: the same errors, and the context stays usable."""
+    wl, ref, _ = workload_and_oracle("read151", 200_000)
+    with bsw.Context(wl.params, 16 << 30) as ctx:
+        for field, k, val in (("q_len", 99_999, -1), ("h0", 50_000, -5), ("t_off", 3, 6), ("q_len", 12, 40_000)):
+            hb = bsw.HostBatch(wl)
+            getattr(hb, field)[k] = val
+            with pytest.raises(bsw.BswError) as e:
+                ctx.extend_host(hb)
+            assert e.value.code == bsw.BSW_EINVAL, (field, k, val)
+        hb = bsw.HostBatch(wl, w_override=np.full(wl.n_pairs, 100, np.int32))
+        hb.w[777] = -1
+        with pytest.raises(bsw.BswError) as e:
+            ctx.extend_host(hb)
+        assert e.value.code == bsw.BSW_EINVAL
+        got, cells = ctx.extend_host(bsw.HostBatch(wl))
+        assert_same(got, ref, "large batch after errors")
+
+
 def test_budget_too_small(bsw):
     wl, _, _ = workload_and_oracle("plain10k")
     with bsw.Context(wl.params, mem_budget_bytes=1 << 16) as ctx:
