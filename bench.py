@@ -43,7 +43,7 @@ METRIC = "BSW GCUPS on 1 GB300 (batched vs plain kernel, bit-exact); p50/p99 ser
 # DRAM bytes read + written per launch of a workload's dominant kernel, from
 # one ncu capture of the current kernel (profiles/k_inter96_u8_read151.md);
 # other kernels and workloads report null.
-MEASURED_TRAFFIC = {("read151", "k_inter<96,u8>"): 139_456_768}
+MEASURED_TRAFFIC = {("read151", "k_inter<96,u8>"): 138_990_592}
 
 U8_NMAX = (256, 192, 128, 96, 64, 48, 32, 16)
 I16_NMAX = (256, 128, 64, 32)
