@@ -319,7 +319,24 @@ def driver_leg(bsw, args):
     ref = driver.extend_seeds(sub, nthreads=cores)
     tcpu = time.perf_counter() - t0
     k = sub.n_seeds
-    mism = int(sum((out[f][:k] != ref[f]).sum() for f in ("qb", "qe", "rb", "re", "score", "w_left", "w_right", "kept")))
+    fields = ("qb", "qe", "rb", "re", "score", "w_left", "w_right", "kept")
+    mism = int(sum((out[f][:k] != ref[f]).sum() for f in fields))
+    # the same seeds with N in 0.2% of the read bases outside the seeds and reference N runs
+    nw = W.inject_n_seeds(sw, 0.002, 0.0005, seed=4)
+    ctx.set_reference(nw.ref)
+    nprep = ctx.prepare_seeds(nw)
+    nout = np.zeros(nw.n_seeds, bsw.ALN_DTYPE)
+    ctx.extend_prepared(nprep, out=nout)
+    ntimes = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        _, ncells = ctx.extend_prepared(nprep, out=nout)
+        ntimes.append(time.perf_counter() - t0)
+    tn = statistics.median(ntimes)
+    n_first = W.SeedWorkload(nw.name, nw.params, nw.reads, nw.read_off, nw.read_len, nw.ref, sub.seed_read, sub.qbeg,
+                             sub.slen, sub.rbeg)
+    nref = driver.extend_seeds(n_first, nthreads=cores)
+    nmism = int(sum((nout[f][:k] != nref[f]).sum() for f in fields))
     ctx.close()
     return {"workload": "seeds151: 500,000 151 bp reads (read151 recipe) x 2 seeds of 19-50 bp, w 100, "
                         "2 band tries", "seeds": sw.n_seeds, "ms": round(t * 1e3, 3),
@@ -329,7 +346,11 @@ def driver_leg(bsw, args):
             "timing": "median of 5 calls, wall clock around the synchronous C-ABI call",
             "parity_sample": {"seeds_checked": k, "fields": 8, "mismatches": mism},
             "cpu_oracle": {"seeds_per_s": round(k / tcpu, 1), "cores": cores,
-                           "sample": "the first %d reads (%d seeds), %.2f s" % (nsub, k, tcpu)}}
+                           "sample": "the first %d reads (%d seeds), %.2f s" % (nsub, k, tcpu)},
+            "with_n": {"reads_n_fraction": round(float((nw.reads == 4).sum() / nw.read_len.sum()), 5),
+                       "ref_n_fraction": round(float((nw.ref == 4).mean()), 5), "ms": round(tn * 1e3, 3),
+                       "seeds_per_s": round(nw.n_seeds / tn, 1), "gcups": round(ncells / tn / 1e9, 3),
+                       "parity_sample": {"seeds_checked": k, "fields": 8, "mismatches": nmism}}}
 
 
 def n_bases_leg(bsw, wl, plan, gcups_no_n, stream):

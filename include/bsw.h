@@ -333,6 +333,11 @@ int bsw_kernel_times(bsw_ctx_t *ctx, bsw_timing_t *out);
  */
 int bsw_set_reference(bsw_ctx_t *ctx, const uint8_t *ref, int64_t ref_len);
 
+/* The same with an N bitmap of the reference (ref_n: bit p & 7 of byte p >> 3
+ * marks base p as N; (ref_len + 7) / 8 bytes; NULL: no N).  N bases score as
+ * in BSW batches (-1 against anything). */
+int bsw_set_reference_n(bsw_ctx_t *ctx, const uint8_t *ref, const uint8_t *ref_n, int64_t ref_len);
+
 typedef struct {
     int32_t read_id;   /* the seed's read, 0..n_reads-1                          */
     int32_t qbeg;      /* seed start in the read                                 */
@@ -379,6 +384,14 @@ typedef struct {
 int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_t *read_off,
                      const int32_t *read_len, int64_t n_seeds, const bsw_seed_t *seeds, int32_t max_band_try,
                      bsw_aln_t *out, int64_t *cells_out);
+
+/* The same with an N bitmap of the reads (reads_n: bit p & 7 of byte p >> 3
+ * marks read base p, as addressed by read_off, as N; NULL: no N).  With N in
+ * the reads or the reference, each side's pairs carry N bitmaps and score N
+ * as -1. */
+int bsw_extend_seeds_n(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const uint8_t *reads_n,
+                       const int64_t *read_off, const int32_t *read_len, int64_t n_seeds, const bsw_seed_t *seeds,
+                       int32_t max_band_try, bsw_aln_t *out, int64_t *cells_out);
 
 /*
  * Suffix array lookup (Section IV-D, Eq. 1: j = S[i]).

@@ -155,6 +155,10 @@ def lib():
             L.bsw_set_reference.restype = ctypes.c_int
             L.bsw_extend_seeds.argtypes = [vp, i64, vp, vp, vp, i64, vp, i32, vp, vp]
             L.bsw_extend_seeds.restype = ctypes.c_int
+            L.bsw_set_reference_n.argtypes = [vp, vp, vp, i64]
+            L.bsw_set_reference_n.restype = ctypes.c_int
+            L.bsw_extend_seeds_n.argtypes = [vp, i64, vp, vp, vp, vp, i64, vp, i32, vp, vp]
+            L.bsw_extend_seeds_n.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -271,6 +275,19 @@ def bsw_kernel_times(ctx: int) -> tuple[int, bsw_timing_t]:
 
 def bsw_set_reference(ctx: int, ref_packed: np.ndarray, ref_len: int) -> int:
     return lib().bsw_set_reference(ctx, ref_packed.ctypes.data, int(ref_len))
+
+
+def bsw_set_reference_n(ctx: int, ref_packed: np.ndarray, ref_n, ref_len: int) -> int:
+    return lib().bsw_set_reference_n(ctx, ref_packed.ctypes.data, None if ref_n is None else ref_n.ctypes.data,
+                                     int(ref_len))
+
+
+def bsw_extend_seeds_n(ctx: int, n_reads: int, reads, reads_n, read_off, read_len, seeds, max_band_try: int, out,
+                       cells) -> int:
+    return lib().bsw_extend_seeds_n(ctx, int(n_reads), reads.ctypes.data,
+                                    None if reads_n is None else reads_n.ctypes.data, read_off.ctypes.data,
+                                    read_len.ctypes.data, int(seeds.shape[0]), seeds.ctypes.data, int(max_band_try),
+                                    out.ctypes.data, ctypes.addressof(cells))
 
 
 def bsw_extend_seeds(ctx: int, n_reads: int, reads, read_off, read_len, seeds, max_band_try: int, out,
@@ -486,29 +503,32 @@ class Context:
             raise BswError(rc, "bsw_sal_lookup")
 
     def set_reference(self, ref_codes: np.ndarray) -> None:
-        """Upload a reference given as codes 0..3 (packed here)."""
-        self._ref_packed = bsw_pack_2bit(ref_codes)
-        rc = bsw_set_reference(self.handle, self._ref_packed, int(ref_codes.shape[0]))
+        """Upload a reference given as codes 0..3, or 0..4 with N (packed here)."""
+        self._ref_packed, self._ref_n = _pack(ref_codes)
+        rc = bsw_set_reference_n(self.handle, self._ref_packed, self._ref_n, int(ref_codes.shape[0]))
         if rc != BSW_OK:
-            raise BswError(rc, "bsw_set_reference")
+            raise BswError(rc, "bsw_set_reference_n")
 
     @staticmethod
     def prepare_seeds(sw):
-        """Packed reads, offsets, lengths and seed records of a SeedWorkload."""
+        """Packed reads (with an N bitmap when they hold N), offsets, lengths
+        and seed records of a SeedWorkload."""
         seeds = np.zeros(sw.n_seeds, SEED_DTYPE)
         seeds["read_id"], seeds["qbeg"], seeds["len"], seeds["rbeg"] = sw.seed_read, sw.qbeg, sw.slen, sw.rbeg
-        return (sw.n_reads, bsw_pack_2bit(sw.reads), np.ascontiguousarray(sw.read_off, np.int64),
+        packed, reads_n = _pack(sw.reads)
+        return (sw.n_reads, packed, reads_n, np.ascontiguousarray(sw.read_off, np.int64),
                 np.ascontiguousarray(sw.read_len, np.int32), seeds)
 
     def extend_prepared(self, prep, max_band_try: int = 2, out=None):
         """bsw_extend_seeds on prepare_seeds' arrays.  Returns (alignments, cells)."""
-        n_reads, reads, read_off, read_len, seeds = prep
+        n_reads, reads, reads_n, read_off, read_len, seeds = prep
         if out is None:
             out = np.zeros(seeds.shape[0], ALN_DTYPE)
         cells = ctypes.c_int64()
-        rc = bsw_extend_seeds(self.handle, n_reads, reads, read_off, read_len, seeds, max_band_try, out, cells)
+        rc = bsw_extend_seeds_n(self.handle, n_reads, reads, reads_n, read_off, read_len, seeds, max_band_try, out,
+                                cells)
         if rc != BSW_OK:
-            raise BswError(rc, "bsw_extend_seeds")
+            raise BswError(rc, "bsw_extend_seeds_n")
         return out, cells.value
 
     def extend_seeds(self, sw, max_band_try: int = 2):

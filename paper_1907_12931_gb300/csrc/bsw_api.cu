@@ -310,6 +310,7 @@ struct bsw_ctx {
     // buffers of a bsw_extend_seeds call
     DevBuf refbuf, drv, drvmeta;     // drvmeta: reads' offsets and lengths, seeds, checks
     int64_t ref_len = -1;
+    bool ref_has_n = false;          // refbuf holds an N bitmap after the packed bases
 
     // suffix array lookup: the uncompressed suffix array and staging
     DevBuf sabuf, salio;
@@ -1166,26 +1167,42 @@ int bsw_kernel_times(bsw_ctx_t *ctx, bsw_timing_t *out)
     return BSW_OK;
 }
 
-int bsw_set_reference(bsw_ctx_t *ctx, const uint8_t *ref, int64_t ref_len)
+int bsw_set_reference_n(bsw_ctx_t *ctx, const uint8_t *ref, const uint8_t *ref_n, int64_t ref_len)
 {
     if (!ctx || ref_len < 0 || (ref_len > 0 && !ref)) return BSW_EINVAL;
     if (!serving_idle(ctx)) return BSW_ESTATE;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
-    const size_t bytes = (size_t)((ref_len + 3) / 4);
+    const size_t bytes = (size_t)((ref_len + 3) / 4), nbytes = ref_n ? (size_t)((ref_len + 7) / 8) : 0;
+    const size_t n_at = align_up(bytes, 256);                 // the bitmap after the packed bases
     ctx->ref_len = -1;
-    int rc = ctx->refbuf.reserve(bytes > 0 ? bytes : 1, ctx->budget);
+    ctx->ref_has_n = false;
+    int rc = ctx->refbuf.reserve(std::max<size_t>(n_at + nbytes, 1), ctx->budget);
     if (rc != BSW_OK) return rc;
-    if (bytes) {
-        cudaError_t e = cudaMemcpy(ctx->refbuf.p, ref, bytes, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cuda_rc(e);
-    }
+    cudaError_t e;
+    if (bytes && (e = cudaMemcpy(ctx->refbuf.p, ref, bytes, cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_rc(e);
+    if (nbytes && (e = cudaMemcpy(ctx->refbuf.p + n_at, ref_n, nbytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_rc(e);
     ctx->ref_len = ref_len;
+    ctx->ref_has_n = nbytes > 0;
     return BSW_OK;
+}
+
+int bsw_set_reference(bsw_ctx_t *ctx, const uint8_t *ref, int64_t ref_len)
+{
+    return bsw_set_reference_n(ctx, ref, nullptr, ref_len);
 }
 
 int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_t *read_off,
                      const int32_t *read_len, int64_t n_seeds, const bsw_seed_t *seeds, int32_t max_band_try,
                      bsw_aln_t *out, int64_t *cells_out)
+{
+    return bsw_extend_seeds_n(ctx, n_reads, reads, nullptr, read_off, read_len, n_seeds, seeds, max_band_try, out,
+                              cells_out);
+}
+
+int bsw_extend_seeds_n(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const uint8_t *reads_n,
+                       const int64_t *read_off, const int32_t *read_len, int64_t n_seeds, const bsw_seed_t *seeds,
+                       int32_t max_band_try, bsw_aln_t *out, int64_t *cells_out)
 {
     if (!ctx || n_reads < 0 || n_seeds < 0 || n_seeds > INT32_MAX || max_band_try < 1 || max_band_try > 8)
         return BSW_EINVAL;
@@ -1222,7 +1239,7 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
     if ((e = cudaMemsetAsync(dm + o_runs, 0, om - o_runs, st)) != cudaSuccess) return cuda_rc(e);   // runs, check
     DriverCheck *chk = (DriverCheck *)(dm + o_chk);
     const DriverIn Dm{(const bsw_seed_t *)(dm + o_seeds), nullptr, (const int64_t *)(dm + o_roff),
-                      (const int32_t *)(dm + o_rlen), ctx->refbuf.p, ctx->ref_len};
+                      (const int32_t *)(dm + o_rlen), ctx->refbuf.p, ctx->ref_len, nullptr, nullptr};
     if ((e = launch_driver_check(Dm, n_reads, N, ctx->P.a, (uint32_t *)(dm + o_runs), chk, st, ctx->sms)) != cudaSuccess)
         return cuda_rc(e);
     if ((e = cudaMemcpyAsync(ctx->h_chk, chk, sizeof(DriverCheck), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
@@ -1246,6 +1263,12 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
                  o_ch0 = take(4 * (size_t)N), o_cw = take(4 * (size_t)N),
                  o_cres = take(sizeof(bsw_result_t) * (size_t)N), o_aln = take(sizeof(bsw_aln_t) * (size_t)N),
                  o_cells = take(8 * 2 * (size_t)max_band_try);
+    // N bitmaps: the reads' (read_bytes packed bytes hold 2 * read_bytes bitmap
+    // bytes' worth of bases: (read_bytes + 1) / 2 bytes) and each side's slots
+    const bool has_n = reads_n != nullptr || ctx->ref_has_n;
+    const size_t rn_bytes = reads_n ? (size_t)((read_bytes + 1) / 2) : 0;
+    const size_t o_rn = take(rn_bytes), o_qn = take(has_n ? (size_t)N * qslot / 8 : 0),
+                 o_tn = take(has_n ? (size_t)N * tslot / 8 : 0);
     bool moved = false;
     if ((rc = ctx->drv.reserve(o, ctx->budget)) != BSW_OK) return rc;
     if ((rc = lane.ensure_work(N, std::max(maxrl, kShortMax), ctx->sms, ctx->budget, &moved)) != BSW_OK) return rc;
@@ -1253,10 +1276,15 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
     uint8_t *d = ctx->drv.p;
     if (read_bytes && (e = cudaMemcpyAsync(d + o_reads, reads, (size_t)read_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_rc(e);
-    const DriverIn D{Dm.seeds, d + o_reads, Dm.read_off, Dm.read_len, ctx->refbuf.p, ctx->ref_len};
+    if (rn_bytes && (e = cudaMemcpyAsync(d + o_rn, reads_n, rn_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_rc(e);
+    const DriverIn D{Dm.seeds, d + o_reads, Dm.read_off, Dm.read_len, ctx->refbuf.p, ctx->ref_len,
+                     reads_n ? d + o_rn : nullptr,
+                     ctx->ref_has_n ? ctx->refbuf.p + align_up((size_t)((ctx->ref_len + 3) / 4), 256) : nullptr};
     const DriverSide S{d + o_q, d + o_t, (int64_t *)(d + o_qoff), (int64_t *)(d + o_toff), (int32_t *)(d + o_qlen),
                        (int32_t *)(d + o_tlen), (int32_t *)(d + o_h0), (int32_t *)(d + o_wcur),
-                       (bsw_result_t *)(d + o_res), qslot, tslot};
+                       (bsw_result_t *)(d + o_res), qslot, tslot, has_n ? d + o_qn : nullptr,
+                       has_n ? d + o_tn : nullptr};
     const DriverCompact C{(int64_t *)(d + o_cqoff), (int64_t *)(d + o_ctoff), (int32_t *)(d + o_cqlen),
                           (int32_t *)(d + o_ctlen), (int32_t *)(d + o_ch0), (int32_t *)(d + o_cw),
                           (bsw_result_t *)(d + o_cres)};
@@ -1280,7 +1308,8 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
     for (int side = 0; side < 2; ++side) {
         const bool left = side == 0;
         if ((e = launch_side(left, D, S, N, w, ctx->P.a, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
-        if ((rc = extend(Batch{N, S.q, S.q_off, S.q_len, S.t, S.t_off, S.t_len, S.h0, nullptr, S.res})) != BSW_OK)
+        if ((rc = extend(Batch{N, S.q, S.q_off, S.q_len, S.t, S.t_off, S.t_len, S.h0, nullptr, S.res, S.q_n, S.t_n})) !=
+            BSW_OK)
             return rc;
         for (int t = 1; t < max_band_try; ++t) {
             const int wt = w << (t - 1), wnext = w << t;
@@ -1293,7 +1322,8 @@ int bsw_extend_seeds(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, cons
             cnt = *ctx->h_status;
             if (cnt == 0) break;
             if ((e = launch_retry_gather(S, list, count, cnt, wnext, C, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
-            if ((rc = extend(Batch{(int64_t)cnt, S.q, C.q_off, C.q_len, S.t, C.t_off, C.t_len, C.h0, C.w, C.res})) != BSW_OK)
+            if ((rc = extend(Batch{(int64_t)cnt, S.q, C.q_off, C.q_len, S.t, C.t_off, C.t_len, C.h0, C.w, C.res, S.q_n,
+                                   S.t_n})) != BSW_OK)
                 return rc;
             if ((e = launch_retry_scatter(S, list, count, cnt, wnext, C, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
         }

@@ -27,9 +27,14 @@ __device__ __forceinline__ uint32_t base_at(const uint8_t *packed, int64_t pos)
     return (__ldg(packed + (pos >> 2)) >> (2 * (pos & 3))) & 3u;
 }
 
+__device__ __forceinline__ uint32_t n_at(const uint8_t *nm, int64_t pos)
+{
+    return nm ? (__ldg(nm + (pos >> 3)) >> (pos & 7)) & 1u : 0u;
+}
+
 // One warp per seed: the side's query and target as 2-bit packed sequences in
-// the seed's fixed slots (qslot, tslot bases, multiples of 4), plus the pair's
-// lengths, offsets and h0.
+// the seed's fixed slots (qslot, tslot bases, multiples of 16), their N
+// bitmaps when the side has them, plus the pair's lengths, offsets and h0.
 template <bool LEFT>
 __global__ void __launch_bounds__(256) k_side(DriverIn D, DriverSide S, int64_t n, int w, int match)
 {
@@ -72,6 +77,26 @@ __global__ void __launch_bounds__(256) k_side(DriverIn D, DriverSide S, int64_t 
                 if (j < tlen) v |= base_at(D.ref, LEFT ? tsrc - j : tsrc + j) << (2 * u);
             }
             S.t[(to >> 2) + b] = (uint8_t)v;
+        }
+        if (S.q_n) {                                         // slots start on a byte of the bitmaps
+            for (int b = lane; b < (qlen + 7) / 8; b += 32) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = 8 * b + u;
+                    if (j < qlen) v |= n_at(D.reads_n, LEFT ? qsrc - j : qsrc + j) << u;
+                }
+                S.q_n[(qo >> 3) + b] = (uint8_t)v;
+            }
+            for (int b = lane; b < (tlen + 7) / 8; b += 32) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = 8 * b + u;
+                    if (j < tlen) v |= n_at(D.ref_n, LEFT ? tsrc - j : tsrc + j) << u;
+                }
+                S.t_n[(to >> 3) + b] = (uint8_t)v;
+            }
         }
         if (lane == 0) {
             S.q_off[k] = qo;

@@ -108,6 +108,7 @@ struct DriverIn {
     const int32_t *read_len;
     const uint8_t *ref;
     int64_t ref_len;
+    const uint8_t *reads_n, *ref_n;   // N bitmaps (bit p & 7 of byte p >> 3), nullable
 };
 
 // One side's pairs: packed sequences in fixed per-seed slots of qslot/tslot
@@ -119,6 +120,7 @@ struct DriverSide {
     int32_t *q_len, *t_len, *h0, *w_cur;
     bsw_result_t *res;
     int qslot, tslot;
+    uint8_t *q_n, *t_n;   // N bitmaps of the slots (both or neither), nullable
 };
 
 // Checks of bsw_extend_seeds' inputs, on the device: every read's offset and

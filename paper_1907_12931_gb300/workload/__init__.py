@@ -259,6 +259,34 @@ class SeedWorkload:
         return int(self.read_len.shape[0])
 
 
+def _covered(starts, ends, total):
+    """Mask of positions [0, total) inside some [start, end)."""
+    starts = np.asarray(starts, np.int64)
+    ends = np.minimum(np.asarray(ends, np.int64), total)
+    m = np.bincount(starts, minlength=total + 1)[:total + 1] - np.bincount(ends, minlength=total + 1)[:total + 1]
+    return np.cumsum(m)[:total] > 0
+
+
+def inject_n_seeds(sw: SeedWorkload, read_rate: float, ref_runs: float, seed: int, run_max: int = 40) -> SeedWorkload:
+    """A copy of sw with N bases (code 4) outside the seeds (seeds are exact
+    matches): about a read_rate fraction of the read bases become N,
+    scattered, and about a ref_runs fraction of the reference bases start a
+    run of 1..run_max N's."""
+    rng = np.random.default_rng(seed)
+    reads, ref = sw.reads.copy(), sw.ref.copy()
+    qs = sw.read_off[sw.seed_read].astype(np.int64) + sw.qbeg
+    in_seed = _covered(qs, qs + sw.slen, reads.shape[0])
+    pos, _ = _draw_positions(sw.read_off, sw.read_len, rng.binomial(int(sw.read_len.sum()), read_rate), rng)
+    pos = pos[~in_seed[pos]]
+    reads[pos] = 4
+    k = rng.binomial(ref.shape[0], ref_runs)
+    start = rng.integers(0, ref.shape[0], k)
+    runs = _covered(start, start + rng.integers(1, run_max + 1, k), ref.shape[0])
+    ref[runs & ~_covered(sw.rbeg, sw.rbeg + sw.slen, ref.shape[0])] = 4
+    return SeedWorkload(sw.name + "+N", sw.params, reads, sw.read_off, sw.read_len, ref, sw.seed_read, sw.qbeg,
+                        sw.slen, sw.rbeg)
+
+
 # Seed workloads: read length, reads, seeds per read, seed; scoring as above, w 100, zdrop 100.
 SEED_CONFIGS = {
     "seeds151": dict(read_len=151, n_reads=500_000, spr=2, seed=11),

@@ -33,6 +33,31 @@ def test_exact_read_extends_to_both_ends():
     assert out["kept"][0] == 1 and out["w_left"][0] == 100 and out["w_right"][0] == 100
 
 
+def test_n_in_read_and_reference():
+    """R11 inside the driver.  Seed [0, 20) at p, so the left side is empty
+    and the right side starts from h0 = 20 with 20 query bases.  An N at read
+    position 30 costs 1 instead of the mismatch's 4: 20 + 10 - 1 + 9 = 38, and
+    the extension still reaches the read end (38 > 33).  An N in the
+    reference opposite read position 35 gives the same 38; both together
+    give 36; an N run of 8 reference bases opposite read positions 25-32
+    gives 20 + 5 - 8 + 7 = 24 at the read end against a local best of 25 at
+    read position 25: 24 > 25 - 5, so the read end is kept."""
+    ref = _ref(2000, seed=9)
+    p = 500
+    read = ref[p:p + 40].copy()
+    a = read.copy(); a[30] = 4
+    out = _one([a], ref, [(0, 0, 20, p)])
+    assert (out["qb"][0], out["qe"][0], out["rb"][0], out["re"][0], out["score"][0]) == (0, 40, p, p + 40, 38)
+    r2 = ref.copy(); r2[p + 35] = 4
+    out = _one([read], r2, [(0, 0, 20, p)])
+    assert (out["qe"][0], out["re"][0], out["score"][0]) == (40, p + 40, 38)
+    out = _one([a], r2, [(0, 0, 20, p)])
+    assert (out["qe"][0], out["re"][0], out["score"][0]) == (40, p + 40, 36)
+    r3 = ref.copy(); r3[p + 25:p + 33] = 4
+    out = _one([read], r3, [(0, 0, 20, p)])
+    assert (out["qe"][0], out["re"][0], out["score"][0]) == (40, p + 40, 24)
+
+
 def test_end_mismatches_clip_or_extend():
     ref = _ref(2000, seed=6)
     p = 300

@@ -112,3 +112,38 @@ def test_invalid_arguments(bsw):
         assert ei.value.code == bsw.BSW_EINVAL
         got, _ = ctx.extend_seeds(sw)                                       # the context still works
         assert got.shape[0] == sw.n_seeds
+
+
+def n_cases():
+    """Hand cases with N in reads and reference: single N, runs, N next to
+    the seed, N at the read ends, all-N read flanks."""
+    sw = hand_cases()
+    reads = [sw.reads[o:o + n].copy() for o, n in zip(sw.read_off, sw.read_len)]
+    ref = sw.ref.copy()
+    seeds = [(int(r), int(q), int(l), int(b)) for r, q, l, b in zip(sw.seed_read, sw.qbeg, sw.slen, sw.rbeg)]
+    reads[0][5] = 4                                  # N in the left flank
+    reads[0][35] = 4                                 # and in the right one
+    reads[5][:4] = 4                                 # N at the read start
+    reads[5][-3:] = 4                                # and at its end
+    ref[300 + 25:300 + 33] = 4                       # an N run opposite read 1's right flank
+    ref[1500 + 45:1500 + 47] = 4                     # N near the deletions of read 7
+    reads[8][:] = 4                                  # an all-N read against its seed's target
+    for r in reads:
+        r[r.shape[0] // 2:r.shape[0] // 2 + 1] = np.where(r.shape[0] > 60, 4, r[r.shape[0] // 2])
+    return W.seeds_from_lists(reads, ref, seeds)
+
+
+@pytest.mark.parametrize("w,tries", [(100, 2), (4, 3), (1, 1)])
+def test_n_hand_cases(bsw, w, tries):
+    sw = n_cases()
+    params = W.Params(W.Scoring(), w=w, zdrop=100, end_bonus=5)
+    compare(bsw, sw, params=params, tries=tries, what="N hand w=%d tries=%d" % (w, tries))
+
+
+@pytest.mark.parametrize("config,n_reads,w,tries", [("seeds151", 20_000, 100, 2), ("seeds250", 6_000, 8, 3)])
+def test_generated_seeds_with_n(bsw, config, n_reads, w, tries):
+    """N in 0.2% of the read bases outside the seeds and reference N runs
+    (0.05% run starts, 1-40 bases)."""
+    sw = W.inject_n_seeds(W.make_seeds(config, n_reads=n_reads), 0.002, 0.0005, seed=4)
+    params = W.Params(W.Scoring(), w=w, zdrop=100, end_bonus=5)
+    compare(bsw, sw, params=params, tries=tries, what="%s+N" % config)
