@@ -429,10 +429,10 @@ int bsw_sal_lookup(bsw_ctx_t *ctx, int64_t n_intervals, const int64_t *k, const 
  *
  * bsw_fm_build: index the reference for SMEM search.  The text is
  * T = ref + its reverse complement (the SMEM search covers both strands);
- * the call builds, on the host, the FM-indexes of T and of reverse(T)
- * (suffix arrays by induced sorting, occurrence tables in buckets of 32 BWT
- * positions) and uploads them (about 2 bytes per reference base; the
- * suffix arrays are not kept).  ref: codes 0..3, n bases, n < 2^30.
+ * the call builds, on the host, the FM-index of T (its suffix array by
+ * induced sorting, the occurrence table in buckets of 32 BWT positions) and
+ * uploads it (2 bytes per reference base; the suffix array is not kept).
+ * ref: codes 0..3, n bases, n < 2^30.
  * Errors: BSW_EINVAL, BSW_ENOMEM, BSW_EBUDGET, BSW_ECUDA, BSW_ESTATE
  * (submitted work pending).
  *
@@ -445,8 +445,12 @@ int bsw_sal_lookup(bsw_ctx_t *ctx, int64_t n_intervals, const int64_t *k, const 
  * suffix array of T.  first[r] (n_reads + 1 entries, nullable) receives the
  * index of read r's first record.  *n_out receives the number of records;
  * if it exceeds out_cap nothing is written to out and BSW_EBUDGET is
- * returned (call again with a larger out).  Device memory: about
- * 4 * n_reads * max(read_len) bytes besides the reads.
+ * returned (call again with a larger out).  Device memory: about 300 bytes
+ * per read besides the reads, plus 16 * (max(read_len) + 1) bytes per read
+ * whose search needs more than 20 match intervals at once (repeats).
+ * bsw_smem_n also takes an N bitmap of the reads (bit p & 7 of byte p >> 3
+ * marks base p as N; NULL: none): an N occurs nowhere in T, so no match
+ * contains one.
  * Errors: BSW_EINVAL, BSW_ESTATE (no index), BSW_EBUDGET, BSW_ECUDA.
  */
 typedef struct {
@@ -460,6 +464,9 @@ int bsw_fm_build(bsw_ctx_t *ctx, const uint8_t *ref, int64_t n);
 int bsw_smem(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_t *read_off,
              const int32_t *read_len, int32_t min_len, bsw_smem_t *out, int64_t out_cap, int64_t *n_out,
              int64_t *first);
+int bsw_smem_n(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const uint8_t *reads_n, const int64_t *read_off,
+               const int32_t *read_len, int32_t min_len, bsw_smem_t *out, int64_t out_cap, int64_t *n_out,
+               int64_t *first);
 
 /* Library version string. */
 const char *bsw_version(void);

@@ -151,6 +151,8 @@ def lib():
             L.bsw_fm_build.restype = ctypes.c_int
             L.bsw_smem.argtypes = [vp, i64, vp, vp, vp, i32, vp, i64, vp, vp]
             L.bsw_smem.restype = ctypes.c_int
+            L.bsw_smem_n.argtypes = [vp, i64, vp, vp, vp, vp, i32, vp, i64, vp, vp]
+            L.bsw_smem_n.restype = ctypes.c_int
             L.bsw_set_reference.argtypes = [vp, vp, i64]
             L.bsw_set_reference.restype = ctypes.c_int
             L.bsw_extend_seeds.argtypes = [vp, i64, vp, vp, vp, i64, vp, i32, vp, vp]
@@ -456,8 +458,9 @@ class Context:
         if rc != BSW_OK:
             raise BswError(rc, "bsw_fm_build")
 
-    def smem(self, reads_packed, read_off, read_len, min_len: int = 19, cap: int | None = None):
-        """SMEMs of packed reads.  Returns (structured records, first[n_reads + 1])."""
+    def smem(self, reads_packed, read_off, read_len, min_len: int = 19, cap: int | None = None, reads_n=None):
+        """SMEMs of packed reads (reads_n: their N bitmap, or None).  Returns
+        (structured records, first[n_reads + 1])."""
         read_off = np.ascontiguousarray(read_off, np.int64)
         read_len = np.ascontiguousarray(read_len, np.int32)
         n = read_len.shape[0]
@@ -466,13 +469,15 @@ class Context:
         cap = 4 * n + 16 if cap is None else cap
         while True:
             out = np.zeros(cap, SMEM_DTYPE)
-            rc = lib().bsw_smem(self.handle, n, reads_packed.ctypes.data, read_off.ctypes.data, read_len.ctypes.data,
-                                int(min_len), out.ctypes.data, cap, ctypes.addressof(n_out), first.ctypes.data)
+            rc = lib().bsw_smem_n(self.handle, n, reads_packed.ctypes.data,
+                                  None if reads_n is None else reads_n.ctypes.data, read_off.ctypes.data,
+                                  read_len.ctypes.data, int(min_len), out.ctypes.data, cap, ctypes.addressof(n_out),
+                                  first.ctypes.data)
             if rc == BSW_EBUDGET and n_out.value > cap:
                 cap = int(n_out.value)
                 continue
             if rc != BSW_OK:
-                raise BswError(rc, "bsw_smem")
+                raise BswError(rc, "bsw_smem_n")
             return out[:n_out.value], first
 
     def sal_set_index(self, sa: np.ndarray) -> None:

@@ -1448,6 +1448,13 @@ int bsw_smem(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_
              const int32_t *read_len, int32_t min_len, bsw_smem_t *out, int64_t out_cap, int64_t *n_out,
              int64_t *first)
 {
+    return bsw_smem_n(ctx, n_reads, reads, nullptr, read_off, read_len, min_len, out, out_cap, n_out, first);
+}
+
+int bsw_smem_n(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const uint8_t *reads_n, const int64_t *read_off,
+               const int32_t *read_len, int32_t min_len, bsw_smem_t *out, int64_t out_cap, int64_t *n_out,
+               int64_t *first)
+{
     if (!ctx || n_reads < 0 || min_len < 1 || out_cap < 0 || !n_out) return BSW_EINVAL;
     if (n_reads > 0 && (!reads || !read_off || !read_len)) return BSW_EINVAL;
     if (!ctx->fm_ready) return BSW_ESTATE;
@@ -1468,6 +1475,7 @@ int bsw_smem(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_
                  o_rlen = take(4 * (size_t)n_reads), o_cnt = take(8 * (size_t)n_reads),
                  o_first = take(8 * (size_t)n_reads), o_ids = take(4 * (size_t)n_reads), o_nids = take(4),
                  o_next = take(4), o_keep = take(sizeof(bsw_smem_t) * kSmemKeep * (size_t)n_reads),
+                 o_rn = take(reads_n ? (size_t)((read_bytes + 1) / 2) : 0),
                  o_out = take(sizeof(bsw_smem_t) * (size_t)std::max<int64_t>(out_cap, 1));
     int rc = ctx->smemio.reserve(o, ctx->budget);
     if (rc != BSW_OK) return rc;
@@ -1479,7 +1487,11 @@ int bsw_smem(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const int64_
         (e = cudaMemcpyAsync(d + o_rlen, read_len, 4 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(d + o_nids, 0, 4, st)) != cudaSuccess)
         return cuda_rc(e);
-    const SmemIn R{d + o_reads, (const int64_t *)(d + o_roff), (const int32_t *)(d + o_rlen), n_reads, lmax};
+    if (reads_n && read_bytes &&
+        (e = cudaMemcpyAsync(d + o_rn, reads_n, (size_t)((read_bytes + 1) / 2), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_rc(e);
+    const SmemIn R{d + o_reads, (const int64_t *)(d + o_roff), (const int32_t *)(d + o_rlen), n_reads, lmax,
+                   reads_n ? d + o_rn : nullptr};
     int32_t *ids = (int32_t *)(d + o_ids);
     uint32_t *nids = (uint32_t *)(d + o_nids);
     int64_t *dfirst = (int64_t *)(d + o_first);

@@ -115,9 +115,11 @@ __device__ __forceinline__ BiIv back_ext(const FmDev &F, const uint32_t C[5], Bi
     return BiIv{C[b] + kb, v.l + sent + above, sb, v.e};
 }
 
-__device__ __forceinline__ int read_base(const uint8_t *reads, int64_t pos)
+// Base pos of the reads: 0..3, or 4 for an N.
+__device__ __forceinline__ int read_base(const SmemIn &R, int64_t pos)
 {
-    return (__ldg(reads + (pos >> 2)) >> (2 * (pos & 3))) & 3;
+    if (R.reads_n && ((__ldg(R.reads_n + (pos >> 3)) >> (pos & 7)) & 1)) return 4;
+    return (__ldg(R.reads + (pos >> 2)) >> (2 * (pos & 3))) & 3;
 }
 
 // All SMEMs of at least min_len bases of the reads t < t_end taken from the
@@ -179,7 +181,11 @@ __device__ void smem_lanes(const SmemIn &R, const FmDev &F, const uint32_t C[5],
                     state = kRead;
                     continue;
                 }
-                const int c0 = read_base(R.reads, base + x);
+                const int c0 = read_base(R, base + x);
+                if (c0 > 3) {                                           // no match starts at an N
+                    ++x;
+                    continue;
+                }
                 v = BiIv{C[c0], C[3 - c0], C[c0 + 1] - C[c0], 0};
                 m = 0;
                 i = x + 1;
@@ -225,8 +231,9 @@ __device__ void smem_lanes(const SmemIn &R, const FmDev &F, const uint32_t C[5],
         // one extension (Algorithm 2), the same code on every lane
         const bool fwd = state == kFwd;
         const BiIv u = fwd ? BiIv{v.l, v.k, v.s, 0} : list[p * stride];
-        const int cb = read_base(R.reads, base + (fwd ? i : j));
-        BiIv w = back_ext(F, C, u, fwd ? 3 - cb : cb);
+        const int cb = read_base(R, base + (fwd ? i : j));
+        BiIv w = back_ext(F, C, u, fwd ? 3 - (cb & 3) : cb & 3);
+        if (cb > 3) w.s = 0;                                        // an N extends nothing
 
         if (fwd) {
             w = BiIv{w.l, w.k, w.s, 0};

@@ -187,6 +187,7 @@ struct SmemIn {
     const int32_t *read_len;
     int64_t n_reads;
     int lmax;
+    const uint8_t *reads_n;   // N bitmap of the reads, nullable
 };
 
 // The index of text[0..n) from its suffix array sa[0..n] (host).

@@ -94,3 +94,37 @@ def test_repetitive_reference(bsw, period):
     reads.append(np.tile(unit, 100 // period + 1)[:100].astype(np.uint8))   # the pure repeat
     for min_len in (1, 19):
         check(bsw, ref, reads, min_len)
+
+
+def test_reads_with_n(bsw):
+    """N in reads (15% of bases, and runs): matches stop at an N and start
+    after one; reads passed with their N bitmap."""
+    rng = np.random.default_rng(300)
+    ref = rng.integers(0, 4, 1500).astype(np.uint8)
+    reads = []
+    for _ in range(50):
+        L = int(rng.integers(1, 70))
+        p = int(rng.integers(0, ref.shape[0] - L))
+        x = ref[p:p + L].copy()
+        if rng.random() < 0.5:
+            x = (3 - x[::-1]).astype(np.uint8)
+        x[rng.random(L) < 0.15] = 4
+        if L > 20 and rng.random() < 0.3:
+            q = int(rng.integers(0, L - 5))
+            x[q:q + 5] = 4
+        reads.append(x)
+    reads.append(np.full(10, 4, np.uint8))
+    rl = np.array([len(r) for r in reads], np.int32)
+    off, total = W.layout(rl, 4)
+    codes = np.zeros(total, np.uint8)
+    for o, r in zip(off, reads):
+        codes[o:o + len(r)] = r
+    packed, nm = bsw.bsw_pack_2bit_n(codes)
+    for min_len in (1, 5):
+        want = smem.smems(ref, reads, min_len)
+        with bsw.Context(W.Params()) as ctx:
+            ctx.fm_build(ref)
+            got, first = ctx.smem(packed, off, rl, min_len=min_len, reads_n=nm)
+        for r, w in enumerate(want):
+            g = got[first[r]:first[r + 1]]
+            assert [tuple(int(v) for v in x) for x in g[["qbeg", "len", "k", "s"]]] == [tuple(x) for x in w], r

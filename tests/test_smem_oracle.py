@@ -9,7 +9,7 @@ from oracle import smem
 
 def brute(ref, x, min_len):
     T = "".join("ACGT"[c] for c in smem.text(ref))
-    xs = "".join("ACGT"[c] for c in x)
+    xs = "".join("ACGTN"[c] for c in x)                              # N (code 4) occurs nowhere in T
     suffixes = sorted(T[i:] + "\x00" for i in range(len(T) + 1))   # "\x00" sorts before A: the terminator
     ends = []
     for i in range(len(xs)):
@@ -61,3 +61,23 @@ def test_hand_example():
     assert got == brute(ref, x, 1)
     # min_len drops the short ones
     assert smem.smems(ref, [x], min_len=3)[0] == [g for g in got if g[1] >= 3]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_oracle_with_n_matches_brute_force(seed):
+    """Reads with N: no match contains an N, and a match may start right
+    after one."""
+    rng = np.random.default_rng(50 + seed)
+    ref = rng.integers(0, 4, 120)
+    reads = []
+    for _ in range(8):
+        L = int(rng.integers(2, 30))
+        p = int(rng.integers(0, ref.shape[0] - L))
+        x = ref[p:p + L].copy()
+        x[rng.random(L) < 0.15] = 4
+        reads.append(x)
+    reads.append(np.array([4, 4, 4]))
+    for min_len in (1, 3):
+        got = smem.smems(ref, reads, min_len)
+        for x, g in zip(reads, got):
+            assert [tuple(int(v) for v in t) for t in g] == brute(ref, x, min_len)
