@@ -447,7 +447,7 @@ int bsw_sal_lookup(bsw_ctx_t *ctx, int64_t n_intervals, const int64_t *k, const 
  * if it exceeds out_cap nothing is written to out and BSW_EBUDGET is
  * returned (call again with a larger out).  Device memory: about 300 bytes
  * per read besides the reads, plus 16 * (max(read_len) + 1) bytes per read
- * whose search needs more than 20 match intervals at once (repeats).
+ * whose search needs more than 24 match intervals at once.
  * bsw_smem_n also takes an N bitmap of the reads (bit p & 7 of byte p >> 3
  * marks base p as N; NULL: none): an N occurs nowhere in T, so no match
  * contains one.

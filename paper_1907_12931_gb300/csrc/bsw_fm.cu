@@ -294,8 +294,6 @@ __device__ __forceinline__ void load_c(const FmDev &F, uint32_t C[5])
     for (int c = 0; c < 5; ++c) C[c] = (uint32_t)F.C[c];
 }
 
-static_assert(sizeof(BiIv) * kListCap * kSmemThreads <= 48 * 1024, "lists beyond the default dynamic shared memory");
-
 // Store mode over all reads with the lists in shared memory.
 __global__ void __launch_bounds__(kSmemThreads) k_smem_store(SmemIn R, FmDev F, int min_len, SmemWork W)
 {
@@ -340,8 +338,10 @@ int grid_for(int64_t n, int per_block, int sms, int per_sm)
 cudaError_t launch_smem_store(const SmemIn &R, const FmDev &F, int min_len, const SmemWork &W, cudaStream_t st, int sms)
 {
     if (R.n_reads <= 0) return cudaSuccess;
-    const size_t smem = sizeof(BiIv) * kListCap * kSmemThreads;   // 40 KB: no opt-in needed
-    cudaError_t e = cudaMemsetAsync(W.next, 0, 4, st);
+    const size_t smem = sizeof(BiIv) * kListCap * kSmemThreads;
+    cudaError_t e = cudaFuncSetAttribute(k_smem_store, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(W.next, 0, 4, st);
     if (e != cudaSuccess) return e;
     k_smem_store<<<grid_for(R.n_reads, kSmemThreads, sms, kSmemBlocksPerSm), kSmemThreads, smem, st>>>(R, F, min_len, W);
     return cudaGetLastError();

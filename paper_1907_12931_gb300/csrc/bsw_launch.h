@@ -200,7 +200,7 @@ struct BiIv {
     uint32_t k, l, s;
     int32_t e;
 };
-constexpr int kSmemThreads = 128, kListCap = 20, kSmemBlocksPerSm = 5, kSmemKeep = 8;
+constexpr int kSmemThreads = 128, kListCap = 24, kSmemBlocksPerSm = 4, kSmemKeep = 8;
 
 // Buffers of one SMEM search.  Store mode: count[r] (-1 and r appended to
 // ovf_list[atomicAdd(ovf_n)] when the read's list exceeds kListCap) and up to
