@@ -118,23 +118,6 @@ __device__ __forceinline__ int n_bit(const uint8_t *nm, int64_t pos)
     return (__ldg(nm + (pos >> 3)) >> (pos & 7)) & 1;
 }
 
-// The first i in [from, len) whose base off + i is marked in the N bitmap, or
-// len if none.
-__device__ __forceinline__ int next_n(const uint8_t *nm, int64_t off, int from, int len)
-{
-    if (!nm || from >= len) return len;
-    const int64_t a = off + from, b = off + len;          // bits [a, b)
-    for (int64_t byte = a >> 3; byte <= (b - 1) >> 3; ++byte) {
-        uint32_t v = __ldg(nm + byte);
-        if (byte == (a >> 3)) v &= 0xffu << (a & 7);
-        if (v) {
-            const int64_t pos = byte * 8 + __ffs(v) - 1;
-            return pos < b ? (int)(pos - off) : len;
-        }
-    }
-    return len;
-}
-
 // Validate each pair, answer the empty ones, and histogram the rest by bin.
 __global__ void __launch_bounds__(512) k_classify(Batch B, Params P, Work W)
 {
