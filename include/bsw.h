@@ -58,6 +58,9 @@ extern "C" {
 #define BSW_ENOTFOUND (-6)  /* unknown or already collected ticket            */
 #define BSW_ESTATE   (-7)   /* the context cannot accept the call             */
 
+/* The longest query a batch pair may have (longer: BSW_EINVAL). */
+#define BSW_MAX_QLEN 32768
+
 /* bsw_batch_t.flags */
 #define BSW_DEVICE_PTRS   0x01u  /* every batch pointer and `out` are device pointers      */
 #define BSW_FORCE_I8      0x02u  /* 8-bit lanes for every pair up to 256 query bases,
@@ -143,7 +146,8 @@ int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonu
  * run).  In device mode it is a device int64 that the call overwrites.
  *
  * Errors: BSW_EINVAL (n_pairs < 0, null pointer, negative length or h0,
- * offset not a multiple of 4, score bound too large, bad flags), BSW_EBUDGET,
+ * offset not a multiple of 4, a query longer than BSW_MAX_QLEN, score bound
+ * h0 + match * min(q_len, t_len) of 2^30 or more, bad flags), BSW_EBUDGET,
  * BSW_ENOMEM, BSW_ECUDA.
  */
 int bsw_extend_batch(bsw_ctx_t *ctx, const bsw_batch_t *batch, bsw_result_t *out,

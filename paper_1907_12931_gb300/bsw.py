@@ -24,6 +24,7 @@ BSW_ECUDA = -4
 BSW_ETIMEOUT = -5
 BSW_ENOTFOUND = -6
 BSW_ESTATE = -7
+BSW_MAX_QLEN = 32768
 
 BSW_DEVICE_PTRS = 0x01
 BSW_FORCE_I8 = 0x02

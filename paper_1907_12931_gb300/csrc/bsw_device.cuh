@@ -10,7 +10,7 @@ namespace bsw {
 // longer ones, and every pair of the 32-bit re-run, in the warp-per-pair kernel.
 constexpr int kShortMax = 256;
 // Longest query the warp-per-pair kernel's slot scratch is sized for.
-constexpr int kLongMax = 32768;
+constexpr int kLongMax = BSW_MAX_QLEN;
 
 // Pair classes.  Classes 0-7: 8-bit lanes for query lengths (192,256],
 // (128,192], (96,128], (64,96], (48,64], (32,48], (16,32], [1,16]; 8-11:

@@ -322,3 +322,28 @@ def test_serving_rejects_and_times_out(bsw):
         if rc == bsw.BSW_PENDING:
             assert ctx.poll(t, 60_000_000) == bsw.BSW_OK
         assert ctx.poll(12345678, 0) == bsw.BSW_ENOTFOUND
+
+
+def test_maximum_query_length(bsw):
+    """Queries of BSW_MAX_QLEN bases (band 500, the long-read parameters): a
+    near-copy, an exact copy whose score leaves the 16-bit range (the 32-bit
+    kernel), and a short pair beside them; one base more is rejected."""
+    L = bsw.BSW_MAX_QLEN
+    rng = np.random.default_rng(77)
+    t = rng.integers(0, 4, L + 500).astype(np.uint8)
+    near = t[:L].copy()
+    flips = rng.random(L) < 0.05
+    near[flips] = (near[flips] + 1) % 4
+    params = W.Params(W.Scoring(), w=500, zdrop=400, end_bonus=5)
+    wl = W.from_lists([near, t[:L], t[:50]], [t, t, t[:150]], [40, 40, 20], params=params, align=4)
+    ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH)
+    assert ref[1][0] == 40 + L                        # the exact copy: h0 + L
+    for flags in (0, "plain", "i32"):
+        got, gc = run(bsw, wl, flag_of(bsw, flags), params=params)
+        assert_same(got, ref, "max qlen/%s" % flags)
+        assert gc == int(cells.sum())
+    too = W.from_lists([t[:L + 1]], [t], [40], params=params, align=4)
+    with bsw.Context(params) as ctx:
+        with pytest.raises(bsw.BswError) as e:
+            ctx.extend_host(bsw.HostBatch(too))
+        assert e.value.code == bsw.BSW_EINVAL
