@@ -138,3 +138,28 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(bsw, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         bsw.lib()
+
+
+def test_header_constants_match_binding(lib):
+    text = open(HEADER).read()
+    import re as _re
+    for name in ("BSW_MAX_QLEN", "BSW_NOALLOC_MAX_PAIRS", "BSW_NOALLOC_MAX_QLEN"):
+        m = _re.search(r"#define\s+%s\s+(\d+)" % name, text)
+        assert m, name
+        assert int(m.group(1)) == getattr(lib, name), name
+
+
+def test_inject_n_seeds_keeps_seeds_exact():
+    """N goes outside the seeds only (seeds are exact matches), at about the
+    asked rates; nothing else changes."""
+    from paper_1907_12931_gb300 import workload as W
+    sw = W.make_seeds("seeds151", n_reads=3000)
+    nw = W.inject_n_seeds(sw, 0.01, 0.0005, seed=1)
+    qs = sw.read_off[sw.seed_read].astype(np.int64) + sw.qbeg
+    for q, ln, r in zip(qs, sw.slen, sw.rbeg):
+        assert not (nw.reads[q:q + ln] == 4).any()
+        assert not (nw.ref[r:r + ln] == 4).any()
+    assert (nw.reads[nw.reads != sw.reads] == 4).all() and (nw.ref[nw.ref != sw.ref] == 4).all()
+    rate = (nw.reads == 4).sum() / sw.read_len.sum()
+    assert 0.003 < rate < 0.01
+    assert 0.003 < (nw.ref == 4).mean() < 0.02
