@@ -79,3 +79,39 @@ def test_errors(bsw, index):
         assert ei.value.code == bsw.BSW_EINVAL
         assert out[:2].cpu().tolist() == index[:2].tolist() and out[2:].cpu().tolist() == [-1, -1, -1]
         np.testing.assert_array_equal(ctx.sal_lookup(np.array([5]), np.array([4])), index[5:9])
+
+
+@pytest.mark.parametrize("layout", ["reversed", "gaps", "short_only"])
+def test_device_lookup_output_layouts(bsw, index, layout):
+    """Outputs placed at arbitrary offsets (intervals in reverse order, gaps
+    between them), and consecutive outputs of short intervals only: each
+    interval's positions land at its own offset, nothing else is written."""
+    import torch
+    k, cnt = intervals(index.shape[0], 40_000, 3)
+    if layout == "short_only":
+        cnt = np.minimum(cnt, 32).astype(np.int32)
+    if layout == "reversed":
+        off = np.zeros(k.shape[0], np.int64)
+        np.cumsum(cnt[::-1][:-1], out=off[1:])
+        off = off[::-1].copy()
+        total = int(cnt.sum())
+    elif layout == "gaps":
+        gap = np.random.default_rng(4).integers(0, 3, k.shape[0])
+        off = np.zeros(k.shape[0], np.int64)
+        np.cumsum((cnt + gap)[:-1], out=off[1:])
+        total = int(off[-1] + cnt[-1])
+    else:
+        off = np.zeros(k.shape[0], np.int64)
+        np.cumsum(cnt[:-1], out=off[1:])
+        total = int(cnt.sum())
+    want = np.full(total, -1, np.int32)
+    for a, c, o in zip(k, cnt, off):
+        want[o:o + c] = index[a:a + c]
+    with bsw.Context(W.Params()) as ctx:
+        ctx.sal_set_index(index)
+        dk, dc, do = (torch.from_numpy(x).cuda() for x in (k, cnt, off))
+        out = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+        ctx.sal_lookup_device(dk, dc, do, out)
+        ctx.sync()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
