@@ -698,14 +698,18 @@ void server_main(bsw_ctx *c)
             }
             std::vector<Request *> &reqs = c->lane_reqs[li];
             int64_t pairs = 0, ecells = 0;
-            while (!c->queue.empty() &&
-                   (reqs.empty() || (pairs + c->queue.front()->b.n_pairs <= kMergePairs &&
-                                     ecells + c->queue.front()->ext.est_cells <= kMergeCells))) {
-                pairs += c->queue.front()->b.n_pairs;
-                ecells += c->queue.front()->ext.est_cells;
-                reqs.push_back(c->queue.front());
-                c->queue.pop_front();
+            try {                        // a request moves to the lane only once the lane's list holds it
+                while (!c->queue.empty() &&
+                       (reqs.empty() || (pairs + c->queue.front()->b.n_pairs <= kMergePairs &&
+                                         ecells + c->queue.front()->ext.est_cells <= kMergeCells))) {
+                    reqs.push_back(c->queue.front());
+                    pairs += c->queue.front()->b.n_pairs;
+                    ecells += c->queue.front()->ext.est_cells;
+                    c->queue.pop_front();
+                }
+            } catch (...) {
             }
+            if (reqs.empty()) break;     // no memory for the list: try again on the next wake-up
             c->lane_busy[li] = true;
             lk.unlock();
             int rc = serve_launch(c, li);
@@ -713,8 +717,15 @@ void server_main(bsw_ctx *c)
             if (rc == BSW_EBUDGET) {
                 bool others = false;
                 for (int k = 0; k < kServeLanes; ++k) others |= (k != li && c->lane_busy[k]);
+                bool requeued = false;
                 if (others) {   // wait for memory held by other lanes
-                    for (auto it = reqs.rbegin(); it != reqs.rend(); ++it) c->queue.push_front(*it);
+                    try {           // an insert at the front either takes them all or changes nothing
+                        c->queue.insert(c->queue.begin(), reqs.begin(), reqs.end());
+                        requeued = true;
+                    } catch (...) {
+                    }
+                }
+                if (requeued) {
                     reqs.clear();
                     c->lane_busy[li] = false;
                     c->serve_lane[li].io.release(c->budget);
@@ -750,6 +761,19 @@ bool serving_idle(bsw_ctx *c)
 }  // namespace
 
 // ------------------------------------------------------------------- C ABI
+
+// No C++ exception crosses the C ABI: the entry points that use the C++
+// library's containers or threads run their bodies through guard, which turns
+// a failed allocation (or any other exception) into BSW_ENOMEM.
+template <class F>
+int guard(F &&f)
+{
+    try {
+        return f();
+    } catch (...) {
+        return BSW_ENOMEM;
+    }
+}
 
 extern "C" {
 
@@ -861,24 +885,26 @@ int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonu
 
 int bsw_extend_batch(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, int64_t *cells_out, void *stream)
 {
-    if (!ctx || !b) return BSW_EINVAL;
-    if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~kKnownFlags)) return BSW_EINVAL;
-    const uint32_t forced = b->flags & (BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32);
-    if (forced & (forced - 1)) return BSW_EINVAL;
-    const bool dev = (b->flags & BSW_DEVICE_PTRS) != 0;
-    // events inside a captured graph would not time this call's kernels
-    if (dev && (b->flags & BSW_TIME_KERNELS) && !(b->flags & BSW_NO_GRAPH)) return BSW_EINVAL;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
-    if (b->n_pairs == 0) {
-        if (cells_out) {
-            if (dev) return cuda_rc(cudaMemsetAsync(cells_out, 0, 8, (cudaStream_t)stream));
-            *cells_out = 0;
+    return guard([&]() -> int {
+        if (!ctx || !b) return BSW_EINVAL;
+        if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~kKnownFlags)) return BSW_EINVAL;
+        const uint32_t forced = b->flags & (BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32);
+        if (forced & (forced - 1)) return BSW_EINVAL;
+        const bool dev = (b->flags & BSW_DEVICE_PTRS) != 0;
+        // events inside a captured graph would not time this call's kernels
+        if (dev && (b->flags & BSW_TIME_KERNELS) && !(b->flags & BSW_NO_GRAPH)) return BSW_EINVAL;
+        if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+        if (b->n_pairs == 0) {
+            if (cells_out) {
+                if (dev) return cuda_rc(cudaMemsetAsync(cells_out, 0, 8, (cudaStream_t)stream));
+                *cells_out = 0;
+            }
+            return BSW_OK;
         }
-        return BSW_OK;
-    }
-    if (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out) return BSW_EINVAL;
-    if (dev) return extend_device(ctx, b, out, cells_out, (cudaStream_t)stream);
-    return extend_host(ctx, b, out, cells_out, (cudaStream_t)stream);
+        if (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out) return BSW_EINVAL;
+        if (dev) return extend_device(ctx, b, out, cells_out, (cudaStream_t)stream);
+        return extend_host(ctx, b, out, cells_out, (cudaStream_t)stream);
+    });
 }
 
 int bsw_sync(bsw_ctx_t *ctx, void *stream)
@@ -896,74 +922,76 @@ int bsw_sync(bsw_ctx_t *ctx, void *stream)
 
 int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, uint64_t *ticket)
 {
-    if (!ctx || !b || !ticket) return BSW_EINVAL;
-    if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~kKnownFlags)) return BSW_EINVAL;
-    if (b->flags & (BSW_DEVICE_PTRS | BSW_PLAIN_KERNEL | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32 |
-                    BSW_TIME_KERNELS))
-        return BSW_EINVAL;   // the serving loop runs the context's batched plan on host inputs
-    if (b->q_n || b->t_n) return BSW_EINVAL;   // no N bitmaps in the serving loop
-    if (b->n_pairs > 0 && (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out))
-        return BSW_EINVAL;
-    Request *r = new (std::nothrow) Request();
-    if (!r) return BSW_ENOMEM;
-    r->b = *b;
-    r->out = out;
-    int rc = check_host_batch(b, ctx->P, &r->ext);
-    if (rc == BSW_OK) {
-        const int64_t N = b->n_pairs;
-        IoLayout L = io_layout(N, r->ext.q_hi - r->ext.q_lo, r->ext.t_hi - r->ext.t_lo);
-        WorkLayout W = work_layout(N, slot_bytes_for(std::max(r->ext.maxn, kShortMax)), warp_slots_needed(ctx->sms));
-        if ((int64_t)(L.total + W.total) > ctx->budget.cap) rc = BSW_EBUDGET;
-    }
-    if (rc == BSW_OK && (b->flags & BSW_COPY_INPUTS) && b->n_pairs > 0) {
-        const int64_t N = b->n_pairs;
-        const size_t qb = (size_t)(r->ext.q_hi - r->ext.q_lo), tb = (size_t)(r->ext.t_hi - r->ext.t_lo);
-        const size_t total = qb + tb + 8 * (size_t)N * 2 + 4 * (size_t)N * (b->w_override ? 4 : 3);
-        try {
-            r->own.resize(total);
-        } catch (...) {
-            rc = BSW_ENOMEM;
-        }
+    return guard([&]() -> int {
+        if (!ctx || !b || !ticket) return BSW_EINVAL;
+        if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~kKnownFlags)) return BSW_EINVAL;
+        if (b->flags & (BSW_DEVICE_PTRS | BSW_PLAIN_KERNEL | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32 |
+                        BSW_TIME_KERNELS))
+            return BSW_EINVAL;   // the serving loop runs the context's batched plan on host inputs
+        if (b->q_n || b->t_n) return BSW_EINVAL;   // no N bitmaps in the serving loop
+        if (b->n_pairs > 0 && (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out))
+            return BSW_EINVAL;
+        Request *r = new (std::nothrow) Request();
+        if (!r) return BSW_ENOMEM;
+        r->b = *b;
+        r->out = out;
+        int rc = check_host_batch(b, ctx->P, &r->ext);
         if (rc == BSW_OK) {
-            uint8_t *p = r->own.data();
-            std::memcpy(p, b->q + r->ext.q_lo, qb);
-            r->b.q = p - r->ext.q_lo;   // keep the caller's offsets valid
-            p += qb;
-            std::memcpy(p, b->t + r->ext.t_lo, tb);
-            r->b.t = p - r->ext.t_lo;
-            p += tb;
-            auto dup = [&](const void *src, size_t bytes) { std::memcpy(p, src, bytes); void *d = p; p += bytes; return d; };
-            r->b.q_off = (const int64_t *)dup(b->q_off, 8 * (size_t)N);
-            r->b.t_off = (const int64_t *)dup(b->t_off, 8 * (size_t)N);
-            r->b.q_len = (const int32_t *)dup(b->q_len, 4 * (size_t)N);
-            r->b.t_len = (const int32_t *)dup(b->t_len, 4 * (size_t)N);
-            r->b.h0 = (const int32_t *)dup(b->h0, 4 * (size_t)N);
-            if (b->w_override) r->b.w_override = (const int32_t *)dup(b->w_override, 4 * (size_t)N);
+            const int64_t N = b->n_pairs;
+            IoLayout L = io_layout(N, r->ext.q_hi - r->ext.q_lo, r->ext.t_hi - r->ext.t_lo);
+            WorkLayout W = work_layout(N, slot_bytes_for(std::max(r->ext.maxn, kShortMax)), warp_slots_needed(ctx->sms));
+            if ((int64_t)(L.total + W.total) > ctx->budget.cap) rc = BSW_EBUDGET;
         }
-    }
-    if (rc != BSW_OK) {
-        delete r;
-        return rc;
-    }
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    if (ctx->stop) {
-        delete r;
-        return BSW_ESTATE;
-    }
-    r->ticket = ctx->next_ticket++;
-    *ticket = r->ticket;
-    ctx->tickets[r->ticket] = r;
-    if (b->n_pairs == 0) {
-        r->status = BSW_OK;
+        if (rc == BSW_OK && (b->flags & BSW_COPY_INPUTS) && b->n_pairs > 0) {
+            const int64_t N = b->n_pairs;
+            const size_t qb = (size_t)(r->ext.q_hi - r->ext.q_lo), tb = (size_t)(r->ext.t_hi - r->ext.t_lo);
+            const size_t total = qb + tb + 8 * (size_t)N * 2 + 4 * (size_t)N * (b->w_override ? 4 : 3);
+            try {
+                r->own.resize(total);
+            } catch (...) {
+                rc = BSW_ENOMEM;
+            }
+            if (rc == BSW_OK) {
+                uint8_t *p = r->own.data();
+                std::memcpy(p, b->q + r->ext.q_lo, qb);
+                r->b.q = p - r->ext.q_lo;   // keep the caller's offsets valid
+                p += qb;
+                std::memcpy(p, b->t + r->ext.t_lo, tb);
+                r->b.t = p - r->ext.t_lo;
+                p += tb;
+                auto dup = [&](const void *src, size_t bytes) { std::memcpy(p, src, bytes); void *d = p; p += bytes; return d; };
+                r->b.q_off = (const int64_t *)dup(b->q_off, 8 * (size_t)N);
+                r->b.t_off = (const int64_t *)dup(b->t_off, 8 * (size_t)N);
+                r->b.q_len = (const int32_t *)dup(b->q_len, 4 * (size_t)N);
+                r->b.t_len = (const int32_t *)dup(b->t_len, 4 * (size_t)N);
+                r->b.h0 = (const int32_t *)dup(b->h0, 4 * (size_t)N);
+                if (b->w_override) r->b.w_override = (const int32_t *)dup(b->w_override, 4 * (size_t)N);
+            }
+        }
+        if (rc != BSW_OK) {
+            delete r;
+            return rc;
+        }
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ctx->stop) {
+            delete r;
+            return BSW_ESTATE;
+        }
+        r->ticket = ctx->next_ticket++;
+        *ticket = r->ticket;
+        ctx->tickets[r->ticket] = r;
+        if (b->n_pairs == 0) {
+            r->status = BSW_OK;
+            return BSW_OK;
+        }
+        ctx->queue.push_back(r);
+        if (!ctx->server_started) {
+            ctx->server = std::thread(server_main, ctx);
+            ctx->server_started = true;
+        }
+        ctx->cv_work.notify_one();
         return BSW_OK;
-    }
-    ctx->queue.push_back(r);
-    if (!ctx->server_started) {
-        ctx->server = std::thread(server_main, ctx);
-        ctx->server_started = true;
-    }
-    ctx->cv_work.notify_one();
-    return BSW_OK;
+    });
 }
 
 int bsw_stream_poll(bsw_ctx_t *ctx, uint64_t ticket, int32_t timeout_us)
@@ -1012,144 +1040,146 @@ int bsw_set_plan(bsw_ctx_t *ctx, const bsw_plan_t *plan)
 
 int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int32_t reps, bsw_plan_t *chosen)
 {
-    if (!ctx || !b) return BSW_EINVAL;
-    if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~BSW_DEVICE_PTRS)) return BSW_EINVAL;
-    if (!serving_idle(ctx)) return BSW_ESTATE;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
-    const int64_t ns = std::min<int64_t>(b->n_pairs, sample_pairs > 0 ? sample_pairs : kTuneSample);
-    if (reps <= 0) reps = 3;
-    if (ns == 0) {
-        if (chosen) *chosen = ctx->pub_plan;
-        return BSW_OK;
-    }
-    if (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0) return BSW_EINVAL;
-    bsw_batch_t sb = *b;
-    sb.n_pairs = ns;
-    Lane &lane = ctx->sync;
-    Batch B;
-    int rc;
-    if (b->flags & BSW_DEVICE_PTRS) {
-        bool moved = false;
-        if ((rc = lane.ensure_work(ns, kLongMax, ctx->sms, ctx->budget, &moved)) != BSW_OK) return rc;
-        if (moved) clear_graphs(ctx);
-        if ((rc = lane.io.reserve(sizeof(bsw_result_t) * (size_t)ns, ctx->budget)) != BSW_OK) return rc;
-        B = Batch{ns, sb.q, sb.q_off, sb.q_len, sb.t, sb.t_off, sb.t_len, sb.h0, sb.w_override,
-                  (bsw_result_t *)lane.io.p, sb.q_n, sb.t_n};
-    } else {
-        StageLayout L;
-        if ((rc = stage_host(ctx, &sb, nullptr, &B, &L)) != BSW_OK) return rc;
-    }
-    const Work W = make_work(lane.work.p, lane.wl);
-    const bool can_pack = packed_scoring_ok(ctx->P);
+    return guard([&]() -> int {
+        if (!ctx || !b) return BSW_EINVAL;
+        if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~BSW_DEVICE_PTRS)) return BSW_EINVAL;
+        if (!serving_idle(ctx)) return BSW_ESTATE;
+        if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+        const int64_t ns = std::min<int64_t>(b->n_pairs, sample_pairs > 0 ? sample_pairs : kTuneSample);
+        if (reps <= 0) reps = 3;
+        if (ns == 0) {
+            if (chosen) *chosen = ctx->pub_plan;
+            return BSW_OK;
+        }
+        if (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0) return BSW_EINVAL;
+        bsw_batch_t sb = *b;
+        sb.n_pairs = ns;
+        Lane &lane = ctx->sync;
+        Batch B;
+        int rc;
+        if (b->flags & BSW_DEVICE_PTRS) {
+            bool moved = false;
+            if ((rc = lane.ensure_work(ns, kLongMax, ctx->sms, ctx->budget, &moved)) != BSW_OK) return rc;
+            if (moved) clear_graphs(ctx);
+            if ((rc = lane.io.reserve(sizeof(bsw_result_t) * (size_t)ns, ctx->budget)) != BSW_OK) return rc;
+            B = Batch{ns, sb.q, sb.q_off, sb.q_len, sb.t, sb.t_off, sb.t_len, sb.h0, sb.w_override,
+                      (bsw_result_t *)lane.io.p, sb.q_n, sb.t_n};
+        } else {
+            StageLayout L;
+            if ((rc = stage_host(ctx, &sb, nullptr, &B, &L)) != BSW_OK) return rc;
+        }
+        const Work W = make_work(lane.work.p, lane.wl);
+        const bool can_pack = packed_scoring_ok(ctx->P);
 
-    // One candidate: a warm-up launch, then the fastest of reps, timed with
-    // events on the lane's stream (the batched path joins its side streams
-    // back into it).  counts receives the pairs each class held.
-    auto time_plan = [&](const bsw_plan_t &k, float *ms, int32_t *counts) -> int {
-        Plan L;
-        if (!make_plan(k.short_max, k.u8_bounds, k.i16_bounds, k.packed != 0, k.warp_cols, k.inter_warps, &L))
-            return BSW_EINVAL;
-        float best = 0.0f;
-        for (int r = 0; r <= reps; ++r) {
-            cudaError_t e;
-            if ((e = cudaEventRecord(ctx->tune_ev[0], lane.S.main)) != cudaSuccess) return cuda_rc(e);
-            if ((e = enqueue_launch(ctx, lane, lane.S, B, W, 0u, true, L)) != cudaSuccess) {
-                lane.work_dirty = true;
-                return cuda_rc(e);
+        // One candidate: a warm-up launch, then the fastest of reps, timed with
+        // events on the lane's stream (the batched path joins its side streams
+        // back into it).  counts receives the pairs each class held.
+        auto time_plan = [&](const bsw_plan_t &k, float *ms, int32_t *counts) -> int {
+            Plan L;
+            if (!make_plan(k.short_max, k.u8_bounds, k.i16_bounds, k.packed != 0, k.warp_cols, k.inter_warps, &L))
+                return BSW_EINVAL;
+            float best = 0.0f;
+            for (int r = 0; r <= reps; ++r) {
+                cudaError_t e;
+                if ((e = cudaEventRecord(ctx->tune_ev[0], lane.S.main)) != cudaSuccess) return cuda_rc(e);
+                if ((e = enqueue_launch(ctx, lane, lane.S, B, W, 0u, true, L)) != cudaSuccess) {
+                    lane.work_dirty = true;
+                    return cuda_rc(e);
+                }
+                if ((e = cudaEventRecord(ctx->tune_ev[1], lane.S.main)) != cudaSuccess) return cuda_rc(e);
+                if ((e = cudaEventSynchronize(ctx->tune_ev[1])) != cudaSuccess) {
+                    lane.work_dirty = true;
+                    return cuda_rc(e);
+                }
+                float t = 0.0f;
+                if ((e = cudaEventElapsedTime(&t, ctx->tune_ev[0], ctx->tune_ev[1])) != cudaSuccess) return cuda_rc(e);
+                if (r == 1 || (r > 1 && t < best)) best = t;
             }
-            if ((e = cudaEventRecord(ctx->tune_ev[1], lane.S.main)) != cudaSuccess) return cuda_rc(e);
-            if ((e = cudaEventSynchronize(ctx->tune_ev[1])) != cudaSuccess) {
-                lane.work_dirty = true;
+            cudaError_t e = cudaMemcpy(ctx->h_status, W.status, 4, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_rc(e);
+            if (*ctx->h_status) return BSW_EINVAL;
+            if ((e = cudaMemcpy(counts, W.cls_count, 4 * (kNumClass + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
                 return cuda_rc(e);
-            }
+            *ms = best;
+            return BSW_OK;
+        };
+
+        // Coordinate descent.  Knobs that only affect classes the sample leaves
+        // empty are not timed (their differences would be noise), and the
+        // boundary of a class the sample leaves empty is removed outright (one
+        // launch fewer, the same work).
+        bsw_plan_t best{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0.0f};
+        float tbest = 0.0f;
+        int32_t cnt[kNumClass + 1], cnt_best[kNumClass + 1];
+        if ((rc = time_plan(best, &tbest, cnt_best)) != BSW_OK) return rc;
+        auto consider = [&](const bsw_plan_t &k) -> int {
             float t = 0.0f;
-            if ((e = cudaEventElapsedTime(&t, ctx->tune_ev[0], ctx->tune_ev[1])) != cudaSuccess) return cuda_rc(e);
-            if (r == 1 || (r > 1 && t < best)) best = t;
+            const int r = time_plan(k, &t, cnt);
+            if (r == BSW_OK && t < 0.99f * tbest) {
+                best = k;
+                tbest = t;
+                std::memcpy(cnt_best, cnt, sizeof(cnt));
+            }
+            return r;
+        };
+        for (int sm : {192, 128, 96, 64}) {
+            bsw_plan_t k = best;
+            k.short_max = sm;
+            if ((rc = consider(k)) != BSW_OK) return rc;
         }
-        cudaError_t e = cudaMemcpy(ctx->h_status, W.status, 4, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_rc(e);
-        if (*ctx->h_status) return BSW_EINVAL;
-        if ((e = cudaMemcpy(counts, W.cls_count, 4 * (kNumClass + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return cuda_rc(e);
-        *ms = best;
+        auto any = [&](int c0, int c1) {   // classes [c0, c1) hold pairs under the best plan
+            for (int c = c0; c < c1; ++c)
+                if (cnt_best[c] > 0) return true;
+            return false;
+        };
+        if (any(kClsW16, kClsW16 + 1))
+            for (int cols : {4, 16}) {
+                bsw_plan_t k = best;
+                k.warp_cols = cols;
+                if ((rc = consider(k)) != BSW_OK) return rc;
+            }
+        if (can_pack && any(2, 8)) {       // the 8-bit classes of bound 128 and below
+            bsw_plan_t k = best;
+            k.packed = 1;
+            if ((rc = consider(k)) != BSW_OK) return rc;
+        }
+        if (any(0, kClsW16))
+            for (int wp : {1, 4}) {
+                bsw_plan_t k = best;
+                k.inter_warps = wp;
+                if ((rc = consider(k)) != BSW_OK) return rc;
+            }
+        // Class boundaries: removing boundary c moves class c's pairs into the
+        // next larger kept class.
+        for (int bit = 1; bit < 8; ++bit) {
+            if (!((best.u8_bounds >> bit) & 1u)) continue;
+            bsw_plan_t k = best;
+            k.u8_bounds &= ~(1u << bit);
+            if (cnt_best[bit] == 0) {
+                best = k;
+                continue;
+            }
+            if ((rc = consider(k)) != BSW_OK) return rc;
+        }
+        for (int bit = 1; bit < 4; ++bit) {
+            if (!((best.i16_bounds >> bit) & 1u)) continue;
+            bsw_plan_t k = best;
+            k.i16_bounds &= ~(1u << bit);
+            if (cnt_best[8 + bit] == 0) {
+                best = k;
+                continue;
+            }
+            if ((rc = consider(k)) != BSW_OK) return rc;
+        }
+        if ((rc = time_plan(best, &tbest, cnt)) != BSW_OK) return rc;
+        make_plan(best.short_max, best.u8_bounds, best.i16_bounds, best.packed != 0, best.warp_cols, best.inter_warps,
+                  &ctx->plan);
+        best.ms = tbest;
+        ctx->pub_plan = best;
+        clear_graphs(ctx);
+        if (chosen) *chosen = best;
         return BSW_OK;
-    };
-
-    // Coordinate descent.  Knobs that only affect classes the sample leaves
-    // empty are not timed (their differences would be noise), and the
-    // boundary of a class the sample leaves empty is removed outright (one
-    // launch fewer, the same work).
-    bsw_plan_t best{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0.0f};
-    float tbest = 0.0f;
-    int32_t cnt[kNumClass + 1], cnt_best[kNumClass + 1];
-    if ((rc = time_plan(best, &tbest, cnt_best)) != BSW_OK) return rc;
-    auto consider = [&](const bsw_plan_t &k) -> int {
-        float t = 0.0f;
-        const int r = time_plan(k, &t, cnt);
-        if (r == BSW_OK && t < 0.99f * tbest) {
-            best = k;
-            tbest = t;
-            std::memcpy(cnt_best, cnt, sizeof(cnt));
-        }
-        return r;
-    };
-    for (int sm : {192, 128, 96, 64}) {
-        bsw_plan_t k = best;
-        k.short_max = sm;
-        if ((rc = consider(k)) != BSW_OK) return rc;
-    }
-    auto any = [&](int c0, int c1) {   // classes [c0, c1) hold pairs under the best plan
-        for (int c = c0; c < c1; ++c)
-            if (cnt_best[c] > 0) return true;
-        return false;
-    };
-    if (any(kClsW16, kClsW16 + 1))
-        for (int cols : {4, 16}) {
-            bsw_plan_t k = best;
-            k.warp_cols = cols;
-            if ((rc = consider(k)) != BSW_OK) return rc;
-        }
-    if (can_pack && any(2, 8)) {       // the 8-bit classes of bound 128 and below
-        bsw_plan_t k = best;
-        k.packed = 1;
-        if ((rc = consider(k)) != BSW_OK) return rc;
-    }
-    if (any(0, kClsW16))
-        for (int wp : {1, 4}) {
-            bsw_plan_t k = best;
-            k.inter_warps = wp;
-            if ((rc = consider(k)) != BSW_OK) return rc;
-        }
-    // Class boundaries: removing boundary c moves class c's pairs into the
-    // next larger kept class.
-    for (int bit = 1; bit < 8; ++bit) {
-        if (!((best.u8_bounds >> bit) & 1u)) continue;
-        bsw_plan_t k = best;
-        k.u8_bounds &= ~(1u << bit);
-        if (cnt_best[bit] == 0) {
-            best = k;
-            continue;
-        }
-        if ((rc = consider(k)) != BSW_OK) return rc;
-    }
-    for (int bit = 1; bit < 4; ++bit) {
-        if (!((best.i16_bounds >> bit) & 1u)) continue;
-        bsw_plan_t k = best;
-        k.i16_bounds &= ~(1u << bit);
-        if (cnt_best[8 + bit] == 0) {
-            best = k;
-            continue;
-        }
-        if ((rc = consider(k)) != BSW_OK) return rc;
-    }
-    if ((rc = time_plan(best, &tbest, cnt)) != BSW_OK) return rc;
-    make_plan(best.short_max, best.u8_bounds, best.i16_bounds, best.packed != 0, best.warp_cols, best.inter_warps,
-              &ctx->plan);
-    best.ms = tbest;
-    ctx->pub_plan = best;
-    clear_graphs(ctx);
-    if (chosen) *chosen = best;
-    return BSW_OK;
+    });
 }
 
 int bsw_kernel_times(bsw_ctx_t *ctx, bsw_timing_t *out)
@@ -1204,145 +1234,147 @@ int bsw_extend_seeds_n(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, co
                        const int64_t *read_off, const int32_t *read_len, int64_t n_seeds, const bsw_seed_t *seeds,
                        int32_t max_band_try, bsw_aln_t *out, int64_t *cells_out)
 {
-    if (!ctx || n_reads < 0 || n_seeds < 0 || n_seeds > INT32_MAX || max_band_try < 1 || max_band_try > 8)
-        return BSW_EINVAL;
-    if (n_seeds > 0 && (!reads || !read_off || !read_len || !seeds || !out)) return BSW_EINVAL;
-    if (ctx->ref_len < 0) return BSW_ESTATE;
-    if (!serving_idle(ctx)) return BSW_ESTATE;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
-    if (cells_out) *cells_out = 0;
-    if (n_seeds == 0) return BSW_OK;
-    const int w = ctx->P.w;
-    if ((int64_t)w << (max_band_try - 1) > (1 << 20)) return BSW_EINVAL;
+    return guard([&]() -> int {
+        if (!ctx || n_reads < 0 || n_seeds < 0 || n_seeds > INT32_MAX || max_band_try < 1 || max_band_try > 8)
+            return BSW_EINVAL;
+        if (n_seeds > 0 && (!reads || !read_off || !read_len || !seeds || !out)) return BSW_EINVAL;
+        if (ctx->ref_len < 0) return BSW_ESTATE;
+        if (!serving_idle(ctx)) return BSW_ESTATE;
+        if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+        if (cells_out) *cells_out = 0;
+        if (n_seeds == 0) return BSW_OK;
+        const int w = ctx->P.w;
+        if ((int64_t)w << (max_band_try - 1) > (1 << 20)) return BSW_EINVAL;
 
-    // Checks on the device (launch_driver_check): reads, seeds inside their
-    // read and the reference, each read's seeds consecutive, the score bound;
-    // they also give the packed-read extent and the longest read.
-    const int64_t N = n_seeds;
-    Lane &lane = ctx->sync;
-    cudaStream_t st = lane.S.main;
-    cudaError_t e;
-    size_t om = 0;
-    auto take_m = [&](size_t bytes) { size_t r = om; om = align_up(om + bytes, 256); return r; };
-    const size_t o_roff = take_m(8 * (size_t)n_reads), o_rlen = take_m(4 * (size_t)n_reads),
-                 o_seeds = take_m(sizeof(bsw_seed_t) * (size_t)N), o_runs = take_m(4 * (size_t)n_reads),
-                 o_chk = take_m(sizeof(DriverCheck));
-    int rc = ctx->drvmeta.reserve(om, ctx->budget);
-    if (rc != BSW_OK) return rc;
-    uint8_t *dm = ctx->drvmeta.p;
-    const struct { size_t off; const void *src; size_t bytes; } meta[] = {
-        {o_roff, read_off, 8 * (size_t)n_reads}, {o_rlen, read_len, 4 * (size_t)n_reads},
-        {o_seeds, seeds, sizeof(bsw_seed_t) * (size_t)N}};
-    for (const auto &cp : meta)
-        if (cp.bytes && (e = cudaMemcpyAsync(dm + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_rc(e);
-    if ((e = cudaMemsetAsync(dm + o_runs, 0, om - o_runs, st)) != cudaSuccess) return cuda_rc(e);   // runs, check
-    DriverCheck *chk = (DriverCheck *)(dm + o_chk);
-    const DriverIn Dm{(const bsw_seed_t *)(dm + o_seeds), nullptr, (const int64_t *)(dm + o_roff),
-                      (const int32_t *)(dm + o_rlen), ctx->refbuf.p, ctx->ref_len, nullptr, nullptr};
-    if ((e = launch_driver_check(Dm, n_reads, N, ctx->P.a, (uint32_t *)(dm + o_runs), chk, st, ctx->sms)) != cudaSuccess)
-        return cuda_rc(e);
-    if ((e = cudaMemcpyAsync(ctx->h_chk, chk, sizeof(DriverCheck), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_rc(e);
-    if (ctx->h_chk->inval) return BSW_EINVAL;
-    const int64_t read_bytes = (int64_t)ctx->h_chk->read_bytes;
-    const int maxrl = ctx->h_chk->maxrl;
-
-    // Device layout: the reads, one side's pairs, the retry batch, the alignments.
-    const int qslot = (int)align_up((size_t)std::max(maxrl, 1), 16);
-    const int tslot = (int)align_up((size_t)maxrl + (size_t)w + 4, 16);
-    size_t o = 0;
-    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
-    const size_t o_reads = take((size_t)read_bytes),
-                 o_q = take((size_t)N * qslot / 4), o_t = take((size_t)N * tslot / 4), o_qoff = take(8 * (size_t)N),
-                 o_toff = take(8 * (size_t)N), o_qlen = take(4 * (size_t)N), o_tlen = take(4 * (size_t)N),
-                 o_h0 = take(4 * (size_t)N), o_wcur = take(4 * (size_t)N), o_res = take(sizeof(bsw_result_t) * (size_t)N),
-                 o_list = take(4 * (size_t)N), o_count = take(4), o_cqoff = take(8 * (size_t)N),
-                 o_ctoff = take(8 * (size_t)N), o_cqlen = take(4 * (size_t)N), o_ctlen = take(4 * (size_t)N),
-                 o_ch0 = take(4 * (size_t)N), o_cw = take(4 * (size_t)N),
-                 o_cres = take(sizeof(bsw_result_t) * (size_t)N), o_aln = take(sizeof(bsw_aln_t) * (size_t)N),
-                 o_cells = take(8 * 2 * (size_t)max_band_try);
-    // N bitmaps: the reads' (read_bytes packed bytes hold 2 * read_bytes bitmap
-    // bytes' worth of bases: (read_bytes + 1) / 2 bytes) and each side's slots
-    const bool has_n = reads_n != nullptr || ctx->ref_has_n;
-    const size_t rn_bytes = reads_n ? (size_t)((read_bytes + 1) / 2) : 0;
-    const size_t o_rn = take(rn_bytes), o_qn = take(has_n ? (size_t)N * qslot / 8 : 0),
-                 o_tn = take(has_n ? (size_t)N * tslot / 8 : 0);
-    bool moved = false;
-    if ((rc = ctx->drv.reserve(o, ctx->budget)) != BSW_OK) return rc;
-    if ((rc = lane.ensure_work(N, std::max(maxrl, kShortMax), ctx->sms, ctx->budget, &moved)) != BSW_OK) return rc;
-    if (moved) clear_graphs(ctx);
-    uint8_t *d = ctx->drv.p;
-    if (read_bytes && (e = cudaMemcpyAsync(d + o_reads, reads, (size_t)read_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_rc(e);
-    if (rn_bytes && (e = cudaMemcpyAsync(d + o_rn, reads_n, rn_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_rc(e);
-    const DriverIn D{Dm.seeds, d + o_reads, Dm.read_off, Dm.read_len, ctx->refbuf.p, ctx->ref_len,
-                     reads_n ? d + o_rn : nullptr,
-                     ctx->ref_has_n ? ctx->refbuf.p + align_up((size_t)((ctx->ref_len + 3) / 4), 256) : nullptr};
-    const DriverSide S{d + o_q, d + o_t, (int64_t *)(d + o_qoff), (int64_t *)(d + o_toff), (int32_t *)(d + o_qlen),
-                       (int32_t *)(d + o_tlen), (int32_t *)(d + o_h0), (int32_t *)(d + o_wcur),
-                       (bsw_result_t *)(d + o_res), qslot, tslot, has_n ? d + o_qn : nullptr,
-                       has_n ? d + o_tn : nullptr};
-    const DriverCompact C{(int64_t *)(d + o_cqoff), (int64_t *)(d + o_ctoff), (int32_t *)(d + o_cqlen),
-                          (int32_t *)(d + o_ctlen), (int32_t *)(d + o_ch0), (int32_t *)(d + o_cw),
-                          (bsw_result_t *)(d + o_cres)};
-    int32_t *list = (int32_t *)(d + o_list);
-    uint32_t *count = (uint32_t *)(d + o_count);
-    bsw_aln_t *aln = (bsw_aln_t *)(d + o_aln);
-    unsigned long long *cells = (unsigned long long *)(d + o_cells);
-    int n_runs = 0;
-    bool first = true;
-    auto extend = [&](const Batch &B) -> int {
-        Work W = make_work(lane.work.p, lane.wl);
-        W.cells = cells + n_runs++;
-        cudaError_t le = enqueue_launch(ctx, lane, lane.S, B, W, 0u, first, ctx->plan);
-        first = false;
-        if (le != cudaSuccess) {
-            lane.work_dirty = true;
-            return cuda_rc(le);
-        }
-        return BSW_OK;
-    };
-    for (int side = 0; side < 2; ++side) {
-        const bool left = side == 0;
-        if ((e = launch_side(left, D, S, N, w, ctx->P.a, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
-        if ((rc = extend(Batch{N, S.q, S.q_off, S.q_len, S.t, S.t_off, S.t_len, S.h0, nullptr, S.res, S.q_n, S.t_n})) !=
-            BSW_OK)
-            return rc;
-        for (int t = 1; t < max_band_try; ++t) {
-            const int wt = w << (t - 1), wnext = w << t;
-            if ((e = cudaMemsetAsync(count, 0, 4, st)) != cudaSuccess) return cuda_rc(e);
-            if ((e = launch_retry_select(S, N, wt, list, count, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
-            uint32_t cnt = 0;
-            if ((e = cudaMemcpyAsync(ctx->h_status, count, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        // Checks on the device (launch_driver_check): reads, seeds inside their
+        // read and the reference, each read's seeds consecutive, the score bound;
+        // they also give the packed-read extent and the longest read.
+        const int64_t N = n_seeds;
+        Lane &lane = ctx->sync;
+        cudaStream_t st = lane.S.main;
+        cudaError_t e;
+        size_t om = 0;
+        auto take_m = [&](size_t bytes) { size_t r = om; om = align_up(om + bytes, 256); return r; };
+        const size_t o_roff = take_m(8 * (size_t)n_reads), o_rlen = take_m(4 * (size_t)n_reads),
+                     o_seeds = take_m(sizeof(bsw_seed_t) * (size_t)N), o_runs = take_m(4 * (size_t)n_reads),
+                     o_chk = take_m(sizeof(DriverCheck));
+        int rc = ctx->drvmeta.reserve(om, ctx->budget);
+        if (rc != BSW_OK) return rc;
+        uint8_t *dm = ctx->drvmeta.p;
+        const struct { size_t off; const void *src; size_t bytes; } meta[] = {
+            {o_roff, read_off, 8 * (size_t)n_reads}, {o_rlen, read_len, 4 * (size_t)n_reads},
+            {o_seeds, seeds, sizeof(bsw_seed_t) * (size_t)N}};
+        for (const auto &cp : meta)
+            if (cp.bytes && (e = cudaMemcpyAsync(dm + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
                 return cuda_rc(e);
-            cnt = *ctx->h_status;
-            if (cnt == 0) break;
-            if ((e = launch_retry_gather(S, list, count, cnt, wnext, C, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
-            if ((rc = extend(Batch{(int64_t)cnt, S.q, C.q_off, C.q_len, S.t, C.t_off, C.t_len, C.h0, C.w, C.res, S.q_n,
-                                   S.t_n})) != BSW_OK)
+        if ((e = cudaMemsetAsync(dm + o_runs, 0, om - o_runs, st)) != cudaSuccess) return cuda_rc(e);   // runs, check
+        DriverCheck *chk = (DriverCheck *)(dm + o_chk);
+        const DriverIn Dm{(const bsw_seed_t *)(dm + o_seeds), nullptr, (const int64_t *)(dm + o_roff),
+                          (const int32_t *)(dm + o_rlen), ctx->refbuf.p, ctx->ref_len, nullptr, nullptr};
+        if ((e = launch_driver_check(Dm, n_reads, N, ctx->P.a, (uint32_t *)(dm + o_runs), chk, st, ctx->sms)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaMemcpyAsync(ctx->h_chk, chk, sizeof(DriverCheck), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_rc(e);
+        if (ctx->h_chk->inval) return BSW_EINVAL;
+        const int64_t read_bytes = (int64_t)ctx->h_chk->read_bytes;
+        const int maxrl = ctx->h_chk->maxrl;
+
+        // Device layout: the reads, one side's pairs, the retry batch, the alignments.
+        const int qslot = (int)align_up((size_t)std::max(maxrl, 1), 16);
+        const int tslot = (int)align_up((size_t)maxrl + (size_t)w + 4, 16);
+        size_t o = 0;
+        auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+        const size_t o_reads = take((size_t)read_bytes),
+                     o_q = take((size_t)N * qslot / 4), o_t = take((size_t)N * tslot / 4), o_qoff = take(8 * (size_t)N),
+                     o_toff = take(8 * (size_t)N), o_qlen = take(4 * (size_t)N), o_tlen = take(4 * (size_t)N),
+                     o_h0 = take(4 * (size_t)N), o_wcur = take(4 * (size_t)N), o_res = take(sizeof(bsw_result_t) * (size_t)N),
+                     o_list = take(4 * (size_t)N), o_count = take(4), o_cqoff = take(8 * (size_t)N),
+                     o_ctoff = take(8 * (size_t)N), o_cqlen = take(4 * (size_t)N), o_ctlen = take(4 * (size_t)N),
+                     o_ch0 = take(4 * (size_t)N), o_cw = take(4 * (size_t)N),
+                     o_cres = take(sizeof(bsw_result_t) * (size_t)N), o_aln = take(sizeof(bsw_aln_t) * (size_t)N),
+                     o_cells = take(8 * 2 * (size_t)max_band_try);
+        // N bitmaps: the reads' (read_bytes packed bytes hold 2 * read_bytes bitmap
+        // bytes' worth of bases: (read_bytes + 1) / 2 bytes) and each side's slots
+        const bool has_n = reads_n != nullptr || ctx->ref_has_n;
+        const size_t rn_bytes = reads_n ? (size_t)((read_bytes + 1) / 2) : 0;
+        const size_t o_rn = take(rn_bytes), o_qn = take(has_n ? (size_t)N * qslot / 8 : 0),
+                     o_tn = take(has_n ? (size_t)N * tslot / 8 : 0);
+        bool moved = false;
+        if ((rc = ctx->drv.reserve(o, ctx->budget)) != BSW_OK) return rc;
+        if ((rc = lane.ensure_work(N, std::max(maxrl, kShortMax), ctx->sms, ctx->budget, &moved)) != BSW_OK) return rc;
+        if (moved) clear_graphs(ctx);
+        uint8_t *d = ctx->drv.p;
+        if (read_bytes && (e = cudaMemcpyAsync(d + o_reads, reads, (size_t)read_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if (rn_bytes && (e = cudaMemcpyAsync(d + o_rn, reads_n, rn_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+        const DriverIn D{Dm.seeds, d + o_reads, Dm.read_off, Dm.read_len, ctx->refbuf.p, ctx->ref_len,
+                         reads_n ? d + o_rn : nullptr,
+                         ctx->ref_has_n ? ctx->refbuf.p + align_up((size_t)((ctx->ref_len + 3) / 4), 256) : nullptr};
+        const DriverSide S{d + o_q, d + o_t, (int64_t *)(d + o_qoff), (int64_t *)(d + o_toff), (int32_t *)(d + o_qlen),
+                           (int32_t *)(d + o_tlen), (int32_t *)(d + o_h0), (int32_t *)(d + o_wcur),
+                           (bsw_result_t *)(d + o_res), qslot, tslot, has_n ? d + o_qn : nullptr,
+                           has_n ? d + o_tn : nullptr};
+        const DriverCompact C{(int64_t *)(d + o_cqoff), (int64_t *)(d + o_ctoff), (int32_t *)(d + o_cqlen),
+                              (int32_t *)(d + o_ctlen), (int32_t *)(d + o_ch0), (int32_t *)(d + o_cw),
+                              (bsw_result_t *)(d + o_cres)};
+        int32_t *list = (int32_t *)(d + o_list);
+        uint32_t *count = (uint32_t *)(d + o_count);
+        bsw_aln_t *aln = (bsw_aln_t *)(d + o_aln);
+        unsigned long long *cells = (unsigned long long *)(d + o_cells);
+        int n_runs = 0;
+        bool first = true;
+        auto extend = [&](const Batch &B) -> int {
+            Work W = make_work(lane.work.p, lane.wl);
+            W.cells = cells + n_runs++;
+            cudaError_t le = enqueue_launch(ctx, lane, lane.S, B, W, 0u, first, ctx->plan);
+            first = false;
+            if (le != cudaSuccess) {
+                lane.work_dirty = true;
+                return cuda_rc(le);
+            }
+            return BSW_OK;
+        };
+        for (int side = 0; side < 2; ++side) {
+            const bool left = side == 0;
+            if ((e = launch_side(left, D, S, N, w, ctx->P.a, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+            if ((rc = extend(Batch{N, S.q, S.q_off, S.q_len, S.t, S.t_off, S.t_len, S.h0, nullptr, S.res, S.q_n, S.t_n})) !=
+                BSW_OK)
                 return rc;
-            if ((e = launch_retry_scatter(S, list, count, cnt, wnext, C, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+            for (int t = 1; t < max_band_try; ++t) {
+                const int wt = w << (t - 1), wnext = w << t;
+                if ((e = cudaMemsetAsync(count, 0, 4, st)) != cudaSuccess) return cuda_rc(e);
+                if ((e = launch_retry_select(S, N, wt, list, count, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+                uint32_t cnt = 0;
+                if ((e = cudaMemcpyAsync(ctx->h_status, count, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                    (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                    return cuda_rc(e);
+                cnt = *ctx->h_status;
+                if (cnt == 0) break;
+                if ((e = launch_retry_gather(S, list, count, cnt, wnext, C, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+                if ((rc = extend(Batch{(int64_t)cnt, S.q, C.q_off, C.q_len, S.t, C.t_off, C.t_len, C.h0, C.w, C.res, S.q_n,
+                                       S.t_n})) != BSW_OK)
+                    return rc;
+                if ((e = launch_retry_scatter(S, list, count, cnt, wnext, C, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+            }
+            if ((e = launch_decide(left, D, S, N, ctx->P.end_bonus, aln, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
         }
-        if ((e = launch_decide(left, D, S, N, ctx->P.end_bonus, aln, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
-    }
-    if ((e = launch_filter(D, N, aln, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
-    std::vector<unsigned long long> hc((size_t)n_runs);
-    Work W = make_work(lane.work.p, lane.wl);
-    if ((e = cudaMemcpyAsync(out, aln, sizeof(bsw_aln_t) * (size_t)N, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(hc.data(), cells, 8 * (size_t)n_runs, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(ctx->h_status, W.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_rc(e);
-    if (cells_out) {
-        unsigned long long tot = 0;
-        for (unsigned long long c : hc) tot += c;
-        *cells_out = (int64_t)tot;
-    }
-    return status_to_rc(*ctx->h_status);
+        if ((e = launch_filter(D, N, aln, st, ctx->sms)) != cudaSuccess) return cuda_rc(e);
+        std::vector<unsigned long long> hc((size_t)n_runs);
+        Work W = make_work(lane.work.p, lane.wl);
+        if ((e = cudaMemcpyAsync(out, aln, sizeof(bsw_aln_t) * (size_t)N, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hc.data(), cells, 8 * (size_t)n_runs, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ctx->h_status, W.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_rc(e);
+        if (cells_out) {
+            unsigned long long tot = 0;
+            for (unsigned long long c : hc) tot += c;
+            *cells_out = (int64_t)tot;
+        }
+        return status_to_rc(*ctx->h_status);
+    });
 }
 
 int bsw_sal_set_index(bsw_ctx_t *ctx, const int32_t *sa, int64_t sa_n)
@@ -1455,98 +1487,100 @@ int bsw_smem_n(bsw_ctx_t *ctx, int64_t n_reads, const uint8_t *reads, const uint
                const int32_t *read_len, int32_t min_len, bsw_smem_t *out, int64_t out_cap, int64_t *n_out,
                int64_t *first)
 {
-    if (!ctx || n_reads < 0 || min_len < 1 || out_cap < 0 || !n_out) return BSW_EINVAL;
-    if (n_reads > 0 && (!reads || !read_off || !read_len)) return BSW_EINVAL;
-    if (!ctx->fm_ready) return BSW_ESTATE;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
-    *n_out = 0;
-    if (first) first[0] = 0;
-    if (n_reads == 0) return BSW_OK;
-    int64_t read_bytes = 0;
-    int lmax = 0;
-    for (int64_t r = 0; r < n_reads; ++r) {
-        if (read_off[r] < 0 || (read_off[r] & 3) || read_len[r] < 0 || read_len[r] > kLongMax) return BSW_EINVAL;
-        read_bytes = std::max(read_bytes, (read_off[r] + read_len[r] + 3) / 4);
-        lmax = std::max(lmax, (int)read_len[r]);
-    }
-    size_t o = 0;
-    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
-    const size_t o_reads = take((size_t)read_bytes), o_roff = take(8 * (size_t)n_reads),
-                 o_rlen = take(4 * (size_t)n_reads), o_cnt = take(8 * (size_t)n_reads),
-                 o_first = take(8 * (size_t)n_reads), o_ids = take(4 * (size_t)n_reads), o_nids = take(4),
-                 o_next = take(4), o_keep = take(sizeof(bsw_smem_t) * kSmemKeep * (size_t)n_reads),
-                 o_rn = take(reads_n ? (size_t)((read_bytes + 1) / 2) : 0),
-                 o_out = take(sizeof(bsw_smem_t) * (size_t)std::max<int64_t>(out_cap, 1));
-    int rc = ctx->smemio.reserve(o, ctx->budget);
-    if (rc != BSW_OK) return rc;
-    uint8_t *d = ctx->smemio.p;
-    cudaStream_t st = ctx->sync.S.main;
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(d + o_reads, reads, (size_t)read_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d + o_roff, read_off, 8 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d + o_rlen, read_len, 4 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(d + o_nids, 0, 4, st)) != cudaSuccess)
-        return cuda_rc(e);
-    if (reads_n && read_bytes &&
-        (e = cudaMemcpyAsync(d + o_rn, reads_n, (size_t)((read_bytes + 1) / 2), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_rc(e);
-    const SmemIn R{d + o_reads, (const int64_t *)(d + o_roff), (const int32_t *)(d + o_rlen), n_reads, lmax,
-                   reads_n ? d + o_rn : nullptr};
-    int32_t *ids = (int32_t *)(d + o_ids);
-    uint32_t *nids = (uint32_t *)(d + o_nids);
-    int64_t *dfirst = (int64_t *)(d + o_first);
-    const SmemWork W{(int64_t *)(d + o_cnt), (bsw_smem_t *)(d + o_keep), dfirst, (bsw_smem_t *)(d + o_out),
-                     (uint32_t *)(d + o_next), nids, ids};
-    auto global_lists = [&](int64_t n_ids, BiIv **lists) -> int {      // lmax + 1 entries hold any list
-        const int r2 = ctx->smemscratch.reserve(sizeof(BiIv) * (size_t)n_ids * (size_t)(lmax + 1), ctx->budget);
-        *lists = (BiIv *)ctx->smemscratch.p;
-        return r2;
-    };
+    return guard([&]() -> int {
+        if (!ctx || n_reads < 0 || min_len < 1 || out_cap < 0 || !n_out) return BSW_EINVAL;
+        if (n_reads > 0 && (!reads || !read_off || !read_len)) return BSW_EINVAL;
+        if (!ctx->fm_ready) return BSW_ESTATE;
+        if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_rc(cudaErrorInvalidDevice);
+        *n_out = 0;
+        if (first) first[0] = 0;
+        if (n_reads == 0) return BSW_OK;
+        int64_t read_bytes = 0;
+        int lmax = 0;
+        for (int64_t r = 0; r < n_reads; ++r) {
+            if (read_off[r] < 0 || (read_off[r] & 3) || read_len[r] < 0 || read_len[r] > kLongMax) return BSW_EINVAL;
+            read_bytes = std::max(read_bytes, (read_off[r] + read_len[r] + 3) / 4);
+            lmax = std::max(lmax, (int)read_len[r]);
+        }
+        size_t o = 0;
+        auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+        const size_t o_reads = take((size_t)read_bytes), o_roff = take(8 * (size_t)n_reads),
+                     o_rlen = take(4 * (size_t)n_reads), o_cnt = take(8 * (size_t)n_reads),
+                     o_first = take(8 * (size_t)n_reads), o_ids = take(4 * (size_t)n_reads), o_nids = take(4),
+                     o_next = take(4), o_keep = take(sizeof(bsw_smem_t) * kSmemKeep * (size_t)n_reads),
+                     o_rn = take(reads_n ? (size_t)((read_bytes + 1) / 2) : 0),
+                     o_out = take(sizeof(bsw_smem_t) * (size_t)std::max<int64_t>(out_cap, 1));
+        int rc = ctx->smemio.reserve(o, ctx->budget);
+        if (rc != BSW_OK) return rc;
+        uint8_t *d = ctx->smemio.p;
+        cudaStream_t st = ctx->sync.S.main;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(d + o_reads, reads, (size_t)read_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d + o_roff, read_off, 8 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d + o_rlen, read_len, 4 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d + o_nids, 0, 4, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if (reads_n && read_bytes &&
+            (e = cudaMemcpyAsync(d + o_rn, reads_n, (size_t)((read_bytes + 1) / 2), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+        const SmemIn R{d + o_reads, (const int64_t *)(d + o_roff), (const int32_t *)(d + o_rlen), n_reads, lmax,
+                       reads_n ? d + o_rn : nullptr};
+        int32_t *ids = (int32_t *)(d + o_ids);
+        uint32_t *nids = (uint32_t *)(d + o_nids);
+        int64_t *dfirst = (int64_t *)(d + o_first);
+        const SmemWork W{(int64_t *)(d + o_cnt), (bsw_smem_t *)(d + o_keep), dfirst, (bsw_smem_t *)(d + o_out),
+                         (uint32_t *)(d + o_next), nids, ids};
+        auto global_lists = [&](int64_t n_ids, BiIv **lists) -> int {      // lmax + 1 entries hold any list
+            const int r2 = ctx->smemscratch.reserve(sizeof(BiIv) * (size_t)n_ids * (size_t)(lmax + 1), ctx->budget);
+            *lists = (BiIv *)ctx->smemscratch.p;
+            return r2;
+        };
 
-    // One search pass: counts, and the records of reads with few; reads whose
-    // lists overflow shared memory are searched with lists in global memory.
-    if ((e = launch_smem_store(R, ctx->fm_t, min_len, W, st, ctx->sms)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(ctx->h_status, nids, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_rc(e);
-    const int64_t n_ovf = *ctx->h_status;
-    if (n_ovf > 0) {
-        BiIv *lists = nullptr;
-        if ((rc = global_lists(n_ovf, &lists)) != BSW_OK) return rc;
-        if ((e = launch_smem_global(false, R, ctx->fm_t, min_len, W, ids, n_ovf, lists, lmax + 1, st, ctx->sms)) !=
-            cudaSuccess)
+        // One search pass: counts, and the records of reads with few; reads whose
+        // lists overflow shared memory are searched with lists in global memory.
+        if ((e = launch_smem_store(R, ctx->fm_t, min_len, W, st, ctx->sms)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ctx->h_status, nids, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_rc(e);
-    }
-    std::vector<int64_t> hc((size_t)n_reads), hf((size_t)n_reads + 1);
-    if ((e = cudaMemcpyAsync(hc.data(), W.count, 8 * (size_t)n_reads, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_rc(e);
-    hf[0] = 0;
-    std::vector<int32_t> many;                                        // reads with more records than were kept
-    for (int64_t r = 0; r < n_reads; ++r) {
-        hf[(size_t)r + 1] = hf[(size_t)r] + hc[(size_t)r];
-        if (hc[(size_t)r] > kSmemKeep) many.push_back((int32_t)r);
-    }
-    const int64_t total = hf[(size_t)n_reads];
-    *n_out = total;
-    if (first) std::memcpy(first, hf.data(), 8 * ((size_t)n_reads + 1));
-    if (total > out_cap) return BSW_EBUDGET;
-    if (total == 0) return BSW_OK;
-    if ((e = cudaMemcpyAsync(dfirst, hf.data(), 8 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = launch_smem_gather(n_reads, W, st, ctx->sms)) != cudaSuccess)
-        return cuda_rc(e);
-    if (!many.empty()) {
-        BiIv *lists = nullptr;
-        if ((rc = global_lists((int64_t)many.size(), &lists)) != BSW_OK) return rc;
-        if ((e = cudaMemcpyAsync(ids, many.data(), 4 * many.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = launch_smem_global(true, R, ctx->fm_t, min_len, W, ids, (int64_t)many.size(), lists, lmax + 1, st,
-                                    ctx->sms)) != cudaSuccess)
+        const int64_t n_ovf = *ctx->h_status;
+        if (n_ovf > 0) {
+            BiIv *lists = nullptr;
+            if ((rc = global_lists(n_ovf, &lists)) != BSW_OK) return rc;
+            if ((e = launch_smem_global(false, R, ctx->fm_t, min_len, W, ids, n_ovf, lists, lmax + 1, st, ctx->sms)) !=
+                cudaSuccess)
+                return cuda_rc(e);
+        }
+        std::vector<int64_t> hc((size_t)n_reads), hf((size_t)n_reads + 1);
+        if ((e = cudaMemcpyAsync(hc.data(), W.count, 8 * (size_t)n_reads, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_rc(e);
-    }
-    if ((e = cudaMemcpyAsync(out, W.out, sizeof(bsw_smem_t) * (size_t)total, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_rc(e);
-    return BSW_OK;
+        hf[0] = 0;
+        std::vector<int32_t> many;                                        // reads with more records than were kept
+        for (int64_t r = 0; r < n_reads; ++r) {
+            hf[(size_t)r + 1] = hf[(size_t)r] + hc[(size_t)r];
+            if (hc[(size_t)r] > kSmemKeep) many.push_back((int32_t)r);
+        }
+        const int64_t total = hf[(size_t)n_reads];
+        *n_out = total;
+        if (first) std::memcpy(first, hf.data(), 8 * ((size_t)n_reads + 1));
+        if (total > out_cap) return BSW_EBUDGET;
+        if (total == 0) return BSW_OK;
+        if ((e = cudaMemcpyAsync(dfirst, hf.data(), 8 * (size_t)n_reads, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = launch_smem_gather(n_reads, W, st, ctx->sms)) != cudaSuccess)
+            return cuda_rc(e);
+        if (!many.empty()) {
+            BiIv *lists = nullptr;
+            if ((rc = global_lists((int64_t)many.size(), &lists)) != BSW_OK) return rc;
+            if ((e = cudaMemcpyAsync(ids, many.data(), 4 * many.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (e = launch_smem_global(true, R, ctx->fm_t, min_len, W, ids, (int64_t)many.size(), lists, lmax + 1, st,
+                                        ctx->sms)) != cudaSuccess)
+                return cuda_rc(e);
+        }
+        if ((e = cudaMemcpyAsync(out, W.out, sizeof(bsw_smem_t) * (size_t)total, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_rc(e);
+        return BSW_OK;
+    });
 }
 
 void bsw_destroy(bsw_ctx_t *ctx)
