@@ -3,18 +3,21 @@
 
 A step is one pass of the whole extension path over one batch: length
 bucketing, the per-class extension kernels and the exact 32-bit re-run, for
-every pair of the 151 bp short-read workload (2,000,000 pairs, inputs resident
-in HBM).  GCUPS counts the DP cells the scalar algorithm computes (the oracle's
-count, which the library reproduces exactly).
+every pair of the 250 bp read workload (4,000,000 pairs, inputs resident in
+HBM), the largest configuration that fits one GPU.  GCUPS counts the DP cells
+the scalar algorithm computes (the oracle's count, which the library
+reproduces exactly).  The default run also measures the 151 bp and long-query
+workloads the same way, a bounded serving sweep (p50/p99 latency at three
+offered loads), N bases, the seed-extension driver, suffix array lookup and
+SMEM search, each checked against the oracle or the definition.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--config read151] [--pairs N] [--serve]
+                  [--config read250] [--pairs N] [--only] [--serve]
 
 --impl reference times the CPU oracle on the host cores, on a bounded sample of
-the same workload.  --serve runs the serving sweep (Poisson arrivals of
-mixed-size requests, p50/p99 latency per offered load) instead of the batch
-benchmark.  Under torchrun each rank runs its own batch (weak scaling, no
-collective on the data path); rank 0 prints the JSON line.
+the same workload.  --serve runs the full serving sweep (ten offered loads)
+instead of the batch benchmark.  Under torchrun each rank runs its own batch
+(weak scaling, no collective on the data path); rank 0 prints the JSON line.
 """
 from __future__ import annotations
 
@@ -33,17 +36,15 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-# Algorithmic integer operations per DP cell of Eq. 2 as BWA-MEM computes it:
-# the diagonal add, the zero-diagonal rule, the 3-way max for H, M - (o + e),
-# the E and F updates (add-max-clamp each), and the row max with its argmax.
-OPS_PER_CELL = 8
 # 32-bit integer lane-operations one SM issues per clock (4 schedulers x 32 lanes).
 LANE_OPS_PER_CLK_PER_SM = 128
 METRIC = "BSW GCUPS on 1 GB300 (batched vs plain kernel, bit-exact); p50/p99 serve latency"
 # DRAM bytes read + written per launch of a workload's dominant kernel, from
-# one ncu capture of the current kernel (profiles/k_inter96_u8_read151.md);
-# other kernels and workloads report null.
-MEASURED_TRAFFIC = {("read151", "k_inter<96,u8>"): 138_990_592}
+# one ncu capture of the current kernel (bytes, source); other kernels and
+# workloads report null.
+MEASURED_TRAFFIC = {}
+
+SECONDARY = ("read151", "long10k")
 
 U8_NMAX = (256, 192, 128, 96, 64, 48, 32, 16)
 I16_NMAX = (256, 128, 64, 32)
@@ -52,7 +53,9 @@ WORKLOAD_TEXT = {
     "read151": "151 bp short-read seed extensions: 2,000,000 left/right pairs from 1,000,000 reads of a 100 Mbp "
                "random reference (0.1% SNPs, 1% sequencing substitutions), seeds 19-151 bp, query 0-132 bp, "
                "target = query + 100; match 1, mismatch 4, gap 6+1k, w 100, zdrop 100, end bonus 5",
-    "read250": "250 bp read seed extensions: 4,000,000 pairs, 2% divergence (10% of it 1-10 bp indels), w 100, zdrop 100",
+    "read250": "250 bp read seed extensions: 4,000,000 left/right pairs from 2,000,000 reads of the 100 Mbp "
+               "reference with 2% divergence (10% of it 1-10 bp indels), seeds 19-250 bp, query 0-231 bp, "
+               "target = query + 100; match 1, mismatch 4, gap 6+1k, w 100, zdrop 100, end bonus 5",
     "plain10k": "10,000 pairs, queries 1-130 bp with 1% substitutions and 0.1% 1-3 bp indels, w 100, zdrop 100",
     "long10k": "20,000 long-query pairs, query log-uniform 1-10 kbp, 12% error, w 500, zdrop 400",
 }
@@ -61,10 +64,10 @@ WORKLOAD_TEXT = {
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="read151")
+    ap.add_argument("--config", default="read250")
     ap.add_argument("--pairs", type=int, default=None)
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -75,7 +78,11 @@ def parse():
     ap.add_argument("--no-nbases", action="store_true", help="skip the N-bases leg")
     ap.add_argument("--plan", default=None,
                     help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps (no autotune)")
-    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point (--serve)")
+    ap.add_argument("--serve-quick", type=int, default=200,
+                    help="requests per point of the bounded serving leg of the default run (0: skip it)")
+    ap.add_argument("--only", action="store_true",
+                    help="measure the --config workload alone (no other workloads or legs)")
     return ap.parse_args()
 
 
@@ -556,60 +563,54 @@ def time_device(ctx, db, flags, steps, warmup, stream, dist):
     return dist.max(ms) / steps
 
 
-def run_gb300(args):
-    import torch
-    from paper_1907_12931_gb300 import bsw, workload as W
+def ops_per_cell(scoring) -> int:
+    """Algorithmic integer operations per cell: 7 when deletions and insertions
+    cost the same (E and F open from one shared M - o - e), else 8."""
+    return 7 if (scoring.o_del == scoring.o_ins and scoring.e_del == scoring.e_ins) else 8
 
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = Dist("nccl")
-    base = W.CONFIGS[args.config]
-    wl = W.make(args.config, n_pairs=args.pairs, seed=base["seed"] + rank)
-    ctx = bsw.Context(wl.params, mem_budget_bytes=40 << 30)
-    hb = bsw.HostBatch(wl)
-    db = bsw.DeviceBatch(hb)
-    stream = torch.cuda.Stream()
-    in_bytes = hb.nbytes()
-    # the execution plan: autotuned on this batch (outside the timed region), or given
-    t_tune = time.perf_counter()
+
+def tune(bsw, ctx, name, n_pairs, seed, args):
+    """The execution plan: given (--plan), the default (--no-tune), or
+    autotuned on a batch of the same recipe drawn from another seed, so the
+    plan is not fitted to the timed batch itself.  Returns (plan, seconds)."""
+    from paper_1907_12931_gb300 import workload as W
+    t0 = time.perf_counter()
     if args.plan:
         ctx.set_plan(bsw.make_plan(*[int(x, 0) for x in args.plan.split(",")]))
         plan = ctx.get_plan()
+    elif args.no_tune:
+        plan = ctx.get_plan()
     else:
-        plan = ctx.get_plan() if args.no_tune else ctx.autotune(db, sample_pairs=wl.n_pairs)
-    t_tune = time.perf_counter() - t_tune
+        twl = W.make(name, n_pairs=n_pairs, seed=seed)
+        tdb = bsw.DeviceBatch(bsw.HostBatch(twl))
+        plan = ctx.autotune(tdb, sample_pairs=twl.n_pairs)
+        del tdb, twl
+    return plan, time.perf_counter() - t0
 
-    # batched path, timed with clocks sampled
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms = time_device(ctx, db, 0, args.steps, args.warmup, stream, dist)
-    clk = clocks.stop()
-    cells = int(db.cells.item())
-    total_cells = dist.sum(cells)
-    gcups = total_cells / (ms * 1e-3) / 1e9
-    out_batched = db.out.cpu().numpy().copy()
 
-    # kernels per step and each class kernel's time within one step (events on
-    # the kernels' own streams; one untimed-region call without a graph)
-    ctx.extend_device(db, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH, stream.cuda_stream)
-    launches_per_step, step_class_ms = ctx.kernel_times()
-    ctx.sync(stream.cuda_stream)
+def plain_leg(bsw, ctx, db, plan, steps, warmup, stream, dist, out_ref, cells_ref):
+    """The plain baselines on the same inputs: the warp-per-pair ring kernel
+    over pairs in input order with 4, 8 and 16 columns per lane (the best is
+    the plain kernel), and the naive global-memory kernel."""
+    per = {}
+    for cols in (4, 8, 16):
+        ctx.set_plan(bsw.make_plan(plan.short_max, plan.u8_bounds, plan.i16_bounds, plan.packed, cols,
+                                   plan.inter_warps))
+        ms = time_device(ctx, db, bsw.BSW_PLAIN_KERNEL, steps, warmup, stream, dist)
+        equal = bool(np.array_equal(db.out.cpu().numpy(), out_ref)) and int(db.cells.item()) == cells_ref
+        per[cols] = (ms, equal)
+    ctx.set_plan(plan)
+    best = min(per, key=lambda c: per[c][0])
+    g_steps = max(2, steps // 3)
+    ms_g = time_device(ctx, db, bsw.BSW_PLAIN_GLOBAL, g_steps, 1, stream, dist)
+    g_equal = bool(np.array_equal(db.out.cpu().numpy(), out_ref)) and int(db.cells.item()) == cells_ref
+    return best, per, ms_g, g_equal
 
-    # plain one-pair-per-warp kernel on the same inputs
-    p_steps = max(3, args.steps // 10)
-    ms_plain = time_device(ctx, db, bsw.BSW_PLAIN_KERNEL, p_steps, max(1, args.warmup // 2), stream, dist)
-    plain_cells = int(db.cells.item())
-    plain_equal = bool(np.array_equal(db.out.cpu().numpy(), out_batched)) and plain_cells == cells
-    gcups_plain = dist.sum(plain_cells) / (ms_plain * 1e-3) / 1e9
 
-    # the same batched path with two pairs per thread (packed 16-bit lanes) in the 8-bit classes
-    s_steps = max(3, args.steps // 10)
-    ms_packed = time_device(ctx, db, bsw.BSW_PACKED_PAIRS, s_steps, max(1, args.warmup // 2), stream, dist)
-    packed_equal = bool(np.array_equal(db.out.cpu().numpy(), out_batched))
-    gcups_packed = total_cells / (ms_packed * 1e-3) / 1e9
-
-    # dominant kernel: the class with the most cells, as a batch of its own;
-    # its kernel's duration from the events around its launch, averaged
+def dominant_leg(bsw, ctx, wl, plan, stream, dist, steps, clk_mhz, sms):
+    """The dominant kernel: the class with the most cells under the plan, run
+    as a batch of its own; its duration from CUDA events recorded on its own
+    stream just before and after its launch, averaged over launches."""
     all_cls = class_of(wl.q_len, wl.t_len, wl.h0, wl.params.scoring.match, plan)
     est = wl.q_len.astype(np.float64) * np.minimum(wl.t_len, 2 * wl.params.w + 1)
     dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(14)]))
@@ -618,103 +619,220 @@ def run_gb300(args):
     for _ in range(2):
         ctx.extend_device(sdb, bsw.BSW_NO_GRAPH, stream.cuda_stream)
     dom_ms = []
-    for _ in range(max(3, args.steps // 4)):
+    for _ in range(max(3, steps // 4)):
         ctx.extend_device(sdb, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH, stream.cuda_stream)
         dom_ms.append(ctx.kernel_times()[1][dom])
     ctx.sync(stream.cuda_stream)
     ms_dom = dist.max(statistics.mean(dom_ms))
     dom_cells = int(sdb.cells.item())
     del sdb
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    f_mhz = clk["sm_mhz"] or 1470.0
-    achieved = dom_cells * OPS_PER_CELL / (ms_dom * 1e-3) / 1e12
+    k = ops_per_cell(wl.params.scoring)
+    f_mhz = clk_mhz or 1470.0
+    achieved = dom_cells * k / (ms_dom * 1e-3) / 1e12
     peak = sms * f_mhz * 1e6 * LANE_OPS_PER_CLK_PER_SM / 1e12
-    dom_kernel = class_kernel(dom, plan, wl.params.scoring)
-    traffic = MEASURED_TRAFFIC.get((args.config, dom_kernel)) if args.pairs is None else None
+    kernel = class_kernel(dom, plan, wl.params.scoring)
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+            "frac": round(achieved / peak, 4),
+            "frac_at_8_ops": round(achieved * 8 / k / peak, 4),
+            "kernel": "%s (batch of its own class: %d pairs, %d cells; CUDA events around the kernel on its "
+                      "stream, mean of %d launches)" % (kernel, sub.n_pairs, dom_cells, len(dom_ms)),
+            "kernel_name": kernel, "launch_ms": round(ms_dom, 4), "cells_per_launch": dom_cells,
+            "ops_per_cell": k,
+            "ops_basis": "diagonal add, zero-diagonal rule, 3-way max for H, M - (o + e) (shared by E and F "
+                         "when the gap costs are symmetric, else one each), the E and F add-max-clamps, the row "
+                         "max with its argmax",
+            "peak_basis": "%d SMs x %.0f MHz (median under load) x %d lane-ops/clk (4 schedulers x 32 lanes)"
+                          % (sms, f_mhz, LANE_OPS_PER_CLK_PER_SM)}
 
-    # end to end through the C ABI with pinned host buffers
-    hbp = pinned_host_batch(bsw, bsw.HostBatch(wl))
-    pout = torch.empty((wl.n_pairs, 6), dtype=torch.int32, pin_memory=True).numpy()
-    e_steps = max(3, args.steps // 20)
-    for _ in range(2):
-        ctx.extend_host(hbp, out=pout)
-    dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
-        out_h, cells_h = ctx.extend_host(hbp, out=pout)
-    t_e2e = dist.max((time.perf_counter() - t0) / e_steps)
-    e2e = dist.sum(cells_h) / t_e2e / 1e9
-    e2e_equal = bool(np.array_equal(out_h, out_batched))
-    n = wl.n_pairs
-    qb = int((wl.q_off[-1] + wl.q_len[-1] + 3) // 4) if n else 0
-    tb = int((wl.t_off[-1] + wl.t_len[-1] + 3) // 4) if n else 0
-    h2d = qb + tb + n * (8 + 4 + 8 + 4 + 4)
-    d2h = n * 24 + 8 + 4 + 40       # results, cells, status, the staged batch's extents record
 
-    # CPU baseline (rank 0): the oracle on the host cores, also a parity check of every pair
-    cpu = None
-    parity = None
+def measure(bsw, args, name, dist, stream, local, world, rank, headline):
+    """One workload: batched GCUPS (timed with clocks sampled), the plain
+    baselines, the dominant kernel's roofline, and every pair checked against
+    the oracle on rank 0.  The headline workload also gets the end-to-end
+    C-ABI leg, the two-pairs-per-thread variant and the CPU baseline."""
+    import torch
+    from paper_1907_12931_gb300 import workload as W
+    base = W.CONFIGS[name]
+    wl = W.make(name, n_pairs=args.pairs if headline else None, seed=base["seed"] + rank)
+    ctx = bsw.Context(wl.params, mem_budget_bytes=40 << 30)
+    hb = bsw.HostBatch(wl)
+    db = bsw.DeviceBatch(hb)
+    in_bytes = hb.nbytes()
+    plan, t_tune = tune(bsw, ctx, name, wl.n_pairs, base["seed"] + 1000 + rank, args)
+    steps = args.steps if headline else max(3, args.steps // 2)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_device(ctx, db, 0, steps, args.warmup, stream, dist)
+    clk = clocks.stop()
+    cells = int(db.cells.item())
+    total_cells = dist.sum(cells)
+    gcups = total_cells / (ms * 1e-3) / 1e9
+    out_batched = db.out.cpu().numpy().copy()
+
+    # kernels per step and each class kernel's time within one step
+    ctx.extend_device(db, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH, stream.cuda_stream)
+    launches_per_step, step_class_ms = ctx.kernel_times()
+    ctx.sync(stream.cuda_stream)
+
+    p_steps = max(3, steps // 10)
+    best_c, per, ms_g, g_equal = plain_leg(bsw, ctx, db, plan, p_steps, max(1, args.warmup // 2), stream, dist,
+                                           out_batched, cells)
+    ms_plain = per[best_c][0]
+    gcups_plain = total_cells / (ms_plain * 1e-3) / 1e9
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = dominant_leg(bsw, ctx, wl, plan, stream, dist, steps, clk["sm_mhz"], sms)
+    traffic = MEASURED_TRAFFIC.get((name, roof["kernel_name"])) if args.pairs is None or not headline else None
+    roof["traffic"] = traffic[0] if traffic else None
+    roof["traffic_source"] = traffic[1] if traffic else None
+    roof["dram_gbs"] = round(traffic[0] / (roof["launch_ms"] * 1e-3) / 1e9, 1) if traffic else None
+
+    rec = {
+        "workload": name, "description": WORKLOAD_TEXT.get(name, name), "pairs": wl.n_pairs,
+        "cells_per_step": cells, "value": round(gcups, 3), "unit": "GCUPS", "ms_per_step": round(ms, 4),
+        "steps": steps,
+        "plain": {"value": round(gcups_plain, 3), "unit": "GCUPS", "ms_per_step": round(ms_plain, 4),
+                  "kernel": "k_plain<%d>: the warp-per-pair ring kernel, one pair per warp in input order, no "
+                            "bucketing, classes or re-run list (best of 4, 8, 16 columns per lane)" % best_c,
+                  "by_columns": {str(c): {"gcups": round(total_cells / (per[c][0] * 1e-3) / 1e9, 3),
+                                          "ms_per_step": round(per[c][0], 4), "bit_exact_vs_batched": per[c][1]}
+                                 for c in per},
+                  "bit_exact_vs_batched": all(v[1] for v in per.values())},
+        "speedup_vs_plain": round(gcups / gcups_plain, 3) if gcups_plain else None,
+        "plain_global": {"value": round(total_cells / (ms_g * 1e-3) / 1e9, 3), "unit": "GCUPS",
+                         "ms_per_step": round(ms_g, 4),
+                         "kernel": "k_plain_global: one column per lane, the row in global memory, input order",
+                         "bit_exact_vs_batched": g_equal},
+        "roofline": roof,
+        "kernels_per_step": launches_per_step,
+        "class_ms_in_step": {bsw.CLASS_NAMES[c]: round(t, 4) for c, t in enumerate(step_class_ms) if t > 0},
+        "plan": dict(plan.as_dict(), tuned=not (args.no_tune or args.plan), tune_s=round(t_tune, 2),
+                     tuned_on="another batch of the same recipe (seed %d)" % (base["seed"] + 1000 + rank)
+                     if not (args.no_tune or args.plan) else None),
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                   "samples": clk["samples"]},
+        "l2": "inputs larger than L2 (%.0f MB resident packed inputs + %.0f MB results)"
+              % (in_bytes / 1e6, wl.n_pairs * 24 / 1e6),
+    }
+
+    if headline:
+        s_steps = max(3, steps // 10)
+        ms_packed = time_device(ctx, db, bsw.BSW_PACKED_PAIRS, s_steps, max(1, args.warmup // 2), stream, dist)
+        rec["two_pairs_per_thread"] = {"value": round(total_cells / (ms_packed * 1e-3) / 1e9, 3), "unit": "GCUPS",
+                                       "ms_per_step": round(ms_packed, 4),
+                                       "bit_exact_vs_batched": bool(np.array_equal(db.out.cpu().numpy(),
+                                                                                   out_batched))}
+        # end to end through the C ABI with pinned host buffers
+        hbp = pinned_host_batch(bsw, bsw.HostBatch(wl))
+        pout = torch.empty((wl.n_pairs, 6), dtype=torch.int32, pin_memory=True).numpy()
+        e_steps = max(3, steps // 20)
+        for _ in range(2):
+            ctx.extend_host(hbp, out=pout)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            out_h, cells_h = ctx.extend_host(hbp, out=pout)
+        t_e2e = dist.max((time.perf_counter() - t0) / e_steps)
+        n = wl.n_pairs
+        qb = int((wl.q_off[-1] + wl.q_len[-1] + 3) // 4) if n else 0
+        tb = int((wl.t_off[-1] + wl.t_len[-1] + 3) // 4) if n else 0
+        rec["e2e"] = {"value": round(dist.sum(cells_h) / t_e2e / 1e9, 3), "unit": "GCUPS",
+                      "h2d_bytes_per_step": qb + tb + n * (8 + 4 + 8 + 4 + 4),
+                      "d2h_bytes_per_step": n * 24 + 8 + 4 + 40, "ms_per_step": round(t_e2e * 1e3, 3),
+                      "bit_exact_vs_device": bool(np.array_equal(out_h, out_batched))}
+        rec["in_bytes"] = in_bytes
+        rec["_wl"] = wl
+        rec["_plan"] = plan
+
+    # every pair against the oracle (rank 0); the headline's pass also times it
     if rank == 0 and not args.no_cpu:
-        cpu, res = cpu_baseline(wl)
-        mism = int((res != out_batched).any(axis=1).sum())
-        parity = {"pairs_checked": int(res.shape[0]), "fields": 6, "mismatches": mism}
+        if headline:
+            cpu, res = cpu_baseline(wl)
+            rec["cpu_baseline"] = cpu
+        else:
+            import oracle
+            res, _, _ = oracle.extend_batch(wl, nthreads=os.cpu_count() or 1)
+        rec["parity"] = {"pairs_checked": int(res.shape[0]), "fields": 6,
+                         "mismatches": int((res != out_batched).any(axis=1).sum())}
+    ctx.close()
+    del db
+    return rec
 
+
+def serve_leg(args):
+    """A bounded serving sweep: three offered loads, --serve-quick requests each."""
+    import serve_bench
+    r = serve_bench.sweep(loads=(0.25, 0.5, 1.0), nreq=args.serve_quick, calib=args.serve_quick)
+    return r
+
+
+def run_gb300(args):
+    import torch
+    from paper_1907_12931_gb300 import bsw
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist("nccl")
+    stream = torch.cuda.Stream()
+    head = measure(bsw, args, args.config, dist, stream, local, world, rank, headline=True)
+    wl, plan = head.pop("_wl"), head.pop("_plan")
+    others = {}
+    if not args.only and args.pairs is None:
+        for name in SECONDARY:
+            if name != args.config:
+                r = measure(bsw, args, name, dist, stream, local, world, rank, headline=False)
+                others[name] = r
+
+    short_read = args.config in ("read151", "read250") and args.pairs is None
     nb_line = None
-    if rank == 0 and not args.no_nbases and args.config in ("read151", "read250") and args.pairs is None:
-        nb_line = n_bases_leg(bsw, wl, plan, gcups / world, stream)
-    drv = None
-    if rank == 0 and not args.no_driver and args.config == "read151" and args.pairs is None:
-        drv = driver_leg(bsw, args)
-    sal_line = None
-    if rank == 0 and not args.no_sal and args.config == "read151" and args.pairs is None:
-        sal_line = sal_leg(bsw, args, stream, measured_peaks().get("hbm_gbs"))
-    smem_line = None
-    if rank == 0 and not args.no_smem and args.config == "read151" and args.pairs is None:
-        smem_line = smem_leg(bsw, args)
+    if rank == 0 and not args.no_nbases and short_read and not args.only:
+        nb_line = n_bases_leg(bsw, wl, plan, head["value"] / world, stream)
+    drv = sal_line = smem_line = serve = None
+    if rank == 0 and args.pairs is None and not args.only:
+        if not args.no_driver:
+            drv = driver_leg(bsw, args)
+        if not args.no_sal:
+            sal_line = sal_leg(bsw, args, stream, measured_peaks().get("hbm_gbs"))
+        if not args.no_smem:
+            smem_line = smem_leg(bsw, args)
+        if args.serve_quick > 0:
+            serve = serve_leg(args)
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": round(gcups, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8" if args.config != "long10k" else "int16", "data": "synthetic",
-            "config": {"workload": args.config, "description": WORKLOAD_TEXT.get(args.config, args.config),
-                       "pairs_per_gpu": n, "cells_per_step": cells,
-                       "l2": "inputs larger than L2 (%.0f MB resident packed inputs + %.0f MB results)"
-                             % (in_bytes / 1e6, n * 24 / 1e6),
+            "metric": METRIC, "value": head["value"], "unit": "GCUPS", "n_gpus": world, "steps": head["steps"],
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8 storage, int32 arithmetic" if args.config != "long10k"
+                     else "int16 storage, int32 arithmetic",
+            "dtype_note": "per-pair lane storage by the exact score bound h0 + match*min(n, m) (8-bit when <= 255, "
+                          "16-bit when <= 32767, else 32-bit); every operation runs in 32-bit registers and pairs "
+                          "whose scores leave their lane range are re-run exactly in 32 bits",
+            "data": "synthetic",
+            "config": {"workload": args.config, "description": head["description"],
+                       "pairs_per_gpu": head["pairs"], "cells_per_step": head["cells_per_step"], "l2": head["l2"],
                        "parallelism": "replicas x%d (pairs sharded by rank, no collective)" % world},
-            "plain": {"value": round(gcups_plain, 3), "unit": "GCUPS", "ms_per_step": round(ms_plain, 4),
-                      "kernel": "one pair per warp, input order", "bit_exact_vs_batched": plain_equal},
-            "speedup_vs_plain": round(gcups / gcups_plain, 3) if gcups_plain else None,
-            "two_pairs_per_thread": {"value": round(gcups_packed, 3), "unit": "GCUPS", "ms_per_step": round(ms_packed, 4),
-                                     "bit_exact_vs_batched": packed_equal},
-            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "dram_gbs": round(traffic / (ms_dom * 1e-3) / 1e9, 1) if traffic else None,
-                         "kernel": "%s (batch of its own class: %d pairs, %d cells; CUDA events around the "
-                                   "kernel on its stream, mean of %d launches)"
-                                   % (dom_kernel, sub.n_pairs, dom_cells, len(dom_ms)),
-                         "launch_ms": round(ms_dom, 4),
-                         "ops_per_cell": OPS_PER_CELL,
-                         "peak_basis": "%d SMs x %.0f MHz (median under load) x %d lane-ops/clk"
-                                       % (sms, f_mhz, LANE_OPS_PER_CLK_PER_SM)},
-            "cpu_baseline": cpu,
-            "parity_sample": parity,
+            "plain": head["plain"], "speedup_vs_plain": head["speedup_vs_plain"],
+            "plain_global": head["plain_global"],
+            "two_pairs_per_thread": head["two_pairs_per_thread"],
+            "roofline": head["roofline"],
+            "cpu_baseline": head.get("cpu_baseline"),
+            "parity_sample": head.get("parity"),
+            "e2e": head["e2e"],
+            "gpu_launches": head["kernels_per_step"] * head["steps"],
+            "kernels_per_step": head["kernels_per_step"],
+            "class_ms_in_step": head["class_ms_in_step"],
+            "plan": head["plan"],
+            "clocks": head["clocks"],
+            "workloads": others,
+            "serving": serve,
             "n_bases": nb_line,
             "extension_driver": drv,
             "suffix_array_lookup": sal_line,
             "smem_search": smem_line,
-            "e2e": {"value": round(e2e, 3), "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": round(t_e2e * 1e3, 3), "bit_exact_vs_device": e2e_equal},
-            "gpu_launches": launches_per_step * args.steps,
-            "kernels_per_step": launches_per_step,
-            "class_ms_in_step": {bsw.CLASS_NAMES[c]: round(t, 4) for c, t in enumerate(step_class_ms) if t > 0},
-            "plan": dict(plan.as_dict(), tuned=not (args.no_tune or args.plan), tune_s=round(t_tune, 2)),
-            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
-                       "samples": clk["samples"]},
             "peaks_file": {k: measured_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     dist.close()
     return 0
 
@@ -724,7 +842,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
-        from paper_1907_12931_gb300 import serve_bench
+        import serve_bench
         return serve_bench.main(args)
     return run_gb300(args)
 

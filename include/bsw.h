@@ -23,7 +23,9 @@
  *   - Bases are 2-bit codes A=0 C=1 G=2 T=3, packed four per byte, base k of a
  *     sequence in bits 2*(k%4)..2*(k%4)+1 of byte k/4 (bsw_pack_2bit).
  *     Offsets are in bases and must be multiples of 4, so every sequence starts
- *     on a byte.  Ambiguous bases (N) are not representable.
+ *     on a byte.  Ambiguous bases (N) ride beside the 2-bit codes in
+ *     optional per-side bitmaps (bsw_batch_t.q_n / t_n, bsw_pack_2bit_n): an
+ *     N scores -1 against any base, N included.
  *   - Extension runs rightward from the seed.  A left extension is the caller's
  *     job: pass the reversed query prefix and the reversed reference window.
  *   - An empty query returns {h0, 0, 0, 0, h0, 0}; an empty target returns
@@ -68,7 +70,10 @@ extern "C" {
                                     leave 0..255 are re-run exactly with 32-bit lanes   */
 #define BSW_FORCE_I16     0x04u  /* 16-bit lanes (same re-run rule above 32767)            */
 #define BSW_FORCE_I32     0x08u  /* 32-bit warp-per-pair kernel for every pair             */
-#define BSW_PLAIN_KERNEL  0x10u  /* baseline: one pair per warp, no bucketing, input order */
+#define BSW_PLAIN_KERNEL  0x10u  /* baseline: one pair per warp in input order (no
+                                    bucketing, classes or re-run list), each pair on
+                                    the warp-per-pair ring kernel with the plan's
+                                    warp_cols columns per lane                       */
 #define BSW_NO_GRAPH      0x20u  /* device-pointer path: launch directly, no CUDA graph    */
 #define BSW_COPY_INPUTS   0x40u  /* submit: copy host inputs at submit time                */
 #define BSW_PACKED_PAIRS  0x80u  /* 8-bit classes up to 128 query bases: two pairs per
@@ -76,6 +81,8 @@ extern "C" {
 #define BSW_TIME_KERNELS  0x100u /* record CUDA events around each class kernel (host
                                     pointers, or device pointers with BSW_NO_GRAPH);
                                     read them with bsw_kernel_times                     */
+#define BSW_PLAIN_GLOBAL  0x200u /* naive baseline: one pair per warp in input order, one
+                                    column per lane, the row's slots in global memory    */
 
 typedef struct bsw_ctx bsw_ctx_t;
 
@@ -168,7 +175,9 @@ int bsw_sync(bsw_ctx_t *ctx, void *cuda_stream);
  * BSW_OK for the ticket, unless BSW_COPY_INPUTS is set (inputs are copied
  * before submit returns; out must still stay valid).
  * Errors: BSW_EINVAL, BSW_EBUDGET (the batch alone exceeds the budget),
- * BSW_ENOMEM, BSW_ESTATE (context shutting down).
+ * BSW_ENOMEM, BSW_ESTATE (context shutting down).  A failed submit registers
+ * nothing: no ticket is issued, *ticket is left as it was, and the library
+ * never writes the batch's out.
  */
 int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *batch, bsw_result_t *out,
                       uint64_t *ticket);
@@ -180,6 +189,36 @@ int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *batch, bsw_result_t *ou
  * released) or the ticket is unknown (BSW_ENOTFOUND).
  */
 int bsw_stream_poll(bsw_ctx_t *ctx, uint64_t ticket, int32_t timeout_us);
+
+/*
+ * Host-side fault injection, for tests of the error paths.  The paper has no
+ * counterpart.  Nothing here touches the GPU: a named host call is made to
+ * fail as if the runtime had refused it, so the caller sees the documented
+ * code and the context must stay usable afterwards.  Sites:
+ *   alloc   a device (cudaMalloc) or pinned host (cudaMallocHost) allocation
+ *           of a context's buffers: the call returns BSW_ENOMEM
+ *   h2d     a host-to-device copy of a host batch (bsw_extend_batch with host
+ *           pointers, the serving loop's staging): BSW_ECUDA
+ *   launch  the launch of a batch's kernels: BSW_ECUDA
+ *   thread  the start of a context's serving thread: bsw_stream_submit
+ *           returns BSW_ENOMEM and registers nothing
+ *   host    a host container allocation in the serving path (ticket table,
+ *           queue, admission list): BSW_ENOMEM from bsw_stream_submit, or a
+ *           retried admission in the serving thread
+ * spec: a comma-separated list of site names, optionally followed by
+ * ":skip" and ":count" (defaults 0 and 1): of the later hits on any listed
+ * site the first `skip` pass and the next `count` fail; then injection stops.
+ * NULL or "" disarms.  The environment variable BSW_FAULT_INJECT, if set when
+ * the library loads, is applied the same way.  Process-wide; not meant for
+ * production use.  Returns BSW_OK, or BSW_EINVAL for a spec it cannot parse
+ * (the previous setting is then kept).
+ */
+#define BSW_FAULT_ALLOC  0x01u
+#define BSW_FAULT_H2D    0x02u
+#define BSW_FAULT_LAUNCH 0x04u
+#define BSW_FAULT_THREAD 0x08u
+#define BSW_FAULT_HOST   0x10u
+int bsw_fault_inject(const char *spec);
 
 /* Static English description of a return code. */
 const char *bsw_strerror(int code);

@@ -5,7 +5,9 @@
 // program measures lane-ops per clock per SM for each instruction kind on the
 // running GPU: one block of 1024 threads per SM, eight dependent chains per
 // thread that feed each other (so nothing folds), SM cycles from clock64().
-// Output: one JSON object per line.
+// Output: one JSON object per line.  It is a measurement program, not part of
+// the library; build it with
+//   nvcc -O3 -gencode arch=compute_103a,code=sm_103a -o _build/int_rates int_rates.cu
 #include <cuda_runtime.h>
 #include <cstdio>
 #include <vector>

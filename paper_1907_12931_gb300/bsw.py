@@ -35,6 +35,13 @@ BSW_NO_GRAPH = 0x20
 BSW_COPY_INPUTS = 0x40
 BSW_PACKED_PAIRS = 0x80
 BSW_TIME_KERNELS = 0x100
+BSW_PLAIN_GLOBAL = 0x200
+
+BSW_FAULT_ALLOC = 0x01
+BSW_FAULT_H2D = 0x02
+BSW_FAULT_LAUNCH = 0x04
+BSW_FAULT_THREAD = 0x08
+BSW_FAULT_HOST = 0x10
 
 # class_ms indices of bsw_timing_t
 CLASS_NAMES = ("u8<256>", "u8<192>", "u8<128>", "u8<96>", "u8<64>", "u8<48>", "u8<32>", "u8<16>",
@@ -162,6 +169,8 @@ def lib():
             L.bsw_set_reference_n.restype = ctypes.c_int
             L.bsw_extend_seeds_n.argtypes = [vp, i64, vp, vp, vp, vp, i64, vp, i32, vp, vp]
             L.bsw_extend_seeds_n.restype = ctypes.c_int
+            L.bsw_fault_inject.argtypes = [ctypes.c_char_p]
+            L.bsw_fault_inject.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -298,6 +307,11 @@ def bsw_extend_seeds(ctx: int, n_reads: int, reads, read_off, read_len, seeds, m
     return lib().bsw_extend_seeds(ctx, int(n_reads), reads.ctypes.data, read_off.ctypes.data, read_len.ctypes.data,
                                   int(seeds.shape[0]), seeds.ctypes.data, int(max_band_try), out.ctypes.data,
                                   ctypes.addressof(cells))
+
+
+def bsw_fault_inject(spec: str | None) -> int:
+    """Arm host-side fault injection ("alloc,h2d:skip:count"; None disarms)."""
+    return lib().bsw_fault_inject(None if spec is None else spec.encode())
 
 
 def bsw_sa_build(codes: np.ndarray) -> np.ndarray:

@@ -18,7 +18,6 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbsw.so")
 SOURCES = ["bsw_kernels.cu", "bsw_api.cu", "bsw_noalloc.cu", "bsw_driver.cu", "bsw_sal.cu", "bsw_sa.cu", "bsw_fm.cu"]
-INT_RATES = os.path.join(BUILD, "int_rates")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -27,15 +26,6 @@ def nvcc() -> str:
         if cand and os.path.exists(cand):
             return cand
     raise RuntimeError("nvcc not found")
-
-
-def build_int_rates() -> str:
-    """The integer issue-rate probe used to ground the ALU roofline (an executable)."""
-    os.makedirs(BUILD, exist_ok=True)
-    src = os.path.join(CSRC, "int_rates.cu")
-    if not os.path.exists(INT_RATES) or os.path.getmtime(INT_RATES) < os.path.getmtime(src):
-        subprocess.check_call([nvcc(), "-O3", "-o", INT_RATES, src] + ARCH)
-    return INT_RATES
 
 
 def _stale() -> bool:

@@ -16,8 +16,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
+#include <system_error>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -34,7 +36,7 @@ namespace {
 
 constexpr uint32_t kKnownFlags = BSW_DEVICE_PTRS | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32 |
                                  BSW_PLAIN_KERNEL | BSW_NO_GRAPH | BSW_COPY_INPUTS | BSW_PACKED_PAIRS |
-                                 BSW_TIME_KERNELS;
+                                 BSW_TIME_KERNELS | BSW_PLAIN_GLOBAL;
 constexpr int64_t kTuneSample = 1 << 21;   // default autotune sample (pairs)
 constexpr int kServeLanes = 3;
 constexpr int64_t kMergePairs = 1 << 20;   // the serving loop merges queued batches up to this many pairs
@@ -48,6 +50,104 @@ struct Budget {
     std::atomic<int64_t> used{0};
 };
 
+// ---------------------------------------------------------- fault injection
+//
+// bsw_fault_inject: listed host call sites fail after `skip` passing hits,
+// `count` times.  The fast path of an unarmed site is one relaxed load.
+struct Faults {
+    std::mutex mu;
+    std::atomic<uint32_t> sites{0};
+    int32_t skip = 0, count = 0;
+};
+
+Faults &faults()
+{
+    static Faults f;
+    return f;
+}
+
+bool fault_hit(uint32_t site)
+{
+    Faults &f = faults();
+    if (!(f.sites.load(std::memory_order_relaxed) & site)) return false;
+    std::lock_guard<std::mutex> lk(f.mu);
+    if (!(f.sites.load() & site)) return false;
+    if (f.skip > 0) {
+        --f.skip;
+        return false;
+    }
+    if (f.count > 0 && --f.count > 0) return true;
+    f.sites = 0;   // the last failure, or nothing left to fail
+    return true;
+}
+
+// "name[,name...][:skip[:count]]" with names alloc, h2d, launch, thread, host.
+bool parse_faults(const char *spec, uint32_t *sites, int32_t *skip, int32_t *count)
+{
+    *sites = 0;
+    *skip = 0;
+    *count = 1;
+    if (!spec || !*spec) {
+        *count = 0;
+        return true;
+    }
+    const char *p = spec;
+    for (;;) {
+        const char *q = p;
+        while (*q && *q != ',' && *q != ':') ++q;
+        const size_t len = (size_t)(q - p);
+        static const struct { const char *name; uint32_t bit; } kSites[] = {
+            {"alloc", BSW_FAULT_ALLOC}, {"h2d", BSW_FAULT_H2D}, {"launch", BSW_FAULT_LAUNCH},
+            {"thread", BSW_FAULT_THREAD}, {"host", BSW_FAULT_HOST}};
+        uint32_t bit = 0;
+        for (const auto &k : kSites)
+            if (std::strlen(k.name) == len && std::strncmp(k.name, p, len) == 0) bit = k.bit;
+        if (!bit) return false;
+        *sites |= bit;
+        p = q;
+        if (*p != ',') break;
+        ++p;
+    }
+    int32_t *num[2] = {skip, count};
+    for (int k = 0; k < 2 && *p == ':'; ++k) {
+        ++p;
+        if (*p < '0' || *p > '9') return false;
+        long v = 0;
+        while (*p >= '0' && *p <= '9') {
+            v = v * 10 + (*p++ - '0');
+            if (v > INT32_MAX) return false;
+        }
+        *num[k] = (int32_t)v;
+    }
+    return *p == '\0';
+}
+
+void set_faults(uint32_t sites, int32_t skip, int32_t count)
+{
+    Faults &f = faults();
+    std::lock_guard<std::mutex> lk(f.mu);
+    f.skip = skip;
+    f.count = count;
+    f.sites = count > 0 ? sites : 0u;
+}
+
+// BSW_FAULT_INJECT in the environment when the library loads.
+struct FaultsFromEnv {
+    FaultsFromEnv()
+    {
+        uint32_t s;
+        int32_t k, c;
+        if (parse_faults(std::getenv("BSW_FAULT_INJECT"), &s, &k, &c)) set_faults(s, k, c);
+    }
+} g_faults_from_env;
+
+// A host-to-device copy that the h2d site can make fail.
+cudaError_t h2d(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    if (fault_hit(BSW_FAULT_H2D)) return cudaErrorInvalidValue;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+}
+
 // One growable device allocation, charged to the context's budget.
 struct DevBuf {
     uint8_t *p = nullptr;
@@ -60,9 +160,10 @@ struct DevBuf {
         if (B.used.load() - (int64_t)cap + (int64_t)want > B.cap) want = align_up(bytes, 256);
         if (B.used.load() - (int64_t)cap + (int64_t)want > B.cap) return BSW_EBUDGET;
         release(B);
-        if (cudaMalloc(&p, want) != cudaSuccess) {
+        if (fault_hit(BSW_FAULT_ALLOC) || cudaMalloc(&p, want) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
+            if (moved) *moved = true;   // the old buffer is gone too
             return BSW_ENOMEM;
         }
         cap = want;
@@ -189,7 +290,7 @@ struct Lane {
         pinned = nullptr;
         pinned_cap = 0;
         size_t want = align_up(bytes + bytes / 4, 1 << 20);
-        if (cudaMallocHost(&pinned, want) != cudaSuccess) {
+        if (fault_hit(BSW_FAULT_ALLOC) || cudaMallocHost(&pinned, want) != cudaSuccess) {
             cudaGetLastError();
             pinned = nullptr;
             return BSW_ENOMEM;
@@ -371,7 +472,7 @@ cudaError_t enqueue_launch(bsw_ctx *c, Lane &lane, const Streams &S, const Batch
     cudaError_t e;
     Params P = c->P;
     P.flags = flags;
-    const bool plain = (flags & BSW_PLAIN_KERNEL) != 0;
+    const bool plain = (flags & (BSW_PLAIN_KERNEL | BSW_PLAIN_GLOBAL)) != 0;
     c->last_launches = plain ? 1 : batched_launches(L, flags);
     if (lane.work_dirty) {
         if ((e = cudaMemsetAsync(W.hist, 0, 4 * kNumBins, S.main)) != cudaSuccess) return e;
@@ -379,7 +480,8 @@ cudaError_t enqueue_launch(bsw_ctx *c, Lane &lane, const Streams &S, const Batch
     }
     if ((e = cudaMemsetAsync(W.cells, 0, 8, S.main)) != cudaSuccess) return e;
     if (reset_status && (e = cudaMemsetAsync(W.status, 0, 4, S.main)) != cudaSuccess) return e;
-    return plain ? launch_plain(B, P, W, S.main, c->sms) : launch_batched(B, P, W, S, c->sms, L, T);
+    if (fault_hit(BSW_FAULT_LAUNCH)) return cudaErrorLaunchFailure;
+    return plain ? launch_plain(B, P, W, S.main, c->sms, L) : launch_batched(B, P, W, S, c->sms, L, T);
 }
 
 // Timing events for BSW_TIME_KERNELS (created on first use); nullptr when the
@@ -468,8 +570,7 @@ int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B
         {L.t_off, b->t_off, 8 * (size_t)N}, {L.t_len, b->t_len, 4 * (size_t)N},
         {L.h0, b->h0, 4 * (size_t)N}, {L.w, b->w_override, b->w_override ? 4 * (size_t)N : 0}};
     for (const Cp &cp : meta)
-        if (cp.bytes && (e = cudaMemcpyAsync(d + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_rc(e);
+        if (cp.bytes && (e = h2d(d + cp.off, cp.src, cp.bytes, st)) != cudaSuccess) return cuda_rc(e);
     const PairMeta M{(const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len), (const int64_t *)(d + L.t_off),
                      (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
                      b->w_override ? (const int32_t *)(d + L.w) : nullptr};
@@ -505,8 +606,7 @@ int stage_host(bsw_ctx *c, const bsw_batch_t *b, cudaStream_t user, Batch *out_B
         {L.qn, b->q_n ? b->q_n + nmask_lo(q_lo) : nullptr, (size_t)qnb},
         {L.tn, b->t_n ? b->t_n + nmask_lo(t_lo) : nullptr, (size_t)tnb}};
     for (const Cp &cp : seqs)
-        if (cp.bytes && (e = cudaMemcpyAsync(sq + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_rc(e);
+        if (cp.bytes && (e = h2d(sq + cp.off, cp.src, cp.bytes, st)) != cudaSuccess) return cuda_rc(e);
     *out_B = Batch{N, sq + L.q - q_lo, M.q_off, M.q_len, sq + L.t - t_lo, M.t_off, M.t_len, M.h0, M.w,
                    (bsw_result_t *)(d + L.out), b->q_n ? sq + L.qn - nmask_lo(q_lo) : nullptr,
                    b->t_n ? sq + L.tn - nmask_lo(t_lo) : nullptr};
@@ -641,7 +741,7 @@ int serve_launch(bsw_ctx *c, int li)
     cudaStream_t st = lane.S.main;
     uint8_t *d = lane.io.p;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(d, h, L.in_end, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = h2d(d, h, L.in_end, st)) != cudaSuccess) return cuda_rc(e);
     Batch B{N, d + L.q, (const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len), d + L.t,
             (const int64_t *)(d + L.t_off), (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
             (const int32_t *)(d + L.w), (bsw_result_t *)(d + L.out)};
@@ -702,6 +802,7 @@ void server_main(bsw_ctx *c)
                 while (!c->queue.empty() &&
                        (reqs.empty() || (pairs + c->queue.front()->b.n_pairs <= kMergePairs &&
                                          ecells + c->queue.front()->ext.est_cells <= kMergeCells))) {
+                    if (fault_hit(BSW_FAULT_HOST)) throw std::bad_alloc();
                     reqs.push_back(c->queue.front());
                     pairs += c->queue.front()->b.n_pairs;
                     ecells += c->queue.front()->ext.est_cells;
@@ -925,13 +1026,14 @@ int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, u
     return guard([&]() -> int {
         if (!ctx || !b || !ticket) return BSW_EINVAL;
         if (b->n_pairs < 0 || b->n_pairs > INT32_MAX || (b->flags & ~kKnownFlags)) return BSW_EINVAL;
-        if (b->flags & (BSW_DEVICE_PTRS | BSW_PLAIN_KERNEL | BSW_FORCE_I8 | BSW_FORCE_I16 | BSW_FORCE_I32 |
-                        BSW_TIME_KERNELS))
+        if (b->flags & (BSW_DEVICE_PTRS | BSW_PLAIN_KERNEL | BSW_PLAIN_GLOBAL | BSW_FORCE_I8 | BSW_FORCE_I16 |
+                        BSW_FORCE_I32 | BSW_TIME_KERNELS))
             return BSW_EINVAL;   // the serving loop runs the context's batched plan on host inputs
         if (b->q_n || b->t_n) return BSW_EINVAL;   // no N bitmaps in the serving loop
         if (b->n_pairs > 0 && (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out))
             return BSW_EINVAL;
-        Request *r = new (std::nothrow) Request();
+        std::unique_ptr<Request> holder(new (std::nothrow) Request());
+        Request *r = holder.get();
         if (!r) return BSW_ENOMEM;
         r->b = *b;
         r->out = out;
@@ -968,30 +1070,56 @@ int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, u
                 if (b->w_override) r->b.w_override = (const int32_t *)dup(b->w_override, 4 * (size_t)N);
             }
         }
-        if (rc != BSW_OK) {
-            delete r;
-            return rc;
-        }
+        if (rc != BSW_OK) return rc;
+        // Commit under the lock, all or nothing: the server thread is started
+        // first, then the ticket and the queue entry go in; if any step
+        // throws, what was added is taken out again and no ticket is issued,
+        // so the server never sees (or writes the out of) a failed request.
         std::lock_guard<std::mutex> lk(ctx->mu);
-        if (ctx->stop) {
-            delete r;
-            return BSW_ESTATE;
-        }
-        r->ticket = ctx->next_ticket++;
-        *ticket = r->ticket;
-        ctx->tickets[r->ticket] = r;
-        if (b->n_pairs == 0) {
-            r->status = BSW_OK;
-            return BSW_OK;
-        }
-        ctx->queue.push_back(r);
-        if (!ctx->server_started) {
-            ctx->server = std::thread(server_main, ctx);
+        if (ctx->stop) return BSW_ESTATE;
+        if (b->n_pairs > 0 && !ctx->server_started) {
+            try {
+                if (fault_hit(BSW_FAULT_THREAD))
+                    throw std::system_error(std::make_error_code(std::errc::resource_unavailable_try_again));
+                ctx->server = std::thread(server_main, ctx);
+            } catch (...) {
+                return BSW_ENOMEM;
+            }
             ctx->server_started = true;
         }
-        ctx->cv_work.notify_one();
+        const uint64_t t = ctx->next_ticket;
+        r->ticket = t;
+        if (b->n_pairs == 0) r->status = BSW_OK;
+        try {
+            if (fault_hit(BSW_FAULT_HOST)) throw std::bad_alloc();
+            ctx->tickets.emplace(t, r);
+        } catch (...) {
+            return BSW_ENOMEM;
+        }
+        if (b->n_pairs > 0) {
+            try {
+                if (fault_hit(BSW_FAULT_HOST)) throw std::bad_alloc();
+                ctx->queue.push_back(r);
+            } catch (...) {
+                ctx->tickets.erase(t);
+                return BSW_ENOMEM;
+            }
+        }
+        holder.release();
+        ctx->next_ticket = t + 1;
+        *ticket = t;
+        if (b->n_pairs > 0) ctx->cv_work.notify_one();
         return BSW_OK;
     });
+}
+
+int bsw_fault_inject(const char *spec)
+{
+    uint32_t sites;
+    int32_t skip, count;
+    if (!parse_faults(spec, &sites, &skip, &count)) return BSW_EINVAL;
+    set_faults(sites, skip, count);
+    return BSW_OK;
 }
 
 int bsw_stream_poll(bsw_ctx_t *ctx, uint64_t ticket, int32_t timeout_us)

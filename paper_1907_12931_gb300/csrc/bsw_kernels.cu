@@ -18,7 +18,10 @@
 //                                owns C consecutive columns of a row chunk and
 //                                F is a max-plus scan across lanes; used for
 //                                long queries and the 32-bit re-run
-//   k_plain                      the baseline: one pair per warp, input order
+//   k_plain<C>                   the baseline: the warp-per-pair ring kernel
+//                                over pairs in input order, no batching
+//   k_plain_global               the naive baseline: one column per lane and
+//                                the row in global memory
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -1307,9 +1310,92 @@ __global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2) k_warp(B
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
 
-// Baseline: one pair per warp in input order, no bucketing, no persistence
-// beyond a grid-stride loop; 16-bit slots when the score bound allows.
-__global__ void __launch_bounds__(256) k_plain(Batch B, Params P, Work W)
+// Checks of one pair for the plain kernels (the checks k_classify makes);
+// answers pairs with an empty side.  Returns the pair's score bound, or -1
+// when there is nothing to compute.
+__device__ __forceinline__ long long plain_check(const Batch &B, const Params &P, const Work &W, int64_t p,
+                                                 int lane)
+{
+    const int n = B.q_len[p], m = B.t_len[p], h0 = B.h0[p];
+    const int64_t qo = B.q_off[p], to = B.t_off[p];
+    const int w = B.w_override ? B.w_override[p] : P.w;
+    if (n < 0 || m < 0 || h0 < 0 || w < 0 || qo < 0 || to < 0 || (qo & 3) || (to & 3)) {
+        if (lane == 0) atomicOr(W.status, kStInval);
+        return -1;
+    }
+    if (n == 0 || m == 0) {
+        if (lane == 0) store_result(&B.out[p], h0, 0, 0, 0, n == 0 ? h0 : -1, 0);
+        return -1;
+    }
+    const long long bound = (long long)h0 + (long long)P.a * min(n, m);
+    if (bound >= (1ll << 30)) {
+        if (lane == 0) atomicOr(W.status, kStInval);
+        return -1;
+    }
+    if (n > P.max_qlen) {
+        if (lane == 0) atomicOr(W.status, kStTooLong);
+        return -1;
+    }
+    return bound;
+}
+
+// The plain baseline: the best one-pair-per-warp kernel with no batching
+// around it.  Each warp takes pairs in input order (grid stride), with no
+// bucketing, no classes and no re-run list, and extends each with the
+// warp-per-pair ring kernel of C columns per lane (16-bit slots when the
+// score bound allows and the pair has no N; the 32-bit kernel otherwise).  A
+// pair whose band needs a larger ring than the warp has uses the warp's
+// global slot scratch.  ring16_log2 / ring32_log2: the warp's rings (0: none).
+template <int C>
+__global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2)
+    k_plain(Batch B, Params P, Work W, int ring16_log2, int ring32_log2, int64_t ring_bytes_per_warp)
+{
+    extern __shared__ uint8_t ring_mem[];
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    uint8_t *slots = W.slots + gw * W.slot_bytes_per_warp;
+    uint8_t *ring = ring_mem + (size_t)(threadIdx.x >> 5) * ring_bytes_per_warp;
+    const bool sym = P.o_del == P.o_ins && P.e_del == P.e_ins;
+    unsigned long long cells = 0;
+    for (int64_t p = gw; p < B.n; p += nw) {
+        const long long bound = plain_check(B, P, W, p, lane);
+        if (bound < 0) continue;
+        const int n = B.q_len[p];
+        const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
+        const bool has_n = (B.q_n || B.t_n) && pair_has_n(B, B.q_off[p], n, B.t_off[p], B.t_len[p]);
+        if (bound <= 32767 && !has_n) {
+            const int need = ring_slots<C>(wb);
+            if (ring16_log2 > 0 && need <= (1 << ring16_log2)) {
+                int *RH = reinterpret_cast<int *>(ring);
+                int *RE = RH + (ring_bytes<true, C>(ring16_log2) / 8);
+                cells += sym ? warp_pair_ring16<C, true>(B, P, (int)p, RH, RE, need - 1)
+                             : warp_pair_ring16<C, false>(B, P, (int)p, RH, RE, need - 1);
+                continue;
+            }
+        } else {
+            int need = 64;
+            while (need < 2 * wb + 3) need <<= 1;
+            if (ring32_log2 > 0 && need <= (1 << ring32_log2)) {
+                cells += has_n ? warp_pair<8, false, true, true>(B, P, (int)p, ring, need - 1)
+                               : warp_pair<8, false, true, false>(B, P, (int)p, ring, need - 1);
+                continue;
+            }
+        }
+        if ((int64_t)(n + 1 + 32 * 8) * 8 > W.slot_bytes_per_warp) {
+            if (lane == 0) atomicOr(W.status, kStTooLong);
+            continue;
+        }
+        cells += has_n ? warp_pair<8, false, false, true>(B, P, (int)p, slots, 0)
+                       : warp_pair<8, false, false, false>(B, P, (int)p, slots, 0);
+    }
+    if (lane == 0 && cells) atomicAdd(W.cells, cells);
+}
+
+// The naive baseline (BSW_PLAIN_GLOBAL): one pair per warp in input order,
+// one column per lane, the row's slots in global memory; 16-bit slots when
+// the score bound allows.
+__global__ void __launch_bounds__(256) k_plain_global(Batch B, Params P, Work W)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1622,6 +1708,12 @@ cudaError_t prepare_kernels(int sms)
         return e;
     if ((e = cudaFuncSetAttribute(k_warp<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_plain<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_plain<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_plain<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
+        return e;
     if ((e = prepare_inter<256, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<192, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<128, true>()) != cudaSuccess) return e;
@@ -1681,11 +1773,38 @@ cudaError_t launch_batched_serial(const Batch &B, const Params &P0, const Work &
     return cudaSuccess;
 }
 
-cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms)
+namespace {
+
+template <int C>
+cudaError_t launch_plain_c(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms)
+{
+    // rings for the context's band: 16-bit for C columns per lane, 32-bit as
+    // the warp kernel's 32-bit class has them; a warp's share of shared
+    // memory holds the larger
+    const int lg16 = ring_log2_for<true, C>(P), lg32 = ring_log2_for<false, 8>(P);
+    const size_t r16 = lg16 ? ring_bytes<true, C>(lg16) : 0, r32 = lg32 ? ring_bytes<false, 8>(lg32) : 0;
+    const size_t per_warp = r16 > r32 ? r16 : r32;
+    constexpr int tpb = warp_threads<C>();
+    constexpr int bps = C >= 16 ? 3 : 2;   // blocks per SM of the launch bounds
+    const size_t smem = per_warp * (tpb / 32);
+    if (smem > kRingSmemMax) return cudaErrorInvalidValue;
+    // at most as many warps as the work buffers have slot regions
+    k_plain<C><<<sms * bps, tpb, smem, st>>>(B, P, W, lg16, lg32, (int64_t)per_warp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms, const Plan &L)
 {
     if (B.n <= 0) return cudaSuccess;
-    k_plain<<<sms * kWarpBlocksPerSM, kWarpKernelThreads, 0, st>>>(B, P, W);
-    return cudaGetLastError();
+    if (P.flags & BSW_PLAIN_GLOBAL) {
+        k_plain_global<<<sms * kWarpBlocksPerSM, kWarpKernelThreads, 0, st>>>(B, P, W);
+        return cudaGetLastError();
+    }
+    if (L.warp_cols == 4) return launch_plain_c<4>(B, P, W, st, sms);
+    if (L.warp_cols == 16) return launch_plain_c<16>(B, P, W, st, sms);
+    return launch_plain_c<8>(B, P, W, st, sms);
 }
 
 }  // namespace bsw

@@ -75,8 +75,10 @@ cudaError_t launch_batched(const Batch &B, const Params &P, const Work &W, const
 cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms,
                                   int warp_blocks, const Plan &L);
 
-// Baseline: one pair per warp in input order.
-cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms);
+// Baseline: one pair per warp in input order, the warp kernel with the
+// plan's columns per lane (or, with BSW_PLAIN_GLOBAL in P.flags, the naive
+// one-column-per-lane kernel with its row in global memory).
+cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms, const Plan &L);
 
 // Per-pair arrays of a host batch already on the device, checked and reduced
 // there: whether any pair is invalid (the checks of bsw_extend_batch) and, over

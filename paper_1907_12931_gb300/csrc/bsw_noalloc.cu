@@ -49,7 +49,6 @@ static __device__ __align__(256) uint8_t g_scratch[BSW_NOALLOC_SCRATCH_BYTES];
 
 struct DeviceSetup {
     bool done = false;
-    int rc = BSW_OK;
     uint8_t *scratch = nullptr;   // device address of g_scratch on that device
     int sms = 0;
 };
@@ -58,28 +57,30 @@ std::mutex g_setup_lock;
 DeviceSetup g_setup[64];
 
 // Once per device, with that device current: the array's device address (in
-// host code the symbol is only a host-side stand-in), SM count, kernel attributes.
+// host code the symbol is only a host-side stand-in), SM count, kernel
+// attributes.  A device counts as set up only when every step succeeded; a
+// failed set-up (for example a first call made during a stream capture)
+// records nothing and is tried again by the next call.
 int setup_device(int dev, DeviceSetup **out)
 {
     if (dev < 0 || dev >= 64) return BSW_EINVAL;
     std::lock_guard<std::mutex> lk(g_setup_lock);
     DeviceSetup &s = g_setup[dev];
     if (!s.done) {
-        s.done = true;
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) {
+        int sms = 0;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            prepare_kernels(sms) != cudaSuccess) {
             cudaGetLastError();
-            s.rc = BSW_ECUDA;
-        } else if (cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-                   prepare_kernels(s.sms) != cudaSuccess) {
-            cudaGetLastError();
-            s.rc = BSW_ECUDA;
-        } else {
-            s.scratch = (uint8_t *)p;
+            return BSW_ECUDA;
         }
+        s.scratch = (uint8_t *)p;
+        s.sms = sms;
+        s.done = true;
     }
     *out = &s;
-    return s.rc;
+    return BSW_OK;
 }
 
 }  // namespace

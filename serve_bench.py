@@ -17,12 +17,17 @@ from __future__ import annotations
 
 import json
 import os
+import sys
 import threading
 import time
 
 import numpy as np
 
-from . import bsw, workload as W
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1907_12931_gb300 import bsw, workload as W  # noqa: E402
 
 POOL_PAIRS = {"read151": 200_000, "read250": 200_000, "long10k": 20_000}
 MAX_REQ = 50_000
@@ -106,12 +111,9 @@ def run_point(ctxs, reqs, rate, verify):
     return lat, wall, cells, mism
 
 
-def main(args) -> int:
-    import torch
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    if int(os.environ.get("RANK", "0")) != 0:
-        return 0
+def sweep(loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0), nreq=1000, calib=200, verify=True):
+    """The serving sweep: pools, contexts, tuned plans, the all-queued peak,
+    then one point per offered load.  Returns the result record."""
     nth = os.cpu_count() or 1
     names = ["read151", "read250", "long10k"]
     pools = [Pool(nm, nth) for nm in names]
@@ -120,7 +122,6 @@ def main(args) -> int:
     ctxs = [ctx_short, ctx_short, ctx_long]
     plans = {"short": ctx_short.autotune(bsw.HostBatch(pools[1].wl)).as_dict(),
              "long": ctx_long.autotune(bsw.HostBatch(pools[2].wl)).as_dict()}
-    nreq = int(getattr(args, "serve_requests", 0) or 1000)
     rng = np.random.default_rng(2024)
 
     # A set of distinct requests (packed once); submissions draw from it.
@@ -136,33 +137,51 @@ def main(args) -> int:
         return [distinct[int(k)] for k in rng.integers(0, len(distinct), count)]
 
     # peak: every request queued at once
-    calib = make_reqs(min(nreq, 200))
-    run_point(ctxs, calib[:20], None, False)                   # warm-up
-    lat, wall, cells, mism = run_point(ctxs, calib, None, True)
+    creqs = make_reqs(min(nreq, calib))
+    run_point(ctxs, creqs[:20], None, False)                   # warm-up
+    lat, wall, cells, mism = run_point(ctxs, creqs, None, verify)
     peak_gcups = cells / wall / 1e9
-    mean_cells = cells / len(calib)
+    mean_cells = cells / len(creqs)
     points = []
     total_mism = mism
     reqs = make_reqs(nreq)
-    for load in (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0):
+    for load in loads:
         rate = load * peak_gcups * 1e9 / mean_cells
-        lat, wall, cells, mism = run_point(ctxs, reqs, rate, True)
+        lat, wall, cells, mism = run_point(ctxs, reqs, rate, verify)
         total_mism += mism
         points.append({"offered_load": load, "offered_req_per_s": round(rate, 2),
                        "p50_ms": round(_percentile(lat, 50), 3), "p99_ms": round(_percentile(lat, 99), 3),
                        "throughput_gcups": round(cells / wall / 1e9, 2), "requests": len(reqs),
                        "mismatches": mism})
+    ctx_short.close()
+    ctx_long.close()
+    return {
+        "workload": "serve: Poisson arrivals, requests of 1-50000 pairs from read151/read250/long10k "
+                    "pools (p = 1/3 each), 20 GB budget over two contexts",
+        "requests_per_point": nreq, "peak_gcups_all_queued": round(peak_gcups, 2),
+        "mean_cells_per_request": int(mean_cells), "plans": plans,
+        "points": points, "bit_exact_mismatches": total_mism,
+        "parity": "every result of every request compared with the oracle" if verify else "not checked",
+    }
+
+
+def main(args) -> int:
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    nreq = int(getattr(args, "serve_requests", 0) or 1000)
+    r = sweep(nreq=nreq)
+    points = r["points"]
     line = {
         "metric": "BSW serve p50/p99 latency vs offered load (continuous batching)",
         "value": points[-1]["p99_ms"], "unit": "ms (p99 at 100% offered load)", "n_gpus": world,
         "higher_is_better": False, "data": "synthetic",
-        "config": {"workload": "serve: Poisson arrivals, requests of 1-50000 pairs from read151/read250/long10k "
-                               "pools (p = 1/3 each), 20 GB budget over two contexts",
-                   "requests_per_point": nreq, "peak_gcups_all_queued": round(peak_gcups, 2),
-                   "mean_cells_per_request": int(mean_cells), "plans": plans},
-        "points": points, "bit_exact_mismatches": total_mism,
+        "config": {"workload": r["workload"], "requests_per_point": nreq,
+                   "peak_gcups_all_queued": r["peak_gcups_all_queued"],
+                   "mean_cells_per_request": r["mean_cells_per_request"], "plans": r["plans"]},
+        "points": points, "bit_exact_mismatches": r["bit_exact_mismatches"],
     }
     print(json.dumps(line), flush=True)
-    ctx_short.close()
-    ctx_long.close()
-    return 0 if total_mism == 0 else 1
+    return 0 if r["bit_exact_mismatches"] == 0 else 1

@@ -16,7 +16,7 @@ from test_gpu_parity import NTH, adversarial, assert_same, flag_of, run
 
 pytestmark = pytest.mark.gpu
 
-FLAGS = [0, "plain", "i8", "i16", "i32", "packed", "i8packed"]
+FLAGS = [0, "plain", "plainglobal", "i8", "i16", "i32", "packed", "i8packed"]
 
 
 @pytest.fixture(scope="module")

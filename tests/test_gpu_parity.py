@@ -46,8 +46,10 @@ def assert_same(got, ref, what):
                              % (what, bad.size, ref.shape[0], k, got[k].tolist(), ref[k].tolist()))
 
 
-def run(bsw, wl, flags=0, device=False, budget=16 << 30, w_override=None, params=None):
+def run(bsw, wl, flags=0, device=False, budget=16 << 30, w_override=None, params=None, warp_cols=None):
     with bsw.Context(params or wl.params, budget) as ctx:
+        if warp_cols is not None:
+            ctx.set_plan(bsw.make_plan(warp_cols=warp_cols))
         hb = bsw.HostBatch(wl, w_override=w_override)
         if not device:
             return ctx.extend_host(hb, flags)
@@ -60,12 +62,13 @@ def run(bsw, wl, flags=0, device=False, budget=16 << 30, w_override=None, params
 
 
 def flag_of(bsw, name):
-    return {0: 0, "plain": bsw.BSW_PLAIN_KERNEL, "i8": bsw.BSW_FORCE_I8, "i16": bsw.BSW_FORCE_I16,
+    return {0: 0, "plain": bsw.BSW_PLAIN_KERNEL, "plainglobal": bsw.BSW_PLAIN_GLOBAL,
+            "i8": bsw.BSW_FORCE_I8, "i16": bsw.BSW_FORCE_I16,
             "i32": bsw.BSW_FORCE_I32, "packed": bsw.BSW_PACKED_PAIRS,
             "i8packed": bsw.BSW_FORCE_I8 | bsw.BSW_PACKED_PAIRS}[name]
 
 
-@pytest.mark.parametrize("flags", [0, "plain", "i8", "i16", "i32", "packed", "i8packed"])
+@pytest.mark.parametrize("flags", [0, "plain", "plainglobal", "i8", "i16", "i32", "packed", "i8packed"])
 def test_plain10k(bsw, flags):
     wl, ref, cells = workload_and_oracle("plain10k")
     f = flag_of(bsw, flags)
@@ -99,10 +102,21 @@ def test_full_workloads_packed_pairs(bsw, config):
 
 
 @pytest.mark.parametrize("config", ["read151", "read250", "long10k"])
-def test_full_workloads_plain(bsw, config):
+@pytest.mark.parametrize("warp_cols", [4, 8, 16])
+def test_full_workloads_plain(bsw, config, warp_cols):
+    """The plain baseline (the ring warp kernel over pairs in input order) with
+    each column count, on every pair of the full workloads."""
     wl, ref, cells = workload_and_oracle(config)
-    got, gc = run(bsw, wl, bsw.BSW_PLAIN_KERNEL, device=True)
-    assert_same(got, ref, config + "/plain")
+    got, gc = run(bsw, wl, bsw.BSW_PLAIN_KERNEL, device=True, warp_cols=warp_cols)
+    assert_same(got, ref, "%s/plain C=%d" % (config, warp_cols))
+    assert gc == cells
+
+
+@pytest.mark.parametrize("config", ["read151", "long10k"])
+def test_full_workloads_plain_global(bsw, config):
+    wl, ref, cells = workload_and_oracle(config)
+    got, gc = run(bsw, wl, bsw.BSW_PLAIN_GLOBAL, device=True)
+    assert_same(got, ref, config + "/plain global")
     assert gc == cells
 
 
@@ -158,14 +172,18 @@ def adversarial():
 
 
 @pytest.mark.parametrize("zdrop", [100, 0, 1, 7])
-@pytest.mark.parametrize("flags", [0, "plain", "i16", "i32", "i8", "packed"])
+@pytest.mark.parametrize("flags", [0, "plain", "plain4", "plain16", "plainglobal", "i16", "i32", "i8", "packed"])
 def test_adversarial(bsw, zdrop, flags):
     wl, ws = adversarial()
     params = W.Params(W.Scoring(), w=100, zdrop=zdrop, end_bonus=5)
     wl.params = params
     ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH, w_override=ws)
+    cols = None
+    if flags in ("plain4", "plain16"):
+        cols = int(flags[5:])
+        flags = "plain"
     f = flag_of(bsw, flags)
-    got, gc = run(bsw, wl, f, w_override=ws)
+    got, gc = run(bsw, wl, f, w_override=ws, warp_cols=cols)
     assert_same(got, ref, "adversarial zdrop=%d flags=%s" % (zdrop, flags))
     assert gc == int(cells.sum())
 

@@ -1,14 +1,18 @@
-"""bsw_extend_batch_noalloc against bsw_extend_batch (needs a GPU).
+"""bsw_extend_batch_noalloc against bsw_extend_batch and the oracle (needs a GPU).
 
 The allocation-free entry point serves callers that may not allocate device
 memory; it keeps its work buffers in one device array that every call reuses.
 Two calls in a row, on different batches, must each give exactly what the
-context-based entry point gives, so nothing a call leaves in the array leaks
-into the next.  This file is collected last on purpose.
+context-based entry point gives and what the CPU oracle gives, so nothing a
+call leaves in the array leaks into the next.  This file is collected last on
+purpose.
 """
+import os
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_1907_12931_gb300 import workload as W
 
 pytestmark = pytest.mark.gpu
@@ -54,6 +58,9 @@ def test_two_calls_in_a_row_match_extend_batch(env):
         assert rc == bsw.BSW_OK, bsw.bsw_strerror(rc)
         np.testing.assert_array_equal(got, ref)
         assert cells == ref_cells
+        want, want_cells, _ = oracle.extend_batch(wl, nthreads=os.cpu_count() or 1)
+        np.testing.assert_array_equal(got, want)
+        assert cells == int(want_cells.sum())
 
 
 def test_forced_lanes_and_limits(env):
