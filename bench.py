@@ -77,7 +77,8 @@ def parse():
     ap.add_argument("--no-smem", action="store_true", help="skip the SMEM search leg")
     ap.add_argument("--no-nbases", action="store_true", help="skip the N-bases leg")
     ap.add_argument("--plan", default=None,
-                    help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps (no autotune)")
+                    help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps[,cta_min] "
+                         "(no autotune)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point (--serve)")
     ap.add_argument("--serve-quick", type=int, default=200,
                     help="requests per point of the bounded serving leg of the default run (0: skip it)")
@@ -204,15 +205,18 @@ def _smallest_class(n, nmax, mask, first):
 
 def class_of(q_len, t_len, h0, match, plan):
     """Kernel class of each pair under a plan, as the library buckets it: 0-7
-    8-bit lanes (class bounds 256..16), 8-11 16-bit lanes (256..32), 12 warp per
-    pair with 16-bit slots, 13 with 32-bit slots, -1 empty."""
+    8-bit lanes (class bounds 256..16), 8-11 16-bit lanes (256..32), 12 block
+    per pair (16-bit range, at least cta_min bases), 13 warp per pair with
+    16-bit-range scores, 14 with 32-bit scores, -1 empty."""
     n = np.asarray(q_len, np.int64)
     m = np.asarray(t_len, np.int64)
     bound = np.asarray(h0, np.int64) + match * np.minimum(n, m)
     u8 = _smallest_class(n, U8_NMAX, plan.u8_bounds | 1, 0)
     i16 = _smallest_class(n, I16_NMAX, plan.i16_bounds | 1, 8)
-    c = np.where(n > plan.short_max, np.where(bound <= 32767, 12, 13),
-                 np.where(bound <= 255, u8, np.where(bound <= 32767, i16, 13)))
+    cta_min = getattr(plan, "cta_min", 0)
+    w16 = np.where((cta_min > 0) & (n >= max(cta_min, 1)), 12, 13)
+    c = np.where(n > plan.short_max, np.where(bound <= 32767, w16, 14),
+                 np.where(bound <= 255, u8, np.where(bound <= 32767, i16, 14)))
     return np.where((n <= 0) | (m <= 0), -1, c)
 
 
@@ -227,7 +231,9 @@ def class_kernel(c, plan, scoring):
         return "k_inter<%d,u8>" % nm
     if c < 12:
         return "k_inter<%d,i16>" % I16_NMAX[c - 8]
-    return "k_warp<%d,s16>" % plan.warp_cols if c == 12 else "k_warp<8,s32>"
+    if c == 12:
+        return "k_cta<8,s16>"
+    return "k_warp<%d,s16>" % plan.warp_cols if c == 13 else "k_warp<8,s32>"
 
 
 # ------------------------------------------------------------------ arms
@@ -595,7 +601,7 @@ def plain_leg(bsw, ctx, db, plan, steps, warmup, stream, dist, out_ref, cells_re
     per = {}
     for cols in (4, 8, 16):
         ctx.set_plan(bsw.make_plan(plan.short_max, plan.u8_bounds, plan.i16_bounds, plan.packed, cols,
-                                   plan.inter_warps))
+                                   plan.inter_warps, plan.cta_min))
         ms = time_device(ctx, db, bsw.BSW_PLAIN_KERNEL, steps, warmup, stream, dist)
         equal = bool(np.array_equal(db.out.cpu().numpy(), out_ref)) and int(db.cells.item()) == cells_ref
         per[cols] = (ms, equal)
@@ -613,7 +619,7 @@ def dominant_leg(bsw, ctx, wl, plan, stream, dist, steps, clk_mhz, sms):
     stream just before and after its launch, averaged over launches."""
     all_cls = class_of(wl.q_len, wl.t_len, wl.h0, wl.params.scoring.match, plan)
     est = wl.q_len.astype(np.float64) * np.minimum(wl.t_len, 2 * wl.params.w + 1)
-    dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(14)]))
+    dom = int(np.argmax([float(est[all_cls == c].sum()) for c in range(15)]))
     sub = wl.subset(np.nonzero(all_cls == dom)[0])
     sdb = bsw.DeviceBatch(bsw.HostBatch(sub))
     for _ in range(2):

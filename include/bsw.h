@@ -306,17 +306,22 @@ int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, 
  *   warp_cols    columns each lane owns per row chunk in the 16-bit
  *                warp-per-pair kernel: 4, 8 or 16.
  *   inter_warps  warps per block of the per-thread kernels: 1, 2 or 4.
+ *   cta_min      queries of at least cta_min bases whose scores fit 16 bits
+ *                (and that hold no N) run one pair per block of 4 warps, the
+ *                row's band split across the warps (uneven batches: the
+ *                longest pairs no longer set the batch's tail); 0: none.  A
+ *                multiple of 64 in [128, BSW_MAX_QLEN], or 0.
  *   ms           output of bsw_autotune (the plan's time on its sample, in
  *                milliseconds); ignored by bsw_set_plan.
  */
 typedef struct {
     int32_t short_max;
     uint32_t u8_bounds, i16_bounds;
-    int32_t packed, warp_cols, inter_warps;
+    int32_t packed, warp_cols, inter_warps, cta_min;
     float ms;
 } bsw_plan_t;
 
-/* The context's current plan (a new context has {256, 0xff, 0xf, 0, 8, 2}).
+/* The context's current plan (a new context has {256, 0xff, 0xf, 0, 8, 2, 0}).
  * Errors: BSW_EINVAL (null argument). */
 int bsw_get_plan(const bsw_ctx_t *ctx, bsw_plan_t *plan);
 
@@ -330,7 +335,8 @@ int bsw_set_plan(bsw_ctx_t *ctx, const bsw_plan_t *plan);
  * timed with CUDA events as the fastest of `reps` launches (reps <= 0: 3)
  * after one warm-up launch, on the context's stream.  The search is
  * coordinate descent from the default plan: short_max (256, 192, 128, 96,
- * 64), warp_cols (8, 4, 16), packed, inter_warps (2, 1, 4), then each class
+ * 64), warp_cols (8, 4, 16), cta_min (0, 8192, 4096, 2048, 1024, 512),
+ * packed, inter_warps (2, 1, 4), then each class
  * boundary removed in turn (8-bit from 192 down, then 16-bit); a change is
  * kept when it is at least 1% faster than the best so far.  A knob that only
  * affects classes holding no pair of the sample is not tried, and the
@@ -352,15 +358,16 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *batch, int64_t sample_pairs,
  * events recorded on the stream of class c's kernel just before and just
  * after its launch (0 if the class was not launched).  Classes: 0-7 the 8-bit
  * per-thread classes of bound 256, 192, 128, 96, 64, 48, 32, 16; 8-11 the
- * 16-bit classes of bound 256, 128, 64, 32; 12 the 16-bit warp-per-pair
- * kernel; 13 the 32-bit one; 14 the 32-bit re-run.  launches = the kernels
+ * 16-bit classes of bound 256, 128, 64, 32; 12 the block-per-pair kernel; 13
+ * the 16-bit warp-per-pair kernel; 14 the 32-bit one; 15 the 32-bit re-run.
+ * launches = the kernels
  * the last batched call launched (timed or not; the plain kernel counts 1).
  * Errors: BSW_EINVAL (null argument), BSW_ESTATE (no timed call yet),
  * BSW_ECUDA.
  */
 typedef struct {
     int32_t launches;
-    float class_ms[15];
+    float class_ms[16];
 } bsw_timing_t;
 int bsw_kernel_times(bsw_ctx_t *ctx, bsw_timing_t *out);
 

@@ -45,7 +45,7 @@ BSW_FAULT_HOST = 0x10
 
 # class_ms indices of bsw_timing_t
 CLASS_NAMES = ("u8<256>", "u8<192>", "u8<128>", "u8<96>", "u8<64>", "u8<48>", "u8<32>", "u8<16>",
-               "i16<256>", "i16<128>", "i16<64>", "i16<32>", "warp16", "warp32", "rerun32")
+               "i16<256>", "i16<128>", "i16<64>", "i16<32>", "cta16", "warp16", "warp32", "rerun32")
 
 FIELDS = ("score", "qle", "tle", "gtle", "gscore", "max_off")
 
@@ -75,7 +75,7 @@ class bsw_batch_t(ctypes.Structure):
 class bsw_plan_t(ctypes.Structure):
     _fields_ = [("short_max", ctypes.c_int32), ("u8_bounds", ctypes.c_uint32), ("i16_bounds", ctypes.c_uint32),
                 ("packed", ctypes.c_int32), ("warp_cols", ctypes.c_int32), ("inter_warps", ctypes.c_int32),
-                ("ms", ctypes.c_float)]
+                ("cta_min", ctypes.c_int32), ("ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,7 +100,7 @@ ALN_DTYPE = np.dtype([("qb", "<i4"), ("qe", "<i4"), ("rb", "<i8"), ("re", "<i8")
 
 
 class bsw_timing_t(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int32), ("class_ms", ctypes.c_float * 15)]
+    _fields_ = [("launches", ctypes.c_int32), ("class_ms", ctypes.c_float * 16)]
 
 
 _lib = None
@@ -324,8 +324,9 @@ def bsw_sa_build(codes: np.ndarray) -> np.ndarray:
     return sa
 
 
-def make_plan(short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8, inter_warps=2) -> bsw_plan_t:
-    return bsw_plan_t(short_max, u8_bounds, i16_bounds, packed, warp_cols, inter_warps, 0.0)
+def make_plan(short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8, inter_warps=2,
+              cta_min=0) -> bsw_plan_t:
+    return bsw_plan_t(short_max, u8_bounds, i16_bounds, packed, warp_cols, inter_warps, cta_min, 0.0)
 
 
 # --------------------------------------------------------------- marshalling

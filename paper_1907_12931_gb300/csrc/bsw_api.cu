@@ -184,7 +184,7 @@ struct DevBuf {
 
 // Byte offsets of the work buffers inside one allocation.
 struct WorkLayout {
-    size_t key, order, rerun, hist, cursor, cls_start, cls_count, cls_next, cells, status, slots, total;
+    size_t key, order, rec, rerun, hist, cursor, cls_start, cls_count, cls_next, cells, status, slots, total;
     int64_t slot_bytes;
 };
 
@@ -195,6 +195,7 @@ WorkLayout work_layout(int64_t n, int64_t slot_bytes, int nwarps)
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
     L.key = take(4 * (size_t)n);
     L.order = take(4 * (size_t)n);
+    L.rec = take(sizeof(PairRec) * (size_t)n);
     L.rerun = take(4 * (size_t)n);
     L.hist = take(4 * kNumBins);
     L.cursor = take(4 * kNumBins);
@@ -214,6 +215,7 @@ Work make_work(uint8_t *base, const WorkLayout &L)
     Work W;
     W.key = (int32_t *)(base + L.key);
     W.order = (int32_t *)(base + L.order);
+    W.rec = (PairRec *)(base + L.rec);
     W.rerun = (int32_t *)(base + L.rerun);
     W.hist = (uint32_t *)(base + L.hist);
     W.cursor = (uint32_t *)(base + L.cursor);
@@ -401,7 +403,7 @@ struct bsw_ctx {
 
     // execution plan (bsw_set_plan / bsw_autotune) and kernel timing
     Plan plan = default_plan();
-    bsw_plan_t pub_plan{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0.0f};
+    bsw_plan_t pub_plan{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0, 0.0f};
     ClassTimer timer{};
     bool timer_ready = false, timer_valid = false;
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
@@ -1154,7 +1156,7 @@ int bsw_set_plan(bsw_ctx_t *ctx, const bsw_plan_t *plan)
     if (plan->packed != 0 && plan->packed != 1) return BSW_EINVAL;
     Plan L;
     if (!make_plan(plan->short_max, plan->u8_bounds, plan->i16_bounds, plan->packed != 0, plan->warp_cols,
-                   plan->inter_warps, &L))
+                   plan->inter_warps, plan->cta_min, &L))
         return BSW_EINVAL;
     if (!serving_idle(ctx)) return BSW_ESTATE;
     ctx->plan = L;
@@ -1204,7 +1206,8 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         // back into it).  counts receives the pairs each class held.
         auto time_plan = [&](const bsw_plan_t &k, float *ms, int32_t *counts) -> int {
             Plan L;
-            if (!make_plan(k.short_max, k.u8_bounds, k.i16_bounds, k.packed != 0, k.warp_cols, k.inter_warps, &L))
+            if (!make_plan(k.short_max, k.u8_bounds, k.i16_bounds, k.packed != 0, k.warp_cols, k.inter_warps,
+                           k.cta_min, &L))
                 return BSW_EINVAL;
             float best = 0.0f;
             for (int r = 0; r <= reps; ++r) {
@@ -1236,7 +1239,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         // empty are not timed (their differences would be noise), and the
         // boundary of a class the sample leaves empty is removed outright (one
         // launch fewer, the same work).
-        bsw_plan_t best{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0.0f};
+        bsw_plan_t best{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0, 0.0f};
         float tbest = 0.0f;
         int32_t cnt[kNumClass + 1], cnt_best[kNumClass + 1];
         if ((rc = time_plan(best, &tbest, cnt_best)) != BSW_OK) return rc;
@@ -1260,12 +1263,18 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
                 if (cnt_best[c] > 0) return true;
             return false;
         };
-        if (any(kClsW16, kClsW16 + 1))
+        if (any(kClsCTA, kClsW16 + 1)) {
             for (int cols : {4, 16}) {
                 bsw_plan_t k = best;
                 k.warp_cols = cols;
                 if ((rc = consider(k)) != BSW_OK) return rc;
             }
+            for (int cm : {8192, 4096, 2048, 1024, 512}) {
+                bsw_plan_t k = best;
+                k.cta_min = cm;
+                if ((rc = consider(k)) != BSW_OK) return rc;
+            }
+        }
         if (can_pack && any(2, 8)) {       // the 8-bit classes of bound 128 and below
             bsw_plan_t k = best;
             k.packed = 1;
@@ -1301,7 +1310,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         }
         if ((rc = time_plan(best, &tbest, cnt)) != BSW_OK) return rc;
         make_plan(best.short_max, best.u8_bounds, best.i16_bounds, best.packed != 0, best.warp_cols, best.inter_warps,
-                  &ctx->plan);
+                  best.cta_min, &ctx->plan);
         best.ms = tbest;
         ctx->pub_plan = best;
         clear_graphs(ctx);

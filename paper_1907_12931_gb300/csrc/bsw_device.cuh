@@ -14,11 +14,13 @@ constexpr int kLongMax = BSW_MAX_QLEN;
 
 // Pair classes.  Classes 0-7: 8-bit lanes for query lengths (192,256],
 // (128,192], (96,128], (64,96], (48,64], (32,48], (16,32], [1,16]; 8-11:
-// 16-bit lanes for (128,256], (64,128], (32,64], [1,32]; 12: warp per pair with
-// 16-bit slots; 13: warp per pair with 32-bit slots; 14: the re-run list.
-constexpr int kNumClass = 14;
-constexpr int kRerun = 14;
-constexpr int kClsW16 = 12, kClsW32 = 13;
+// 16-bit lanes for (128,256], (64,128], (32,64], [1,32]; 12: block (several
+// warps) per pair, the longest queries of the 16-bit range; 13: warp per pair
+// with 16-bit-range scores; 14: warp per pair with 32-bit scores; 15: the
+// re-run list.
+constexpr int kNumClass = 15;
+constexpr int kRerun = 15;
+constexpr int kClsCTA = 12, kClsW16 = 13, kClsW32 = 14;
 
 // Counting-sort bins.  Within a class the bins run from long to short queries,
 // so the persistent kernels take the longest work first.  The 8-bit bins also
@@ -67,10 +69,19 @@ struct Batch {
     const uint8_t *q_n, *t_n;
 };
 
+// One pair's fields as the counting sort lays them out in sorted order (32
+// bytes), so the class kernels read them coalesced instead of gathering six
+// arrays at random positions.
+struct __align__(16) PairRec {
+    int64_t q_off, t_off;
+    int32_t n, m, h0, w;
+};
+
 // Device scratch for one batch launch (allocated and owned by the host runtime).
 struct Work {
     int32_t *key;              // [n] counting-sort bin, -1 = done or invalid
     int32_t *order;            // [n] pair ids grouped by bin
+    PairRec *rec;              // [n] the pairs' fields in the same order (nullable)
     uint32_t *hist;            // [kNumBins], zero between launches
     uint32_t *cursor;          // [kNumBins]
     int32_t *cls_start;        // [kNumClass + 1]

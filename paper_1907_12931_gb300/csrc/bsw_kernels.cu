@@ -220,8 +220,9 @@ __global__ void __launch_bounds__(1024) k_scan(Work W, ClassTable T)
 // per non-empty bin reserves the tile's range in that bin.
 constexpr int kScatterThreads = 512, kScatterPer = 8, kScatterTile = kScatterThreads * kScatterPer;
 
-__global__ void __launch_bounds__(kScatterThreads) k_scatter(int64_t n, Work W)
+__global__ void __launch_bounds__(kScatterThreads) k_scatter(Batch B, Params P, Work W)
 {
+    const int64_t n = B.n;
     __shared__ uint32_t cnt[kNumBins];
     __shared__ uint32_t base[kNumBins];
     for (int64_t tile = (int64_t)blockIdx.x * kScatterTile; tile < n; tile += (int64_t)gridDim.x * kScatterTile) {
@@ -240,8 +241,22 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(int64_t n, Work W)
             if (cnt[k]) base[k] = atomicAdd(&W.cursor[k], cnt[k]);
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < kScatterPer; ++u)
-            if (key[u] >= 0) W.order[base[key[u]] + rank[u]] = (int32_t)(tile + u * kScatterThreads + threadIdx.x);
+        for (int u = 0; u < kScatterPer; ++u) {
+            if (key[u] < 0) continue;
+            const int64_t p = tile + u * kScatterThreads + threadIdx.x;
+            const uint32_t pos = base[key[u]] + rank[u];
+            W.order[pos] = (int32_t)p;
+            if (W.rec) {
+                PairRec r;
+                r.q_off = B.q_off[p];
+                r.t_off = B.t_off[p];
+                r.n = B.q_len[p];
+                r.m = B.t_len[p];
+                r.h0 = B.h0[p];
+                r.w = B.w_override ? B.w_override[p] : P.w;
+                W.rec[pos] = r;
+            }
+        }
         __syncthreads();
     }
 }
@@ -335,11 +350,11 @@ __device__ __forceinline__ bool slot_nonzero(uint32_t w)
 // them carry no N code.
 template <int NMAX, bool U8, bool NM>
 __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const Params &P, const Work &W,
-                                                         int p, uint32_t *S)
+                                                         int p, const PairRec &R, uint32_t *S)
 {
     constexpr int VMAX = U8 ? 255 : 32767;
-    const int n = B.q_len[p], m = B.t_len[p], h0 = B.h0[p];
-    const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
+    const int n = R.n, m = R.m, h0 = R.h0;
+    const int wb = clip_band(P, n, R.w);
     const int e_del = P.e_del, e_ins = P.e_ins;
     const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
     if (h0 > VMAX || n > NMAX) {
@@ -349,7 +364,7 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
 
     // Eq. 3, first row: H = h0 at column 0, max(0, h0 - o_ins - c*e_ins) after.
     // 8-bit lanes: an N column gets the selector of byte 4 (the -1 profile).
-    const int64_t q_off = B.q_off[p];
+    const int64_t q_off = R.q_off;
     const uint8_t *qp = B.q + (q_off >> 2);
     for (int c = 0; c <= n; c += 4) {
         const uint32_t byte = c < n ? __ldg(qp + (c >> 2)) : 0u;
@@ -364,9 +379,9 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
         }
     }
     const uint8_t *tn = NM ? B.t_n : nullptr;
-    const int64_t t_off = B.t_off[p];
+    const int64_t t_off = R.t_off;
 
-    const uint8_t *tp = B.t + (B.t_off[p] >> 2);
+    const uint8_t *tp = B.t + (t_off >> 2);
     const uint32_t mb8 = (uint32_t)(-P.b) & 0xffu;
     const uint32_t mis4 = mb8 * 0x01010101u;
     const uint32_t flip = ((uint32_t)P.a ^ mb8) & 0xffu;
@@ -492,7 +507,18 @@ __global__ void __launch_bounds__(256) k_inter(Batch B, Params P, Work W, int cl
         g = __shfl_sync(kFull, g, 0);
         if (g >= ngroups) break;
         const int idx = (g << 5) + lane;
-        if (idx < count) cells += inter_pair<NMAX, U8, NM>(B, P, W, W.order[start + idx], S);
+        if (idx < count) {
+            const int p = W.order[start + idx];
+            PairRec R;
+            if (W.rec) {
+                R = W.rec[start + idx];
+            } else {
+                R.q_off = B.q_off[p]; R.t_off = B.t_off[p];
+                R.n = B.q_len[p]; R.m = B.t_len[p]; R.h0 = B.h0[p];
+                R.w = B.w_override ? B.w_override[p] : P.w;
+            }
+            cells += inter_pair<NMAX, U8, NM>(B, P, W, p, R, S);
+        }
         __syncwarp();
     }
     for (int d = 16; d > 0; d >>= 1) cells += __shfl_xor_sync(kFull, cells, d);
@@ -1010,12 +1036,12 @@ __device__ unsigned long long warp_pair(const Batch &B, const Params &P, int p, 
     return ncell;
 }
 
-// Ring position of column j with one padding word per C: lane L of a full
-// chunk reads column cb + C*L + k (cb a multiple of C), at word
-// const + (C+1)*L + k, and C+1 is odd, so the 32 lanes hit 32 banks.  (The
-// smaller last chunks of a row, C/2 or C/4 columns per lane, see up to 2-way
-// conflicts; one pad per 32 instead would need 32-aligned chunk starts and,
-// for w' = 500, rings of twice the size.)
+// Ring position (in 8-byte slots) of column j with one padding slot per C:
+// lane L of a full chunk reads column cb + C*L + k (cb a multiple of C), at
+// slot const + (C+1)*L + k.  A warp's 64-bit accesses are served a half-warp
+// at a time; 2(C+1) words apart, the 16 lanes of a half cover 32 distinct
+// banks.  (The smaller last chunks of a row, C/2 or C/4 columns per lane,
+// see up to 2-way conflicts.)
 template <int C>
 __device__ __forceinline__ int ring_pos(int j, int mask)
 {
@@ -1035,22 +1061,31 @@ __host__ __device__ constexpr int chunk_cover(int s)
                 : (s - 32 * C * ((s - 1) / (32 * C))) > 8 * C ? 16 * C : 8 * C);
 }
 
+// The ring kernels keep one int2 {H(i-1, j-1), E(i, j)} per column, so a
+// cell costs one 64-bit load and one 64-bit store of shared memory.
+//
 // One row chunk of the ring kernel: lane L owns the CC columns
-// [cb + CC*L, cb + CC*L + CC) of rings laid out for C columns per lane
-// (CC = C, C/2 or C/4: the lane's columns stay consecutive ring words).  RH
-// holds H(i-1, j-1) and RE holds E(i, j) of column j, one 32-bit word each,
-// so loads and stores need no packing.  Columns outside the band read empty
-// slots (ring invariant below), so no load is masked.  F entering the chunk
-// is carry_f; the F scan across lanes is a prefix max of
-// floc + (lane+1)*CC*e_ins.  LAST: the chunk holding column hi - 1; it stores
-// columns up to and including hi (column hi's slot gets H(i, hi-1) with E = 0,
-// the row-end value) and none beyond.  SYM: o_del = o_ins and e_del = e_ins,
-// so E and F open from the same M - o - e.
-template <int C, int CC, bool LAST, bool SYM>
-__device__ __forceinline__ void ring_chunk(const uint8_t *qp, int n, uint32_t tmask, int *RH, int *RE, int mask,
-                                           int cb, int hi, int a, int mb, int e_del, int e_ins, int oe_del,
-                                           int oe_ins, int lane, int &carry_f, int &carry_h, int &key_l)
+// [cb + CC*L, cb + CC*L + CC) of a ring laid out for C columns per lane (CC
+// = C, C/2 or C/4: the lane's columns stay consecutive ring slots).  Columns
+// outside the band read empty slots (ring invariant below), so no load is
+// masked.  Each lane loads its slots, computes M and the E of the next row
+// for every column, and a local F pass; the F entering each lane is a prefix
+// max over the warp of floc + (lane+1)*CC*e_ins (F(i,j) = max(0, max_{k<j}
+// (M_k - o - e - (j-1-k)e)), Eq. 2 with the affine gap of Eq. 3); then H and
+// the stores.  Slot j receives H(i, j-1) (the next row's diagonal) and
+// E(i+1, j); the lane stores slot j0 + k once H of column j0 + k - 1 is
+// known, and slot j0 last, with H of the previous lane's last column.  F
+// entering the chunk is carry_f, H of the column before it carry_h.  LAST:
+// the chunk holding column hi - 1; it stores columns up to and including hi
+// (slot hi gets H(i, hi-1) with E = 0, the row-end value) and none beyond.
+// SYM: o_del = o_ins and e_del = e_ins (E and F open from one M - o - e).
+// E1: e_del = e_ins = 1 (the F offsets are immediates).
+template <int C, int CC, bool LAST, bool SYM, bool E1>
+__device__ __forceinline__ void ring_chunk(const uint8_t *qp, int n, uint32_t tmask, int2 *RG, int mask, int cb,
+                                           int hi, int a, int mb, int e_del, int e_ins, int oe_del, int oe_ins,
+                                           int lane, int &carry_f, int &carry_h, int &key_l)
 {
+    const int ed = E1 ? 1 : e_del, ei = E1 ? 1 : e_ins;
     const int j0 = cb + lane * CC;
     uint32_t qbits = 0;
     if (CC >= 4) {
@@ -1060,23 +1095,20 @@ __device__ __forceinline__ void ring_chunk(const uint8_t *qp, int n, uint32_t tm
     } else if (j0 < n) {
         qbits = (uint32_t)__ldg(qp + (j0 >> 2)) >> (2 * (j0 & 3));
     }
-    const uint32_t x = qbits ^ tmask;
-    const uint32_t mism = (x | (x >> 1)) & 0x55555555u;   // bit 2k: query base != t_i
-    const int pos = ring_pos<C>(j0, mask);
-    int *rh = RH + pos, *re = RE + pos;
-    int M[CC], T[CC], Ev[CC], Fl[CC], H[CC];
+    const uint32_t x = qbits ^ tmask;                       // field k is zero where query base j0 + k is t_i
+    int2 *rg = RG + ring_pos<C>(j0, mask);
+    int M[CC], Ev[CC], Fl[CC];
     int floc = 0;
 #pragma unroll
     for (int k = 0; k < CC; ++k) {
-        const int d = rh[k];                                // H(i-1, j-1)
-        Ev[k] = re[k];                                      // E(i, j)
-        const int sc = (mism >> (2 * k)) & 1u ? mb : a;
-        M[k] = __viaddmin_s32(d, sc, d << 16);              // d > 0 ? d + sc : <= 0
-        T[k] = M[k] - oe_ins;
+        const int2 v = rg[k];                               // H(i-1, j-1), E(i, j)
+        const int sc = (x & (3u << (2 * k))) ? mb : a;
+        M[k] = __viaddmin_s32(v.x, sc, v.x << 16);          // v.x > 0 ? v.x + sc : <= 0
+        Ev[k] = v.y;
         Fl[k] = floc;
-        floc = __viaddmax_s32_relu(floc, -e_ins, T[k]);
+        floc = __viaddmax_s32_relu(floc, -ei, M[k] - oe_ins);
     }
-    const int ce = CC * e_ins;
+    const int ce = CC * ei;
     int v = floc + (lane + 1) * ce;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) v = max(v, __shfl_up_sync(kFull, v, d));
@@ -1084,40 +1116,35 @@ __device__ __forceinline__ void ring_chunk(const uint8_t *qp, int n, uint32_t tm
     if (lane == 0) vex = carry_f;
     const int g = max(carry_f, vex) - lane * ce;            // F entering the lane's first column
     const int vall = __shfl_sync(kFull, v, 31);
-#pragma unroll
-    for (int k = 0; k < CC; ++k) {
-        const int F = __viaddmax_s32(g, -k * e_ins, Fl[k]);
-        const int h = __vimax3_s32(M[k], Ev[k], F);
-        H[k] = h;
-        key_l = max(key_l, h * 32768 + j0 + k);
-    }
-    int hin = __shfl_up_sync(kFull, H[CC - 1], 1);
-    if (lane == 0) hin = carry_h;
     const int kst = LAST ? hi - j0 : CC;                    // columns j0 + k, k <= kst, are stored
+    int kk = 0, hp = 0, e20 = 0;
 #pragma unroll
     for (int k = 0; k < CC; ++k) {
-        const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, SYM ? T[k] : M[k] - oe_del);
-        if (!LAST || k <= kst) {
-            rh[k] = hin;
-            re[k] = e2;
-        }
-        hin = H[k];
+        const int F = __viaddmax_s32(g, -k * ei, Fl[k]);
+        const int h = __vimax3_s32(M[k], Ev[k], F);
+        kk = max(kk, h * 32768 + k);                        // row key H*32768 + column: ties to the larger column
+        const int e2 = __viaddmax_s32_relu(Ev[k], -ed, M[k] - (SYM ? oe_ins : oe_del));   // E(i+1, j)
+        if (k == 0) e20 = e2;
+        else if (!LAST || k <= kst) rg[k] = make_int2(hp, e2);
+        hp = h;
     }
+    int hin = __shfl_up_sync(kFull, hp, 1);
+    if (lane == 0) hin = carry_h;
+    if (!LAST || kst >= 0) rg[0] = make_int2(hin, e20);
+    key_l = max(key_l, kk + j0);
     carry_f = max(carry_f, vall) - 32 * ce;
     if (!LAST) {
-        carry_h = __shfl_sync(kFull, H[CC - 1], 31);
+        carry_h = __shfl_sync(kFull, hp, 31);
     } else if (hi == cb + 32 * CC && lane == 31) {
-        const int ph = ring_pos<C>(hi, mask);
-        RH[ph] = H[CC - 1];
-        RE[ph] = 0;
+        RG[ring_pos<C>(hi, mask)] = make_int2(hp, 0);
     }
 }
 
-// The warp-per-pair extension with its row in shared-memory rings (scores
+// The warp-per-pair extension with its row in a shared-memory ring (scores
 // up to 32767, for the row key H * 32768 + column), C columns per lane (4, 8
-// or 16).  Each row runs
-// chunks of 32*C columns and a last chunk of 32*C, 16*C or 8*C columns,
-// whichever is the smallest that holds the rest of the band.
+// or 16).  Each row runs chunks of 32*C columns and a last chunk of 32*C,
+// 16*C or 8*C columns, whichever is the smallest that holds the rest of the
+// band.
 //
 // Ring invariant: at the start of a row every slot outside [lo, hi) is zero
 // (H = E = 0) unless the band will initialise it on first visit.  It holds
@@ -1131,9 +1158,8 @@ __device__ __forceinline__ void ring_chunk(const uint8_t *qp, int n, uint32_t tm
 // nothing.  The ring is sized by ring_slots, so that no out-of-band lane
 // (at most chunk_cover(2w' + C) columns from the first chunk's start) reads a
 // slot of a band column through the ring's wrap.
-template <int C, bool SYM>
-__device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, int p, int *RH, int *RE,
-                                               int mask)
+template <int C, bool SYM, bool E1>
+__device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, int p, int2 *RG, int mask)
 {
     static_assert(C == 4 || C == 8 || C == 16, "columns per lane");
     const int lane = threadIdx.x & 31;
@@ -1145,10 +1171,7 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
     const uint8_t *qp = B.q + (B.q_off[p] >> 2);
     const uint8_t *tp = B.t + (B.t_off[p] >> 2);
     const int words = mask + 1 + (mask + 1) / C;
-    for (int w = lane; w < words; w += 32) {
-        RH[w] = 0;
-        RE[w] = 0;
-    }
+    for (int w = lane; w < words; w += 32) RG[w] = make_int2(0, 0);
     int hw = -1, lo = 0, hi = n;
     int best = h0, bi = -1, bj = -1, gbest = -1, gi = -1, moff = 0;
     unsigned long long ncell = 0;
@@ -1156,41 +1179,35 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         const int tb = (__ldg(tp + (i >> 2)) >> (2 * (i & 3))) & 3;
         const uint32_t tmask = (uint32_t)tb * 0x55555555u;    // t_i in each 2-bit field
         const int lo_new = max(lo, i - wb);
-        for (int c = lo + lane; c < lo_new; c += 32) {           // left the band
-            RH[ring_pos<C>(c, mask)] = 0;
-            RE[ring_pos<C>(c, mask)] = 0;
-        }
+        for (int c = lo + lane; c < lo_new; c += 32)             // left the band
+            RG[ring_pos<C>(c, mask)] = make_int2(0, 0);
         lo = lo_new;
         hi = min(min(hi, i + wb + 1), n);
         for (int c = hw + 1 + lane; c <= hi - 1; c += 32)     // first visit of columns (hw, hi-1]
-            RH[ring_pos<C>(c, mask)] = c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins);
+            RG[ring_pos<C>(c, mask)] = make_int2(c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins), 0);
         hw = max(hw, hi - 1);
-        if (lane == 0) {
-            RH[ring_pos<C>(hi, mask)] = 0;
-            RE[ring_pos<C>(hi, mask)] = 0;
-        }
+        if (lane == 0) RG[ring_pos<C>(hi, mask)] = make_int2(0, 0);
         __syncwarp();
         const int hl0 = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
         int carry_f = 0, carry_h = hl0, key_l = 0;
         int cb = (lo / C) * C;
         if (lo < hi) {
             while (hi - cb > 32 * C) {
-                ring_chunk<C, C, false, SYM>(qp, n, tmask, RH, RE, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
-                                          lane, carry_f, carry_h, key_l);
+                ring_chunk<C, C, false, SYM, E1>(qp, n, tmask, RG, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                                                 lane, carry_f, carry_h, key_l);
                 cb += 32 * C;
             }
             if (hi - cb > 16 * C)
-                ring_chunk<C, C, true, SYM>(qp, n, tmask, RH, RE, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
-                                         lane, carry_f, carry_h, key_l);
+                ring_chunk<C, C, true, SYM, E1>(qp, n, tmask, RG, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
+                                                lane, carry_f, carry_h, key_l);
             else if (hi - cb > 8 * C)
-                ring_chunk<C, C / 2, true, SYM>(qp, n, tmask, RH, RE, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
-                                             lane, carry_f, carry_h, key_l);
+                ring_chunk<C, C / 2, true, SYM, E1>(qp, n, tmask, RG, mask, cb, hi, a, mb, e_del, e_ins, oe_del,
+                                                    oe_ins, lane, carry_f, carry_h, key_l);
             else
-                ring_chunk<C, C / 4, true, SYM>(qp, n, tmask, RH, RE, mask, cb, hi, a, mb, e_del, e_ins, oe_del, oe_ins,
-                                             lane, carry_f, carry_h, key_l);
+                ring_chunk<C, C / 4, true, SYM, E1>(qp, n, tmask, RG, mask, cb, hi, a, mb, e_del, e_ins, oe_del,
+                                                    oe_ins, lane, carry_f, carry_h, key_l);
         } else if (lane == 0) {
-            RH[ring_pos<C>(hi, mask)] = hl0;                  // empty band: the row-end value is the first column's
-            RE[ring_pos<C>(hi, mask)] = 0;
+            RG[ring_pos<C>(hi, mask)] = make_int2(hl0, 0);    // empty band: the row-end value is the first column's
         }
         __syncwarp();
         hw = max(hw, hi);                                      // slot hi holds the row-end value now
@@ -1198,7 +1215,7 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         const int rm = key >> 15, rj = key & 32767;
         if (hi > lo) ncell += (unsigned)(hi - lo);
         if (max(lo, hi) == n) {                                // H(i, n-1), now in slot hi
-            const int hl = RH[ring_pos<C>(hi, mask)];
+            const int hl = RG[ring_pos<C>(hi, mask)].x;
             if (hl >= gbest) gi = i;
             gbest = max(gbest, hl);
         }
@@ -1214,22 +1231,320 @@ __device__ unsigned long long warp_pair_ring16(const Batch &B, const Params &P, 
         int nlo = hi;                                          // rule c with ballots
         for (int base = lo; base < hi; base += 32) {
             const int j = base + lane;
-            const int v = j < hi ? RH[ring_pos<C>(j, mask)] | RE[ring_pos<C>(j, mask)] : 0;
-            const unsigned bal = __ballot_sync(kFull, v != 0);
+            int2 sv = make_int2(0, 0);
+            if (j < hi) sv = RG[ring_pos<C>(j, mask)];
+            const unsigned bal = __ballot_sync(kFull, (sv.x | sv.y) != 0);
             if (bal) { nlo = base + __ffs(bal) - 1; break; }
         }
         lo = nlo;
         int last = lo - 1;
         for (int top = hi; top >= lo; top -= 32) {
             const int j = top - lane;
-            const int v = j >= lo ? RH[ring_pos<C>(j, mask)] | RE[ring_pos<C>(j, mask)] : 0;
-            const unsigned bal = __ballot_sync(kFull, v != 0);
+            int2 sv = make_int2(0, 0);
+            if (j >= lo) sv = RG[ring_pos<C>(j, mask)];
+            const unsigned bal = __ballot_sync(kFull, (sv.x | sv.y) != 0);
             if (bal) { last = top - (__ffs(bal) - 1); break; }
         }
         hi = min(last + 2, n);
     }
     if (lane == 0) store_result(&B.out[p], best, bj + 1, bi + 1, gi + 1, gbest, moff);
     return ncell;
+}
+
+// The ring kernel's variant for the scoring: symmetric gap costs share
+// M - o - e, and unit extensions make the F offsets immediates.
+template <int C>
+__device__ __forceinline__ unsigned long long ring16_pair(const Batch &B, const Params &P, int p, int2 *RG, int mask)
+{
+    const bool sym = P.o_del == P.o_ins && P.e_del == P.e_ins;
+    if (sym && P.e_del == 1) return warp_pair_ring16<C, true, true>(B, P, p, RG, mask);
+    return sym ? warp_pair_ring16<C, true, false>(B, P, p, RG, mask) : warp_pair_ring16<C, false, false>(B, P, p, RG, mask);
+}
+
+// ------------------------------------------------------- one pair per block
+//
+// The longest queries run one pair per block of kCtaWarps warps.  Each row's
+// band is cut into chunks of 32*C columns (lane L of a chunk owns C
+// consecutive columns, as in the warp kernel) dealt to the warps in rounds:
+// chunk r*kCtaWarps + w is warp w's in round r.  The warps of a round
+// compute their chunks at the same time.  F crosses chunk boundaries as a
+// max-plus map: a chunk turns the F entering it into max(f, B) - 32*C*e_ins
+// at its end, where B is its lanes' scan total, so after one block barrier
+// each warp folds the maps of the chunks before it.  H of a chunk's last
+// column is the next chunk's diagonal input: within a round the chunk's lane
+// 31 writes it into the next chunk's first slot (after the barrier, so after
+// that chunk has read the slot's old value); across rounds it goes through
+// shared memory.  Row decisions are the warp kernel's, taken by every thread
+// from values the warps publish in shared memory before a second barrier:
+// each warp's row key, the row-end value, and the first and last non-zero
+// slot that the warps owning the band's ends find in their own chunks (the
+// rare row whose end chunk is all zero scans the rest after the barrier).
+// The ring and its invariant are the warp kernel's, sized for full chunks.
+constexpr int kCtaWarps = 4;
+constexpr int kCtaNone = -0x40000000;
+
+struct CtaCtl {
+    int sf[2][kCtaWarps];   // by round parity: each chunk's F map total
+    int sh[2];              // by round parity: H of the round's last column
+    int skey[kCtaWarps];    // each warp's row key (H * 32768 + column)
+    int slo, shi, shl;      // first / last non-zero slot found by the owning warps, H(i, hi-1)
+    int pair;               // the block's next pair
+};
+
+// Ring slots for band w' with full chunks of 32*C columns: a power of two, at
+// least 2w' + 3 and at least the columns of the chunks that cover 2w' + C
+// columns from a C-aligned start.
+template <int C>
+__host__ __device__ inline int cta_ring_slots(int wb)
+{
+    const int cover = 32 * C * ((2 * wb + C + 32 * C - 1) / (32 * C));
+    int need = 64;
+    while (need < 2 * wb + 3 || need < cover) need <<= 1;
+    return need;
+}
+
+template <int C, bool SYM, bool E1>
+__device__ unsigned long long cta_pair(const Batch &B, const Params &P, int p, int2 *RG, int mask, CtaCtl &S)
+{
+    constexpr int NT = kCtaWarps * 32, CW = 32 * C;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = B.q_len[p], m = B.t_len[p], h0 = B.h0[p];
+    const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
+    const int a = P.a, mb = -P.b;
+    const int e_del = E1 ? 1 : P.e_del, e_ins = E1 ? 1 : P.e_ins;
+    const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
+    const int ce = C * e_ins;
+    const uint8_t *qp = B.q + (B.q_off[p] >> 2);
+    const uint8_t *tp = B.t + (B.t_off[p] >> 2);
+    const int words = mask + 1 + (mask + 1) / C;
+    for (int w = tid; w < words; w += NT) RG[w] = make_int2(0, 0);
+    __syncthreads();
+    int hw = -1, lo = 0, hi = n;
+    int best = h0, bi = -1, bj = -1, gbest = -1, gi = -1, moff = 0;
+    unsigned long long ncell = 0;
+    for (int i = 0; i < m; ++i) {
+        const int tb = (__ldg(tp + (i >> 2)) >> (2 * (i & 3))) & 3;
+        const uint32_t tmask = (uint32_t)tb * 0x55555555u;
+        const int lo_new = max(lo, i - wb);
+        const int hi_new = min(min(hi, i + wb + 1), n);
+        const int cb0 = (lo_new / C) * C;
+        const int nch = lo_new < hi_new ? (hi_new - cb0 + CW - 1) / CW : 0;
+        // Ring set-up, each slot by the warp whose chunk reads it: the slots
+        // that left the band (left of or in chunk 0: warp 0), first visits of
+        // columns (hw, hi_new - 1] and the empty slot at hi_new.
+        if (warp == 0)
+            for (int c = lo + lane; c < lo_new; c += 32) RG[ring_pos<C>(c, mask)] = make_int2(0, 0);
+        for (int c = hw + 1 + lane; c <= hi_new - 1; c += 32)
+            if (((c - cb0) / CW) % kCtaWarps == warp)
+                RG[ring_pos<C>(c, mask)] = make_int2(c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins), 0);
+        if (lane == 0 && ((hi_new - cb0) / CW) % kCtaWarps == warp) RG[ring_pos<C>(hi_new, mask)] = make_int2(0, 0);
+        hw = max(hw, hi_new - 1);
+        __syncwarp();
+        const int hl0 = lo_new == 0 ? max(0, h0 - oe_del - i * e_del) : 0;
+        int key_l = 0, cf_round = 0;
+        for (int r = 0; r * kCtaWarps < nch; ++r) {
+            const int c = r * kCtaWarps + warp;
+            const bool active = c < nch, last = c == nch - 1;
+            const int cb = cb0 + c * CW, j0 = cb + lane * C;
+            int M[C], Ev[C], Fl[C];
+            int2 *rg = RG + ring_pos<C>(j0, mask);
+            int v = 0;
+            if (active) {
+                uint32_t qbits = 0;
+#pragma unroll
+                for (int u = 0; u < C / 4; ++u)
+                    if (j0 + 4 * u < n) qbits |= (uint32_t)__ldg(qp + (j0 >> 2) + u) << (8 * u);
+                const uint32_t x = qbits ^ tmask;
+                int floc = 0;
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const int2 sv = rg[k];
+                    const int sc = (x & (3u << (2 * k))) ? mb : a;
+                    M[k] = __viaddmin_s32(sv.x, sc, sv.x << 16);
+                    Ev[k] = sv.y;
+                    Fl[k] = floc;
+                    floc = __viaddmax_s32_relu(floc, -e_ins, M[k] - oe_ins);
+                }
+                v = floc + (lane + 1) * ce;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) v = max(v, __shfl_up_sync(kFull, v, d));
+                if (lane == 31) S.sf[r & 1][warp] = v;
+            }
+            __syncthreads();
+            // F entering this chunk (the maps of the round's chunks before
+            // it applied to the round's carry), and entering the next round
+            const int nact = min(kCtaWarps, nch - r * kCtaWarps);
+            int cf = cf_round, cf_mine = 0;
+            for (int w2 = 0; w2 < nact; ++w2) {
+                if (w2 == warp) cf_mine = cf;
+                cf = max(cf, S.sf[r & 1][w2]) - 32 * ce;
+            }
+            cf_round = cf;
+            if (active) {
+                int vex = __shfl_up_sync(kFull, v, 1);
+                if (lane == 0) vex = cf_mine;
+                const int g = max(cf_mine, vex) - lane * ce;
+                const int kst = last ? hi_new - j0 : C;
+                int kk = 0, hp = 0, e20 = 0;
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const int F = __viaddmax_s32(g, -k * e_ins, Fl[k]);
+                    const int h = __vimax3_s32(M[k], Ev[k], F);
+                    kk = max(kk, h * 32768 + k);
+                    const int e2 = __viaddmax_s32_relu(Ev[k], -e_del, M[k] - (SYM ? oe_ins : oe_del));
+                    if (k == 0) e20 = e2;
+                    else if (!last || k <= kst) rg[k] = make_int2(hp, e2);
+                    hp = h;
+                }
+                key_l = max(key_l, kk + j0);
+                const int hin = __shfl_up_sync(kFull, hp, 1);
+                if (!last || kst >= 0) {
+                    if (lane > 0) rg[0] = make_int2(hin, e20);
+                    else if (warp == 0) rg[0] = make_int2(r == 0 ? hl0 : S.sh[(r - 1) & 1], e20);
+                    else rg[0].y = e20;                 // .x comes from the previous warp's chunk
+                }
+                if (lane == 31) {
+                    if (!last && warp < kCtaWarps - 1) RG[ring_pos<C>(cb + CW, mask)].x = hp;
+                    else if (!last) S.sh[r & 1] = hp;
+                    else if (hi_new == cb + CW) RG[ring_pos<C>(hi_new, mask)] = make_int2(hp, 0);
+                }
+            }
+        }
+        // publish the warp's row key, the row-end value and the band-end scans
+        const int kw = (int)__reduce_max_sync(kFull, (unsigned)key_l);
+        if (lane == 0) S.skey[warp] = kw;
+        __syncwarp();
+        if (nch == 0) {
+            if (tid == 0) {
+                RG[ring_pos<C>(hi_new, mask)] = make_int2(hl0, 0);
+                S.shl = hl0;
+            }
+        } else {
+            const int wl = (nch - 1) % kCtaWarps;       // the warp of the chunk holding hi_new - 1
+            const int cbl = cb0 + (nch - 1) * CW;
+            if (warp == wl && lane == 0) S.shl = RG[ring_pos<C>(hi_new, mask)].x;
+            if (warp == 0) {                            // first non-zero slot in chunk 0
+                const int end = min(hi_new, cb0 + CW);
+                int f = kCtaNone;
+                for (int base = lo_new; base < end; base += 32) {
+                    const int j = base + lane;
+                    int2 sv = make_int2(0, 0);
+                    if (j < end) sv = RG[ring_pos<C>(j, mask)];
+                    const unsigned bal = __ballot_sync(kFull, (sv.x | sv.y) != 0);
+                    if (bal) { f = base + __ffs(bal) - 1; break; }
+                }
+                if (lane == 0) S.slo = f;
+            }
+            if (warp == wl) {                           // last non-zero slot in the last chunk
+                // its first slot's H comes from another warp unless it starts a round
+                const int low = max(lo_new, (nch - 1) % kCtaWarps == 0 ? cbl : cbl + 1);
+                int f = kCtaNone;
+                for (int top = hi_new; top >= low; top -= 32) {
+                    const int j = top - lane;
+                    int2 sv = make_int2(0, 0);
+                    if (j >= low) sv = RG[ring_pos<C>(j, mask)];
+                    const unsigned bal = __ballot_sync(kFull, (sv.x | sv.y) != 0);
+                    if (bal) { f = top - (__ffs(bal) - 1); break; }
+                }
+                if (lane == 0) S.shi = f;
+            }
+        }
+        __syncthreads();
+        int key = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kCtaWarps; ++w2) key = max(key, S.skey[w2]);
+        const int rm = key >> 15, rj = key & 32767;
+        const int hl = S.shl;
+        lo = lo_new;
+        hi = hi_new;
+        hw = max(hw, hi);                                  // slot hi holds the row-end value now
+        if (hi > lo) ncell += (unsigned)(hi - lo);
+        if (max(lo, hi) == n) {
+            if (hl >= gbest) gi = i;
+            gbest = max(gbest, hl);
+        }
+        if (rm == 0) break;
+        if (rm > best) {
+            best = rm; bi = i; bj = rj;
+            moff = max(moff, abs(rj - i));
+        } else if (P.zdrop > 0) {
+            const int di = i - bi, dj = rj - bj;
+            const int drop = di > dj ? best - rm - (di - dj) * e_del : best - rm - (dj - di) * e_ins;
+            if (drop > P.zdrop) break;
+        }
+        // rule c: rm > 0, so a chunk was active and both scans ran
+        int nlo = S.slo, last = S.shi;
+        const bool more = nlo == kCtaNone || last == kCtaNone;
+        if (nlo == kCtaNone) {                             // chunk 0 is all zero: scan the rest
+            nlo = hi;
+            for (int base = min(hi, cb0 + CW); base < hi; base += 32) {
+                const int j = base + lane;
+                int2 sv = make_int2(0, 0);
+                if (j < hi) sv = RG[ring_pos<C>(j, mask)];
+                const unsigned bal = __ballot_sync(kFull, (sv.x | sv.y) != 0);
+                if (bal) { nlo = base + __ffs(bal) - 1; break; }
+            }
+        }
+        if (last == kCtaNone) {                            // the last chunk is all zero: scan below it
+            const int cbl = cb0 + (nch - 1) * CW;
+            const int top0 = max(lo, (nch - 1) % kCtaWarps == 0 ? cbl : cbl + 1) - 1;
+            last = nlo - 1;
+            for (int top = top0; top >= nlo; top -= 32) {
+                const int j = top - lane;
+                int2 sv = make_int2(0, 0);
+                if (j >= nlo) sv = RG[ring_pos<C>(j, mask)];
+                const unsigned bal = __ballot_sync(kFull, (sv.x | sv.y) != 0);
+                if (bal) { last = top - (__ffs(bal) - 1); break; }
+            }
+        }
+        if (more) __syncthreads();                         // the scans read slots the next row rewrites
+        lo = nlo;
+        hi = min(last + 2, n);
+    }
+    if (tid == 0) store_result(&B.out[p], best, bj + 1, bi + 1, gi + 1, gbest, moff);
+    return ncell;
+}
+
+template <int C>
+__device__ __forceinline__ unsigned long long cta_pair_any(const Batch &B, const Params &P, int p, int2 *RG, int mask,
+                                                           CtaCtl &S)
+{
+    const bool sym = P.o_del == P.o_ins && P.e_del == P.e_ins;
+    if (sym && P.e_del == 1) return cta_pair<C, true, true>(B, P, p, RG, mask, S);
+    return sym ? cta_pair<C, true, false>(B, P, p, RG, mask, S) : cta_pair<C, false, false>(B, P, p, RG, mask, S);
+}
+
+// Persistent block-per-pair kernel over a class list.  A pair whose band
+// needs a larger ring than the block has (a per-pair band override wider
+// than the context's) goes to the 32-bit re-run list, whose warp kernel
+// takes any band.
+template <int C>
+__global__ void __launch_bounds__(kCtaWarps * 32, 5) k_cta(Batch B, Params P, Work W, int cls, int ring_log2)
+{
+    extern __shared__ int2 cta_ring[];
+    __shared__ CtaCtl S;
+    const int count = W.cls_count[cls];
+    const int32_t *list = W.order + W.cls_start[cls];
+    unsigned long long cells = 0;
+    for (;;) {
+        if (threadIdx.x == 0) S.pair = (int)atomicAdd(&W.cls_next[cls], 1u);
+        __syncthreads();
+        const int g = S.pair;
+        __syncthreads();
+        if (g >= count) break;
+        const int p = list[g];
+        const int n = B.q_len[p];
+        const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
+        const int need = cta_ring_slots<C>(wb);
+        if (ring_log2 > 0 && need <= (1 << ring_log2)) {
+            const unsigned long long c = cta_pair_any<C>(B, P, p, cta_ring, need - 1, S);
+            if (threadIdx.x == 0) cells += c;
+        } else if (threadIdx.x == 0) {
+            W.rerun[atomicAdd(&W.cls_count[kRerun], 1)] = p;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && cells) atomicAdd(W.cells, cells);
 }
 
 // Slots of the ring for band w' and C columns per lane: a power of two, at
@@ -1244,13 +1559,12 @@ __host__ __device__ inline int ring_slots(int wb)
     return need;
 }
 
-// Bytes of one warp's rings: for the 16-bit kernel two rings (H and E) of
-// 2^lg 32-bit slots plus one padding word per 32 (ring_pos), for the 32-bit
-// one 2^lg slots of 8 bytes.
+// Bytes of one warp's ring of 2^lg slots of 8 bytes; the 16-bit kernel's
+// also has one padding slot per C (ring_pos).
 template <bool S16, int C>
 __host__ __device__ constexpr size_t ring_bytes(int lg)
 {
-    return S16 ? 2 * (((size_t)4 << lg) + ((size_t)4 << lg) / C) : (size_t)8 << lg;
+    return S16 ? ((size_t)8 << lg) + ((size_t)8 << lg) / C : (size_t)8 << lg;
 }
 
 // Persistent warp-per-pair kernel over a class list (or the re-run list).
@@ -1262,7 +1576,7 @@ __host__ __device__ constexpr size_t ring_bytes(int lg)
 template <int C> constexpr int warp_threads() { return C >= 16 ? 128 : kWarpKernelThreads; }
 
 template <int C, bool S16>
-__global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
+__global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 4 : 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
 {
     extern __shared__ uint8_t ring_mem[];
     const int lane = threadIdx.x & 31;
@@ -1287,11 +1601,7 @@ __global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2) k_warp(B
             while (need < 2 * wb + 3) need <<= 1;
             if (need <= (1 << ring_log2)) {
                 if (S16) {
-                    int *RH = reinterpret_cast<int *>(ring);
-                    int *RE = RH + (ring_bytes<true, C>(ring_log2) / 8);
-                    cells += P.o_del == P.o_ins && P.e_del == P.e_ins
-                                 ? warp_pair_ring16<C, true>(B, P, p, RH, RE, need - 1)
-                                 : warp_pair_ring16<C, false>(B, P, p, RH, RE, need - 1);
+                    cells += ring16_pair<C>(B, P, p, reinterpret_cast<int2 *>(ring), need - 1);
                 } else if (B.q_n || B.t_n) {
                     cells += warp_pair<C, false, true, true>(B, P, p, ring, need - 1);
                 } else {
@@ -1356,7 +1666,6 @@ __global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2)
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     uint8_t *slots = W.slots + gw * W.slot_bytes_per_warp;
     uint8_t *ring = ring_mem + (size_t)(threadIdx.x >> 5) * ring_bytes_per_warp;
-    const bool sym = P.o_del == P.o_ins && P.e_del == P.e_ins;
     unsigned long long cells = 0;
     for (int64_t p = gw; p < B.n; p += nw) {
         const long long bound = plain_check(B, P, W, p, lane);
@@ -1367,10 +1676,7 @@ __global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2)
         if (bound <= 32767 && !has_n) {
             const int need = ring_slots<C>(wb);
             if (ring16_log2 > 0 && need <= (1 << ring16_log2)) {
-                int *RH = reinterpret_cast<int *>(ring);
-                int *RE = RH + (ring_bytes<true, C>(ring16_log2) / 8);
-                cells += sym ? warp_pair_ring16<C, true>(B, P, (int)p, RH, RE, need - 1)
-                             : warp_pair_ring16<C, false>(B, P, (int)p, RH, RE, need - 1);
+                cells += ring16_pair<C>(B, P, (int)p, reinterpret_cast<int2 *>(ring), need - 1);
                 continue;
             }
         } else {
@@ -1437,9 +1743,10 @@ __global__ void __launch_bounds__(256) k_plain_global(Batch B, Params P, Work W)
 // ------------------------------------------------------------------ launcher
 
 bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, int warp_cols, int inter_warps,
-               Plan *out)
+               int cta_min, Plan *out)
 {
     if (short_max < 64 || short_max > kShortMax) return false;
+    if (cta_min != 0 && (cta_min < 128 || cta_min > kLongMax || (cta_min & 63))) return false;
     if (warp_cols != 4 && warp_cols != 8 && warp_cols != 16) return false;
     if (inter_warps != 1 && inter_warps != 2 && inter_warps != 4) return false;
     if ((u8_mask & ~0xffu) || (i16_mask & ~0xfu)) return false;
@@ -1448,6 +1755,7 @@ bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, 
     L.packed = packed;
     L.warp_cols = warp_cols;
     L.inter_warps = inter_warps;
+    L.cta_min = cta_min;
     int32_t *b = L.cls.b;
     // A disabled class gets an empty range; its queries fall to the next
     // larger enabled class.
@@ -1455,7 +1763,10 @@ bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, 
     b[8] = kBinI16;
     for (int c = 7; c >= 1; --c)
         b[c] = ((u8_mask >> c) & 1u) ? kBinU8 + (kShortMax - kU8Nmax[c]) * kU8H0Buckets : b[c + 1];
-    b[kClsW16] = kBinW16;
+    // the 16-bit warp bins run from long to short queries (bin kBinW16 + 639
+    // - n / 64): the block-per-pair class takes those of n >= cta_min
+    b[kClsCTA] = kBinW16;
+    b[kClsW16] = kBinW16 + (cta_min ? 640 - (cta_min >> 6) : 0);
     for (int c = 11; c >= 9; --c) b[c] = ((i16_mask >> (c - 8)) & 1u) ? kBinI16 + kShortMax - kI16Nmax[c - 8] : b[c + 1];
     b[kClsW32] = kBinW32;
     b[kNumClass] = kNumBins;
@@ -1466,7 +1777,7 @@ bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, 
 Plan default_plan()
 {
     Plan L;
-    make_plan(kShortMax, 0xffu, 0xfu, false, 8, 2, &L);
+    make_plan(kShortMax, 0xffu, 0xfu, false, 8, 2, 0, &L);
     return L;
 }
 
@@ -1585,6 +1896,26 @@ int ring_log2_for(const Params &P)
     return per_block <= kRingSmemMax ? lg : 0;
 }
 
+// Ring of the block-per-pair kernel for the context's band (0: none fits).
+constexpr int kCtaCols = 8;
+int g_cta_blocks = 1;   // resident blocks per SM, set by prepare_kernels
+
+int cta_ring_log2(const Params &P)
+{
+    int lg = 6;
+    const int need = cta_ring_slots<kCtaCols>(P.w);
+    while ((1 << lg) < need && lg < 16) ++lg;
+    return ring_bytes<true, kCtaCols>(lg) <= kRingSmemMax ? lg : 0;
+}
+
+cudaError_t launch_cta(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms)
+{
+    const int lg = cta_ring_log2(P);
+    const size_t smem = lg ? ring_bytes<true, kCtaCols>(lg) : 0;
+    k_cta<kCtaCols><<<sms * g_cta_blocks, kCtaWarps * 32, smem, st>>>(B, P, W, cls, lg);
+    return cudaGetLastError();
+}
+
 template <int C, bool S16>
 cudaError_t launch_warp(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int blocks)
 {
@@ -1628,19 +1959,27 @@ cudaError_t cls_w32(const Batch &B, const Params &P, const Work &W, int c, cudaS
     return launch_warp<8, false>(B, P, W, c, st, wblocks);
 }
 
+cudaError_t cls_cta(const Batch &B, const Params &P, const Work &W, int c, cudaStream_t st, int sms, int,
+                    const Plan &)
+{
+    return launch_cta(B, P, W, c, st, sms);
+}
+
 constexpr ClassLaunch kClassLaunch[kNumClass + 1] = {
     cls_u8<256>, cls_u8<192>, cls_u8<128>, cls_u8<96>, cls_u8<64>, cls_u8<48>, cls_u8<32>, cls_u8<16>,
-    cls_i16<256>, cls_i16<128>, cls_i16<64>, cls_i16<32>, cls_w16, cls_w32, cls_w32};
+    cls_i16<256>, cls_i16<128>, cls_i16<64>, cls_i16<32>, cls_cta, cls_w16, cls_w32, cls_w32};
 
 // Launch order of the classes in the forked path and the side stream of each:
-// the long 8-bit classes first, each stream ending with shorter work.
-constexpr int kForkOrder[kNumClass] = {0, 1, 2, 3, 4, 5, 6, 7, kClsW16, kClsW32, 8, 9, 10, 11};
-constexpr int kClassStream[kNumClass] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2};
+// the longest work first (block-per-pair pairs, then the long 8-bit
+// classes), each stream ending with shorter work.
+constexpr int kForkOrder[kNumClass] = {kClsCTA, 0, 1, 2, 3, 4, 5, 6, 7, kClsW16, kClsW32, 8, 9, 10, 11};
+constexpr int kClassStream[kNumClass] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 2, 2, 0, 2, 2};
 
 // Whether class c can hold pairs under the plan and the batch flags (classes
 // that cannot are not launched).
 bool class_live(int c, const Plan &L, uint32_t flags)
 {
+    if (c == kClsCTA) return L.cls.b[kClsCTA] != L.cls.b[kClsW16];
     if (c >= kClsW16) return true;
     if (flags & BSW_FORCE_I32) return false;
     const bool u8 = c < 8;
@@ -1673,7 +2012,7 @@ cudaError_t launch_prepass(const Batch &B, const Params &P, const Work &W, cudaS
     k_scan<<<1, 1024, 0, st>>>(W, L.cls);
     const int sblocks = (int)((B.n + kScatterTile - 1) / kScatterTile < (int64_t)sms * 2
                                   ? (B.n + kScatterTile - 1) / kScatterTile : (int64_t)sms * 2);
-    k_scatter<<<sblocks, kScatterThreads, 0, st>>>(B.n, W);
+    k_scatter<<<sblocks, kScatterThreads, 0, st>>>(B, P, W);
     return cudaGetLastError();
 }
 
@@ -1710,6 +2049,18 @@ cudaError_t prepare_kernels(int sms)
         return e;
     if ((e = cudaFuncSetAttribute(k_plain<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_cta<kCtaCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) !=
+        cudaSuccess)
+        return e;
+    {
+        // resident blocks for the ring of a w = 500 band (the long-query workload's)
+        const int nb_smem = (int)ring_bytes<true, kCtaCols>(11);
+        int nb = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cta<kCtaCols>, kCtaWarps * 32, nb_smem)) !=
+            cudaSuccess)
+            return e;
+        g_cta_blocks = nb > 0 ? nb : 1;
+    }
     if ((e = cudaFuncSetAttribute(k_plain<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_plain<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)

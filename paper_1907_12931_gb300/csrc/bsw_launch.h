@@ -34,13 +34,15 @@ struct Plan {
     bool packed;
     int32_t warp_cols;     // 4, 8 or 16
     int32_t inter_warps;   // 1, 2 or 4
+    int32_t cta_min;       // queries of at least this many bases in the 16-bit range run one pair per block (0: none)
 };
 
 // u8_mask bit k enables kU8Nmax[k] as a class (bit 0 is always on), i16_mask
 // bit k enables kI16Nmax[k]; a query goes to the smallest enabled class that
-// holds it.  Returns false for values out of range.
+// holds it.  cta_min: 0, or a multiple of 64 in [128, kLongMax].  Returns
+// false for values out of range.
 bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, int warp_cols, int inter_warps,
-               Plan *out);
+               int cta_min, Plan *out);
 Plan default_plan();
 
 // Whether the scoring lets the packed two-pairs-per-thread kernel run.

@@ -115,6 +115,7 @@ extern "C" int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int3
     Work W;
     W.key = (int32_t *)(base + kOffKey);
     W.order = (int32_t *)(base + kOffOrder);
+    W.rec = nullptr;   // the class kernels gather the pairs' fields from the batch
     W.rerun = (int32_t *)(base + kOffRerun);
     W.hist = (uint32_t *)(base + kOffHist);
     W.cursor = (uint32_t *)(base + kOffCursor);

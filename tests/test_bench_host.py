@@ -9,9 +9,9 @@ from paper_1907_12931_gb300 import workload as W
 
 
 class _Plan:
-    def __init__(self, short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8):
+    def __init__(self, short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8, cta_min=0):
         self.short_max, self.u8_bounds, self.i16_bounds = short_max, u8_bounds, i16_bounds
-        self.packed, self.warp_cols = packed, warp_cols
+        self.packed, self.warp_cols, self.cta_min = packed, warp_cols, cta_min
 
 
 def _class_one(n, m, h0, match, plan):
@@ -20,14 +20,16 @@ def _class_one(n, m, h0, match, plan):
         return -1
     bound = h0 + match * min(n, m)
     if n > plan.short_max:
-        return 12 if bound <= 32767 else 13
+        if bound > 32767:
+            return 14
+        return 12 if plan.cta_min and n >= plan.cta_min else 13
     if bound <= 255:
         kept = [k for k in range(8) if k == 0 or (plan.u8_bounds >> k) & 1]
         return max((k for k in kept if bench.U8_NMAX[k] >= n), key=lambda k: k)
     if bound <= 32767:
         kept = [k for k in range(4) if k == 0 or (plan.i16_bounds >> k) & 1]
         return 8 + max(k for k in kept if bench.I16_NMAX[k] >= n)
-    return 13
+    return 14
 
 
 def test_class_of_matches_definition():
@@ -38,7 +40,8 @@ def test_class_of_matches_definition():
     h0 = rng.integers(0, 300, n.shape[0])
     h0[::11] = 40000
     plans = [_Plan(), _Plan(short_max=64), _Plan(short_max=128, u8_bounds=0x5, i16_bounds=0x1),
-             _Plan(u8_bounds=0x0, i16_bounds=0x0), _Plan(short_max=192, u8_bounds=0xa3, i16_bounds=0xb)]
+             _Plan(u8_bounds=0x0, i16_bounds=0x0), _Plan(short_max=192, u8_bounds=0xa3, i16_bounds=0xb),
+             _Plan(short_max=96, cta_min=1024), _Plan(cta_min=128)]
     for plan, match in itertools.product(plans, (1, 2)):
         got = bench.class_of(n, m, h0, match, plan)
         want = [_class_one(int(a), int(b), int(c), match, plan) for a, b, c in zip(n, m, h0)]
@@ -51,8 +54,9 @@ def test_class_kernel_names():
     assert bench.class_kernel(3, _Plan(packed=1), sc) == "k_inter2<128>"
     assert bench.class_kernel(0, _Plan(packed=1), sc) == "k_inter<256,u8>"
     assert bench.class_kernel(9, _Plan(), sc) == "k_inter<128,i16>"
-    assert bench.class_kernel(12, _Plan(warp_cols=16), sc) == "k_warp<16,s16>"
-    assert bench.class_kernel(13, _Plan(), sc) == "k_warp<8,s32>"
+    assert bench.class_kernel(12, _Plan(cta_min=1024), sc) == "k_cta<8,s16>"
+    assert bench.class_kernel(13, _Plan(warp_cols=16), sc) == "k_warp<16,s16>"
+    assert bench.class_kernel(14, _Plan(), sc) == "k_warp<8,s32>"
     # large gap costs: the packed kernel does not apply
     assert bench.class_kernel(3, _Plan(packed=1), W.Scoring(1, 200, 100, 1, 100, 1)) == "k_inter<96,u8>"
 

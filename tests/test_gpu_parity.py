@@ -46,10 +46,10 @@ def assert_same(got, ref, what):
                              % (what, bad.size, ref.shape[0], k, got[k].tolist(), ref[k].tolist()))
 
 
-def run(bsw, wl, flags=0, device=False, budget=16 << 30, w_override=None, params=None, warp_cols=None):
+def run(bsw, wl, flags=0, device=False, budget=16 << 30, w_override=None, params=None, warp_cols=None, cta_min=0):
     with bsw.Context(params or wl.params, budget) as ctx:
-        if warp_cols is not None:
-            ctx.set_plan(bsw.make_plan(warp_cols=warp_cols))
+        if warp_cols is not None or cta_min:
+            ctx.set_plan(bsw.make_plan(warp_cols=warp_cols or 8, cta_min=cta_min))
         hb = bsw.HostBatch(wl, w_override=w_override)
         if not device:
             return ctx.extend_host(hb, flags)
@@ -360,6 +360,9 @@ def test_maximum_query_length(bsw):
         got, gc = run(bsw, wl, flag_of(bsw, flags), params=params)
         assert_same(got, ref, "max qlen/%s" % flags)
         assert gc == int(cells.sum())
+    got, gc = run(bsw, wl, 0, params=params, cta_min=128)             # one pair per block
+    assert_same(got, ref, "max qlen/block per pair")
+    assert gc == int(cells.sum())
     too = W.from_lists([t[:L + 1]], [t], [40], params=params, align=4)
     with bsw.Context(params) as ctx:
         with pytest.raises(bsw.BswError) as e:

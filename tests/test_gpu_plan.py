@@ -23,6 +23,9 @@ PLANS = [
     {"u8_bounds": 0x55, "i16_bounds": 0x5, "inter_warps": 1},
     {"packed": 1, "inter_warps": 4},
     {"short_max": 128, "packed": 1, "u8_bounds": 0x0, "warp_cols": 16},
+    {"short_max": 64, "cta_min": 128},
+    {"short_max": 96, "warp_cols": 16, "cta_min": 1024},
+    {"cta_min": 4096, "warp_cols": 4},
 ]
 
 
@@ -87,11 +90,12 @@ def test_forced_lanes_under_plan(bsw, flag):
 def test_set_plan_rejects_bad_fields(bsw):
     wl, _, _ = workload_and_oracle("plain10k")
     bad = [{"short_max": 63}, {"short_max": 257}, {"warp_cols": 5}, {"warp_cols": 32}, {"inter_warps": 3},
-           {"packed": 2}, {"u8_bounds": 0x100}, {"i16_bounds": 0x10}]
+           {"packed": 2}, {"u8_bounds": 0x100}, {"i16_bounds": 0x10}, {"cta_min": 64}, {"cta_min": 1000},
+           {"cta_min": 32832}, {"cta_min": -64}]
     with bsw.Context(wl.params) as ctx:
         before = ctx.get_plan().as_dict()
         assert before == {"short_max": 256, "u8_bounds": 0xff, "i16_bounds": 0xf, "packed": 0, "warp_cols": 8,
-                          "inter_warps": 2, "ms": 0.0}
+                          "inter_warps": 2, "cta_min": 0, "ms": 0.0}
         for b in bad:
             with pytest.raises(bsw.BswError) as ei:
                 ctx.set_plan(bsw.make_plan(**b))
@@ -168,8 +172,9 @@ def test_kernel_times(bsw):
         ctx.sync()
         torch.cuda.synchronize()
         assert_same(db.out.cpu().numpy(), ref, "timed launch")
-        assert launches == 18                              # 3 bucketing + 14 classes + re-run
-        assert ms[3] > 0 and ms[14] > 0                    # u8<96> carries most cells; re-run always launches
+        assert launches == 18                              # 3 bucketing + 14 classes (no block class) + re-run
+        assert ms[3] > 0 and ms[15] > 0                    # u8<96> carries most cells; re-run always launches
+        assert ms[12] == 0                                 # cta_min 0: no block-per-pair launch
         assert all(t >= 0 for t in ms)
         # a plan with fewer classes launches fewer kernels
         ctx.set_plan(bsw.make_plan(short_max=128, u8_bounds=0x5, i16_bounds=0x1))
@@ -185,8 +190,8 @@ def test_kernel_times(bsw):
         assert_same(db.out.cpu().numpy(), ref, "timed launch, reduced plan")
 
 
-@pytest.mark.parametrize("cols", [4, 8, 16])
-def test_ring_wrap_band_edges(bsw, cols):
+@pytest.mark.parametrize("cols,cta", [(4, 0), (8, 0), (16, 0), (8, 128)])
+def test_ring_wrap_band_edges(bsw, cols, cta):
     """Band widths just under a power of two with full-width bands (near
     identical sequences): the chunks' out-of-band lanes reach furthest past the
     band there, and must never read a band column through the ring's wrap."""
@@ -203,6 +208,62 @@ def test_ring_wrap_band_edges(bsw, cols):
     for w in (126, 127, 254, 255, 500, 508, 510, 511):
         wl.params = W.Params(W.Scoring(), w=w, zdrop=0, end_bonus=5)
         ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH)
-        got, gc = run_plan(bsw, wl, {"short_max": 64, "warp_cols": cols}, device=True)
-        assert_same(got, ref, "w=%d cols=%d" % (w, cols))
+        got, gc = run_plan(bsw, wl, {"short_max": 64, "warp_cols": cols, "cta_min": cta}, device=True)
+        assert_same(got, ref, "w=%d cols=%d cta_min=%d" % (w, cols, cta))
         assert gc == int(cells.sum())
+
+
+@pytest.mark.parametrize("w", [3, 40, 100, 127, 128, 129, 383, 384, 500, 1000, 2100])
+def test_block_per_pair_band_widths(bsw, w):
+    """One pair per block over band widths that give one chunk, several chunks
+    in one round, and several rounds (4 warps x 256 columns per round), with
+    z-drop on, for long near-copies and for queries with indels."""
+    rng = np.random.default_rng(1000 + w)
+    qs, ts, hs = [], [], []
+    for n in (130, 300, 900, 2500, 5000):
+        for err in (0.0, 0.02, 0.12):
+            ref = rng.integers(0, 4, n + w + 600).astype(np.uint8)
+            q = list(ref[:n])
+            k = 0
+            out = []
+            while k < len(q):                                  # substitutions and 1-3 bp indels
+                u = rng.random()
+                if u < err / 2:
+                    out.append(int((q[k] + 1 + rng.integers(0, 3)) % 4)); k += 1
+                elif u < 3 * err / 4:
+                    k += int(rng.integers(1, 4))
+                elif u < err:
+                    out.extend(int(x) for x in rng.integers(0, 4, int(rng.integers(1, 4)))); 
+                else:
+                    out.append(int(q[k])); k += 1
+            qs.append(np.array(out, np.uint8)); ts.append(ref[: len(out) + w]); hs.append(int(rng.integers(19, 61)))
+    wl = W.from_lists(qs, ts, hs, align=4)
+    for zd in (100, 0):
+        wl.params = W.Params(W.Scoring(), w=w, zdrop=zd, end_bonus=5)
+        ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH)
+        got, gc = run_plan(bsw, wl, {"short_max": 64, "cta_min": 128}, device=True)
+        assert_same(got, ref, "block per pair w=%d zdrop=%d" % (w, zd))
+        assert gc == int(cells.sum())
+
+
+def test_block_per_pair_other_scorings(bsw):
+    """Asymmetric gap costs and extensions above 1 take the kernel's general
+    variants (no shared M - o - e, no immediate offsets)."""
+    wl = W.make("long10k", n_pairs=600)
+    for sc in ((1, 4, 6, 1, 6, 1), (2, 3, 5, 2, 4, 1), (1, 6, 1, 1, 1, 1), (5, 9, 3, 3, 8, 2), (1, 4, 6, 2, 6, 2)):
+        wl.params = W.Params(W.Scoring(*sc), w=300, zdrop=200, end_bonus=3)
+        ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH)
+        got, gc = run_plan(bsw, wl, {"short_max": 96, "cta_min": 512}, device=True)
+        assert_same(got, ref, "block per pair scoring %s" % (sc,))
+        assert gc == int(cells.sum())
+
+
+def test_block_per_pair_band_override(bsw):
+    """Per-pair bands wider than the context's ring go to the re-run list."""
+    wl = W.make("long10k", n_pairs=500)
+    ws = np.where(np.arange(wl.n_pairs) % 3 == 0, 1500, np.where(np.arange(wl.n_pairs) % 3 == 1, 50, 500))
+    ws = ws.astype(np.int32)
+    ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH, w_override=ws)
+    got, gc = run_plan(bsw, wl, {"short_max": 96, "cta_min": 256}, w_override=ws)
+    assert_same(got, ref, "block per pair, band overrides")
+    assert gc == int(cells.sum())
