@@ -1576,7 +1576,7 @@ __host__ __device__ constexpr size_t ring_bytes(int lg)
 template <int C> constexpr int warp_threads() { return C >= 16 ? 128 : kWarpKernelThreads; }
 
 template <int C, bool S16>
-__global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 4 : 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
+__global__ void __launch_bounds__(C >= 16 ? 128 : 256, C >= 16 ? 3 : 2) k_warp(Batch B, Params P, Work W, int cls, int ring_log2)
 {
     extern __shared__ uint8_t ring_mem[];
     const int lane = threadIdx.x & 31;
