@@ -117,8 +117,8 @@ typedef struct {
  * included (BWA-MEM's rule; the paper's alphabet has four bases), and the
  * base's 2-bit code is ignored.  Pairs with an N run in the 8-bit per-thread
  * kernels when their scores fit, else in the 32-bit warp-per-pair kernel.
- * bsw_pack_2bit_n packs text with N.  The serving calls (bsw_stream_submit)
- * take no N bitmaps.
+ * bsw_pack_2bit_n packs text with N.  bsw_stream_submit takes them too (and
+ * copies them with BSW_COPY_INPUTS).
  */
 
 /*
@@ -171,7 +171,9 @@ int bsw_sync(bsw_ctx_t *ctx, void *cuda_stream);
  * (flags: 0 or BSW_COPY_INPUTS; the other flags are rejected).  A server thread admits
  * queued batches as stream slots and device memory within the budget free up,
  * merges small ones into one launch, and overlaps launches on several streams
- * (continuous batching).  Inputs and out must stay valid until poll returns
+ * (continuous batching).  A batch may carry N bitmaps (q_n, t_n).  An
+ * admission that finds the budget held by busy lanes waits for one of them to
+ * finish.  Inputs and out must stay valid until poll returns
  * BSW_OK for the ticket, unless BSW_COPY_INPUTS is set (inputs are copied
  * before submit returns; out must still stay valid).
  * Errors: BSW_EINVAL, BSW_EBUDGET (the batch alone exceeds the budget),
@@ -181,6 +183,30 @@ int bsw_sync(bsw_ctx_t *ctx, void *cuda_stream);
  */
 int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *batch, bsw_result_t *out,
                       uint64_t *ticket);
+
+/*
+ * Serving counters since the context was made or last reset (reset != 0
+ * zeroes them after reading).  A launch is one merged batch on one
+ * execution lane; its device interval runs from the event recorded before its
+ * host-to-device copy to the event after its results are copied back (CUDA
+ * events on the lane's stream), kept for the latest 65536 launches.
+ *   requests        requests finished (any status)
+ *   launches        launches finished
+ *   merged          requests that shared their launch with another request
+ *   budget_waits    admissions put back to wait for device memory that busy
+ *                   lanes held (the budget, not a failure)
+ *   busy_ms         the sum of the launches' intervals
+ *   union_ms        the time at least one launch was on the device (busy_ms /
+ *                   union_ms > 1: launches overlapped)
+ *   max_concurrent  the most launches on the device at one moment
+ * Errors: BSW_EINVAL (null argument).
+ */
+typedef struct {
+    int64_t requests, launches, merged, budget_waits;
+    double busy_ms, union_ms;
+    int32_t max_concurrent;
+} bsw_serve_stats_t;
+int bsw_stream_stats(bsw_ctx_t *ctx, bsw_serve_stats_t *out, int32_t reset);
 
 /*
  * Wait up to timeout_us microseconds (0: just check; < 0: wait without limit)
@@ -246,6 +272,24 @@ int bsw_pack_2bit_n(const uint8_t *in, int64_t n, uint8_t *out, uint8_t *out_n);
  * limit at least 1.  Returns -1 on bad arguments.
  */
 int32_t bsw_band_width(const bsw_ctx_t *ctx, int32_t qlen, int32_t w);
+
+/*
+ * Split one batch over several devices (pairs are independent, so there is
+ * no exchange step: each device runs its part with its own context and the
+ * parts' results, concatenated in order, are the batch's results).  Part k
+ * is the contiguous pair range [bounds[k], bounds[k+1]); bounds[0] = 0 and
+ * bounds[parts] = n_pairs.  The ranges balance the estimated work: pair p
+ * weighs q_len[p] * min(t_len[p], 2w' + 1), its band area, w' its band after
+ * the gap-limit clip (bsw_band_width's rule, w_override[p] when given), and
+ * the boundaries are where the running weight first reaches k/parts of the
+ * total.  Host pointers (q_len, t_len, w_override nullable); no device work,
+ * so it needs no context.  sc, w, end_bonus: as bsw_init.
+ * Errors: BSW_EINVAL (null pointers, n_pairs < 0, parts < 1, a negative
+ * length or band).
+ */
+int bsw_partition(const bsw_scoring_t *sc, int32_t w, int32_t end_bonus, const int32_t *q_len,
+                  const int32_t *t_len, const int32_t *w_override, int64_t n_pairs, int32_t parts,
+                  int64_t *bounds);
 
 /*
  * bsw_extend_batch_noalloc: the batched extension for callers that cannot

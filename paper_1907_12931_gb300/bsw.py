@@ -99,6 +99,15 @@ ALN_DTYPE = np.dtype([("qb", "<i4"), ("qe", "<i4"), ("rb", "<i8"), ("re", "<i8")
                       ("w_left", "<i4"), ("w_right", "<i4"), ("kept", "<i4")])
 
 
+class bsw_serve_stats_t(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("launches", ctypes.c_int64), ("merged", ctypes.c_int64),
+                ("budget_waits", ctypes.c_int64), ("busy_ms", ctypes.c_double), ("union_ms", ctypes.c_double),
+                ("max_concurrent", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class bsw_timing_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int32), ("class_ms", ctypes.c_float * 16)]
 
@@ -169,6 +178,10 @@ def lib():
             L.bsw_set_reference_n.restype = ctypes.c_int
             L.bsw_extend_seeds_n.argtypes = [vp, i64, vp, vp, vp, vp, i64, vp, i32, vp, vp]
             L.bsw_extend_seeds_n.restype = ctypes.c_int
+            L.bsw_partition.argtypes = [ctypes.POINTER(bsw_scoring_t), i32, i32, vp, vp, vp, i64, i32, vp]
+            L.bsw_partition.restype = ctypes.c_int
+            L.bsw_stream_stats.argtypes = [vp, ctypes.POINTER(bsw_serve_stats_t), i32]
+            L.bsw_stream_stats.restype = ctypes.c_int
             L.bsw_fault_inject.argtypes = [ctypes.c_char_p]
             L.bsw_fault_inject.restype = ctypes.c_int
             _lib = L
@@ -309,6 +322,22 @@ def bsw_extend_seeds(ctx: int, n_reads: int, reads, read_off, read_len, seeds, m
                                   ctypes.addressof(cells))
 
 
+def bsw_partition(params, q_len, t_len, parts: int, w_override=None) -> np.ndarray:
+    """Contiguous pair ranges balanced by band area for `parts` devices:
+    bounds[parts + 1] with part k = pairs [bounds[k], bounds[k+1])."""
+    sc = params.scoring
+    s = bsw_scoring_t(sc.match, sc.mismatch, sc.o_del, sc.e_del, sc.o_ins, sc.e_ins)
+    ql = np.ascontiguousarray(q_len, np.int32)
+    tl = np.ascontiguousarray(t_len, np.int32)
+    wo = None if w_override is None else np.ascontiguousarray(w_override, np.int32)
+    bounds = np.zeros(int(parts) + 1, np.int64)
+    rc = lib().bsw_partition(ctypes.byref(s), int(params.w), int(params.end_bonus), ql.ctypes.data, tl.ctypes.data,
+                             None if wo is None else wo.ctypes.data, ql.shape[0], int(parts), bounds.ctypes.data)
+    if rc != BSW_OK:
+        raise BswError(rc, "bsw_partition")
+    return bounds
+
+
 def bsw_fault_inject(spec: str | None) -> int:
     """Arm host-side fault injection ("alloc,h2d:skip:count"; None disarms)."""
     return lib().bsw_fault_inject(None if spec is None else spec.encode())
@@ -445,6 +474,13 @@ class Context:
 
     def poll(self, ticket: int, timeout_us: int = -1) -> int:
         return bsw_stream_poll(self.handle, ticket, timeout_us)
+
+    def stream_stats(self, reset: bool = False) -> dict:
+        st = bsw_serve_stats_t()
+        rc = lib().bsw_stream_stats(self.handle, ctypes.byref(st), 1 if reset else 0)
+        if rc != BSW_OK:
+            raise BswError(rc, "bsw_stream_stats")
+        return st.as_dict()
 
     def get_plan(self) -> bsw_plan_t:
         return bsw_get_plan(self.handle)

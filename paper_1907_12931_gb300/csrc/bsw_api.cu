@@ -235,6 +235,7 @@ int64_t slot_bytes_for(int maxn) { return (int64_t)align_up((size_t)(maxn + 1 + 
 struct Lane {
     Streams S{};
     cudaEvent_t done = nullptr;
+    cudaEvent_t t_start = nullptr, t_end = nullptr;   // serving lanes: a launch's device interval
     DevBuf work, io, seq;       // seq: sequences of a staged host batch
     WorkLayout wl{};
     bool work_dirty = true;     // histogram must be zeroed before the next launch
@@ -250,6 +251,7 @@ struct Lane {
         }
         if (cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess) return BSW_ECUDA;
         if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) return BSW_ECUDA;
+        if (cudaEventCreate(&t_start) != cudaSuccess || cudaEventCreate(&t_end) != cudaSuccess) return BSW_ECUDA;
         return BSW_OK;
     }
     void destroy(Budget &B)
@@ -261,6 +263,9 @@ struct Lane {
         }
         if (S.fork) cudaEventDestroy(S.fork);
         if (done) cudaEventDestroy(done);
+        if (t_start) cudaEventDestroy(t_start);
+        if (t_end) cudaEventDestroy(t_end);
+        t_start = t_end = nullptr;
         if (S.main) cudaStreamDestroy(S.main);
         work.release(B);
         io.release(B);
@@ -338,7 +343,7 @@ int check_host_batch(const bsw_batch_t *b, const Params &P, Extents *x)
 // Device layout of a staged serving batch (one contiguous copy from the lane's
 // pinned staging).
 struct IoLayout {
-    size_t q, t, q_off, q_len, t_off, t_len, h0, w, out, cells, status, in_end, total;
+    size_t q, t, qn, tn, q_off, q_len, t_off, t_len, h0, w, out, cells, status, in_end, total;
 };
 
 // N bitmap bytes staged for packed bytes [lo, hi) (two packed bytes per
@@ -346,13 +351,17 @@ struct IoLayout {
 inline int64_t nmask_lo(int64_t lo) { return lo / 2; }
 inline int64_t nmask_bytes(int64_t lo, int64_t hi) { return hi > lo ? (hi + 1) / 2 - lo / 2 : 0; }
 
-IoLayout io_layout(int64_t N, int64_t qbytes, int64_t tbytes)
+// qbytes, tbytes: the staged packed bytes; with N bitmaps (has_n) one bitmap
+// byte per two packed bytes of each side.
+IoLayout io_layout(int64_t N, int64_t qbytes, int64_t tbytes, bool has_n)
 {
     IoLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
     L.q = take((size_t)qbytes);
     L.t = take((size_t)tbytes);
+    L.qn = take(has_n ? (size_t)(qbytes + 1) / 2 : 0);
+    L.tn = take(has_n ? (size_t)(tbytes + 1) / 2 : 0);
     L.q_off = take(8 * (size_t)N);
     L.q_len = take(4 * (size_t)N);
     L.t_off = take(8 * (size_t)N);
@@ -386,7 +395,22 @@ struct Request {
     std::vector<uint8_t> own;   // owned input copies (BSW_COPY_INPUTS)
     int status = BSW_PENDING;
     int64_t out_pos = 0;        // position of this request's pairs in the merged launch
+    int64_t qpos = 0, tpos = 0; // first staged packed byte of its queries / targets
 };
+
+// Staged packed bytes of a request's side starting at cursor `pos`: the side
+// starts on the parity of its first used byte lo (so base offsets move by a
+// multiple of 8 and its N bitmap bytes copy unshifted) and on a bitmap byte
+// of its own (so no bitmap byte is shared with the request before it).
+inline int64_t stage_start(int64_t pos, int64_t lo) { return ((pos + 1) & ~(int64_t)1) + (lo & 1); }
+
+// Serving counters (bsw_stream_stats) and each launch's device interval,
+// in milliseconds from the context's reference event.
+struct ServeStats {
+    int64_t requests = 0, launches = 0, merged = 0, budget_waits = 0;
+    std::vector<std::pair<float, float>> iv;
+};
+constexpr size_t kStatsIntervals = 1 << 16;   // intervals kept (the most recent)
 
 }  // namespace
 
@@ -449,6 +473,11 @@ struct bsw_ctx {
     size_t lane_out_off[kServeLanes] = {0, 0, 0};
     IoLayout lane_io[kServeLanes];
     bool lane_busy[kServeLanes] = {false, false, false};
+    bool lane_has_n[kServeLanes] = {false, false, false};
+    bool mem_wait = false;            // an admission waits for memory held by busy lanes
+    ServeStats stats;
+    cudaEvent_t ref_ev = nullptr;     // reference point of the launch intervals
+    bool ref_ok = false;
 };
 
 namespace {
@@ -703,27 +732,38 @@ int serve_launch(bsw_ctx *c, int li)
     std::vector<Request *> &reqs = c->lane_reqs[li];
     int64_t N = 0, qb = 0, tb = 0;
     int maxn = 0;
+    bool has_n = false;
     for (Request *r : reqs) {
         r->out_pos = N;
         N += r->b.n_pairs;
-        qb += r->ext.q_hi - r->ext.q_lo;
-        tb += r->ext.t_hi - r->ext.t_lo;
+        r->qpos = stage_start(qb, r->ext.q_lo);
+        qb = r->qpos + (r->ext.q_hi - r->ext.q_lo);
+        r->tpos = stage_start(tb, r->ext.t_lo);
+        tb = r->tpos + (r->ext.t_hi - r->ext.t_lo);
         maxn = std::max(maxn, r->ext.maxn);
+        has_n |= r->b.q_n != nullptr || r->b.t_n != nullptr;
     }
-    IoLayout L = io_layout(N, qb, tb);
+    IoLayout L = io_layout(N, qb, tb, has_n);
     int rc;
     if ((rc = lane.io.reserve(L.total, c->budget)) != BSW_OK) return rc;
     if ((rc = lane.ensure_work(N, std::max(maxn, kShortMax), c->sms, c->budget, nullptr)) != BSW_OK) return rc;
     if ((rc = lane.ensure_pinned(L.total)) != BSW_OK) return rc;
     uint8_t *h = lane.pinned;
-    int64_t qpos = 0, tpos = 0, k0 = 0;
+    if (has_n) std::memset(h + L.qn, 0, L.q_off - L.qn);   // both bitmaps: requests without N stage none
+    int64_t k0 = 0;
     for (Request *r : reqs) {
         const bsw_batch_t &b = r->b;
         const int64_t n = b.n_pairs;
-        std::memcpy(h + L.q + qpos, b.q + r->ext.q_lo, (size_t)(r->ext.q_hi - r->ext.q_lo));
-        std::memcpy(h + L.t + tpos, b.t + r->ext.t_lo, (size_t)(r->ext.t_hi - r->ext.t_lo));
+        std::memcpy(h + L.q + r->qpos, b.q + r->ext.q_lo, (size_t)(r->ext.q_hi - r->ext.q_lo));
+        std::memcpy(h + L.t + r->tpos, b.t + r->ext.t_lo, (size_t)(r->ext.t_hi - r->ext.t_lo));
+        if (b.q_n)
+            std::memcpy(h + L.qn + (r->qpos >> 1), b.q_n + (r->ext.q_lo >> 1),
+                        (size_t)(((r->ext.q_hi + 1) >> 1) - (r->ext.q_lo >> 1)));
+        if (b.t_n)
+            std::memcpy(h + L.tn + (r->tpos >> 1), b.t_n + (r->ext.t_lo >> 1),
+                        (size_t)(((r->ext.t_hi + 1) >> 1) - (r->ext.t_lo >> 1)));
         int64_t *qo = (int64_t *)(h + L.q_off) + k0, *to = (int64_t *)(h + L.t_off) + k0;
-        const int64_t dq = 4 * (qpos - r->ext.q_lo), dt = 4 * (tpos - r->ext.t_lo);
+        const int64_t dq = 4 * (r->qpos - r->ext.q_lo), dt = 4 * (r->tpos - r->ext.t_lo);
         for (int64_t k = 0; k < n; ++k) {
             // pairs that are never read (empty sides) keep a valid offset of 0
             const bool used = b.q_len[k] > 0 && b.t_len[k] > 0;
@@ -736,17 +776,17 @@ int serve_launch(bsw_ctx *c, int li)
         int32_t *wv = (int32_t *)(h + L.w) + k0;
         if (b.w_override) std::memcpy(wv, b.w_override, 4 * (size_t)n);
         else for (int64_t k = 0; k < n; ++k) wv[k] = c->P.w;
-        qpos += r->ext.q_hi - r->ext.q_lo;
-        tpos += r->ext.t_hi - r->ext.t_lo;
         k0 += n;
     }
     cudaStream_t st = lane.S.main;
     uint8_t *d = lane.io.p;
     cudaError_t e;
+    if ((e = cudaEventRecord(lane.t_start, st)) != cudaSuccess) return cuda_rc(e);
     if ((e = h2d(d, h, L.in_end, st)) != cudaSuccess) return cuda_rc(e);
     Batch B{N, d + L.q, (const int64_t *)(d + L.q_off), (const int32_t *)(d + L.q_len), d + L.t,
             (const int64_t *)(d + L.t_off), (const int32_t *)(d + L.t_len), (const int32_t *)(d + L.h0),
-            (const int32_t *)(d + L.w), (bsw_result_t *)(d + L.out)};
+            (const int32_t *)(d + L.w), (bsw_result_t *)(d + L.out), has_n ? d + L.qn : nullptr,
+            has_n ? d + L.tn : nullptr};
     Work W = make_work(lane.work.p, lane.wl);
     if ((e = enqueue_launch(c, lane, lane.S, B, W, 0u, true, c->plan)) != cudaSuccess) {
         lane.work_dirty = true;
@@ -755,31 +795,58 @@ int serve_launch(bsw_ctx *c, int li)
     if ((e = cudaMemcpyAsync(h + L.out, d + L.out, sizeof(bsw_result_t) * (size_t)N, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_rc(e);
     if ((e = cudaMemcpyAsync(h + L.status, W.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaEventRecord(lane.t_end, st)) != cudaSuccess) return cuda_rc(e);
     if ((e = cudaEventRecord(lane.done, st)) != cudaSuccess) return cuda_rc(e);
     c->lane_io[li] = L;
     c->lane_pairs[li] = N;
+    c->lane_has_n[li] = has_n;
     return BSW_OK;
 }
 
-void finish_lane(bsw_ctx *c, int li, int rc)
+// Called with the lock held.  launched: the lane's work reached the device
+// (its events are recorded), so its interval is kept.
+void finish_lane(bsw_ctx *c, int li, int rc, bool launched)
 {
     Lane &lane = c->serve_lane[li];
     const IoLayout &L = c->lane_io[li];
     if (rc == BSW_OK) rc = status_to_rc(*(uint32_t *)(lane.pinned + L.status));
+    ServeStats &S = c->stats;
     for (Request *r : c->lane_reqs[li]) {
         if (rc == BSW_OK)
             std::memcpy(r->out, lane.pinned + L.out + sizeof(bsw_result_t) * (size_t)r->out_pos,
                         sizeof(bsw_result_t) * (size_t)r->b.n_pairs);
         r->status = rc;
     }
+    S.requests += (int64_t)c->lane_reqs[li].size();
+    if (c->lane_reqs[li].size() > 1) S.merged += (int64_t)c->lane_reqs[li].size();
+    if (launched) {
+        ++S.launches;
+        float a = 0.0f, b = 0.0f;
+        if (c->ref_ok && cudaEventElapsedTime(&a, c->ref_ev, lane.t_start) == cudaSuccess &&
+            cudaEventElapsedTime(&b, c->ref_ev, lane.t_end) == cudaSuccess) {
+            try {
+                if (S.iv.size() >= kStatsIntervals) S.iv.erase(S.iv.begin(), S.iv.begin() + kStatsIntervals / 2);
+                S.iv.emplace_back(a, b);
+            } catch (...) {
+            }
+        } else {
+            cudaGetLastError();
+        }
+    }
     c->lane_reqs[li].clear();
     c->lane_busy[li] = false;
+    c->mem_wait = false;   // memory may be free now
 }
 
 void server_main(bsw_ctx *c)
 {
     cudaSetDevice(c->device);
     std::unique_lock<std::mutex> lk(c->mu);
+    if (cudaEventCreate(&c->ref_ev) == cudaSuccess && cudaEventRecord(c->ref_ev, c->sync.S.main) == cudaSuccess &&
+        cudaEventSynchronize(c->ref_ev) == cudaSuccess)
+        c->ref_ok = true;
+    else
+        cudaGetLastError();
     for (;;) {
         bool progressed = false;
         // completions
@@ -787,27 +854,50 @@ void server_main(bsw_ctx *c)
             if (!c->lane_busy[li]) continue;
             cudaError_t q = cudaEventQuery(c->serve_lane[li].done);
             if (q == cudaErrorNotReady) continue;
-            finish_lane(c, li, q == cudaSuccess ? BSW_OK : cuda_rc(q));
+            finish_lane(c, li, q == cudaSuccess ? BSW_OK : cuda_rc(q), true);
             progressed = true;
         }
         if (progressed) c->cv_done.notify_all();
-        // admissions: continuous batching into free lanes
-        for (int li = 0; li < kServeLanes && !c->queue.empty(); ++li) {
+        // admissions: continuous batching into free lanes (none while an
+        // admission waits for memory that busy lanes hold)
+        bool any_busy = false;
+        for (int li = 0; li < kServeLanes; ++li) any_busy |= c->lane_busy[li];
+        if (!any_busy) c->mem_wait = false;
+        for (int li = 0; li < kServeLanes && !c->queue.empty() && !c->mem_wait; ++li) {
             if (c->lane_busy[li]) continue;
             if (!c->lane_created[li]) {
                 if (c->serve_lane[li].create() != BSW_OK) continue;
                 c->lane_created[li] = true;
             }
             std::vector<Request *> &reqs = c->lane_reqs[li];
-            int64_t pairs = 0, ecells = 0;
+            int64_t pairs = 0, ecells = 0, qb = 0, tb = 0;
+            int maxn = 0;
+            bool has_n = false;
+            // Whether the merged launch, with request r added, fits the budget
+            // on its own (every request alone does: bsw_stream_submit checks).
+            auto fits = [&](const Request *r) {
+                const bool n2 = has_n || r->b.q_n || r->b.t_n;
+                const IoLayout L = io_layout(pairs + r->b.n_pairs, qb + (r->ext.q_hi - r->ext.q_lo) + 2,
+                                             tb + (r->ext.t_hi - r->ext.t_lo) + 2, n2);
+                const WorkLayout W = work_layout(pairs + r->b.n_pairs,
+                                                 slot_bytes_for(std::max(std::max(maxn, r->ext.maxn), kShortMax)),
+                                                 warp_slots_needed(c->sms));
+                return (int64_t)(L.total + W.total) <= c->budget.cap;
+            };
             try {                        // a request moves to the lane only once the lane's list holds it
                 while (!c->queue.empty() &&
                        (reqs.empty() || (pairs + c->queue.front()->b.n_pairs <= kMergePairs &&
-                                         ecells + c->queue.front()->ext.est_cells <= kMergeCells))) {
+                                         ecells + c->queue.front()->ext.est_cells <= kMergeCells &&
+                                         fits(c->queue.front())))) {
                     if (fault_hit(BSW_FAULT_HOST)) throw std::bad_alloc();
+                    const Request *r = c->queue.front();
                     reqs.push_back(c->queue.front());
-                    pairs += c->queue.front()->b.n_pairs;
-                    ecells += c->queue.front()->ext.est_cells;
+                    pairs += r->b.n_pairs;
+                    ecells += r->ext.est_cells;
+                    qb += r->ext.q_hi - r->ext.q_lo + 2;
+                    tb += r->ext.t_hi - r->ext.t_lo + 2;
+                    maxn = std::max(maxn, r->ext.maxn);
+                    has_n |= r->b.q_n || r->b.t_n;
                     c->queue.pop_front();
                 }
             } catch (...) {
@@ -832,11 +922,13 @@ void server_main(bsw_ctx *c)
                     reqs.clear();
                     c->lane_busy[li] = false;
                     c->serve_lane[li].io.release(c->budget);
+                    c->mem_wait = true;
+                    ++c->stats.budget_waits;
                     break;
                 }
             }
             if (rc != BSW_OK) {
-                finish_lane(c, li, rc);
+                finish_lane(c, li, rc, false);
                 c->cv_done.notify_all();
             }
             progressed = true;
@@ -948,6 +1040,38 @@ int32_t bsw_band_width(const bsw_ctx_t *ctx, int32_t qlen, int32_t w)
     return std::min(w, std::min(cap(P.o_ins, P.e_ins), cap(P.o_del, P.e_del)));
 }
 
+int bsw_partition(const bsw_scoring_t *sc, int32_t w, int32_t end_bonus, const int32_t *q_len, const int32_t *t_len,
+                  const int32_t *w_override, int64_t n_pairs, int32_t parts, int64_t *bounds)
+{
+    if (!sc || !bounds || parts < 1 || n_pairs < 0 || w < 0 || end_bonus < 0) return BSW_EINVAL;
+    if (n_pairs > 0 && (!q_len || !t_len)) return BSW_EINVAL;
+    if (sc->match <= 0 || sc->e_del <= 0 || sc->e_ins <= 0 || sc->o_del < 0 || sc->o_ins < 0) return BSW_EINVAL;
+    auto cap = [&](int32_t n, int o, int e) {
+        const long long x = (long long)n * sc->match + end_bonus - o + e;
+        const long long k = x / e;
+        return k > 1 ? k : 1ll;
+    };
+    // two passes (the total, then the boundaries) and no per-pair storage
+    long double total = 0.0L;
+    for (int64_t p = 0; p < n_pairs; ++p) {
+        const int32_t n = q_len[p], m = t_len[p], wp = w_override ? w_override[p] : w;
+        if (n < 0 || m < 0 || wp < 0) return BSW_EINVAL;
+        const long long wb = std::min<long long>(wp, std::min(cap(n, sc->o_ins, sc->e_ins), cap(n, sc->o_del, sc->e_del)));
+        total += (long double)n * (long double)std::min<long long>(m, 2 * wb + 1);
+    }
+    bounds[0] = 0;
+    long double run = 0.0L;
+    int k = 1;
+    for (int64_t p = 0; p < n_pairs && k < parts; ++p) {
+        const int32_t n = q_len[p], m = t_len[p], wp = w_override ? w_override[p] : w;
+        const long long wb = std::min<long long>(wp, std::min(cap(n, sc->o_ins, sc->e_ins), cap(n, sc->o_del, sc->e_del)));
+        run += (long double)n * (long double)std::min<long long>(m, 2 * wb + 1);
+        while (k < parts && run * parts >= total * k) bounds[k++] = p + 1;
+    }
+    while (k <= parts) bounds[k++] = n_pairs;
+    return BSW_OK;
+}
+
 int bsw_init(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, int32_t end_bonus, int64_t mem_budget_bytes,
              bsw_ctx_t **out)
 {
@@ -1031,7 +1155,6 @@ int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, u
         if (b->flags & (BSW_DEVICE_PTRS | BSW_PLAIN_KERNEL | BSW_PLAIN_GLOBAL | BSW_FORCE_I8 | BSW_FORCE_I16 |
                         BSW_FORCE_I32 | BSW_TIME_KERNELS))
             return BSW_EINVAL;   // the serving loop runs the context's batched plan on host inputs
-        if (b->q_n || b->t_n) return BSW_EINVAL;   // no N bitmaps in the serving loop
         if (b->n_pairs > 0 && (!b->q || !b->q_off || !b->q_len || !b->t || !b->t_off || !b->t_len || !b->h0 || !out))
             return BSW_EINVAL;
         std::unique_ptr<Request> holder(new (std::nothrow) Request());
@@ -1042,14 +1165,17 @@ int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, u
         int rc = check_host_batch(b, ctx->P, &r->ext);
         if (rc == BSW_OK) {
             const int64_t N = b->n_pairs;
-            IoLayout L = io_layout(N, r->ext.q_hi - r->ext.q_lo, r->ext.t_hi - r->ext.t_lo);
+            IoLayout L = io_layout(N, r->ext.q_hi - r->ext.q_lo + 2, r->ext.t_hi - r->ext.t_lo + 2,
+                                   b->q_n != nullptr || b->t_n != nullptr);
             WorkLayout W = work_layout(N, slot_bytes_for(std::max(r->ext.maxn, kShortMax)), warp_slots_needed(ctx->sms));
             if ((int64_t)(L.total + W.total) > ctx->budget.cap) rc = BSW_EBUDGET;
         }
         if (rc == BSW_OK && (b->flags & BSW_COPY_INPUTS) && b->n_pairs > 0) {
             const int64_t N = b->n_pairs;
             const size_t qb = (size_t)(r->ext.q_hi - r->ext.q_lo), tb = (size_t)(r->ext.t_hi - r->ext.t_lo);
-            const size_t total = qb + tb + 8 * (size_t)N * 2 + 4 * (size_t)N * (b->w_override ? 4 : 3);
+            const size_t qnb = b->q_n ? (size_t)(((r->ext.q_hi + 1) >> 1) - (r->ext.q_lo >> 1)) : 0;
+            const size_t tnb = b->t_n ? (size_t)(((r->ext.t_hi + 1) >> 1) - (r->ext.t_lo >> 1)) : 0;
+            const size_t total = qb + tb + qnb + tnb + 8 * (size_t)N * 2 + 4 * (size_t)N * (b->w_override ? 4 : 3);
             try {
                 r->own.resize(total);
             } catch (...) {
@@ -1063,6 +1189,16 @@ int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, u
                 std::memcpy(p, b->t + r->ext.t_lo, tb);
                 r->b.t = p - r->ext.t_lo;
                 p += tb;
+                if (qnb) {                  // the N bitmaps' bytes of the copied bases, offsets kept valid too
+                    std::memcpy(p, b->q_n + (r->ext.q_lo >> 1), qnb);
+                    r->b.q_n = p - (r->ext.q_lo >> 1);
+                    p += qnb;
+                }
+                if (tnb) {
+                    std::memcpy(p, b->t_n + (r->ext.t_lo >> 1), tnb);
+                    r->b.t_n = p - (r->ext.t_lo >> 1);
+                    p += tnb;
+                }
                 auto dup = [&](const void *src, size_t bytes) { std::memcpy(p, src, bytes); void *d = p; p += bytes; return d; };
                 r->b.q_off = (const int64_t *)dup(b->q_off, 8 * (size_t)N);
                 r->b.t_off = (const int64_t *)dup(b->t_off, 8 * (size_t)N);
@@ -1111,6 +1247,45 @@ int bsw_stream_submit(bsw_ctx_t *ctx, const bsw_batch_t *b, bsw_result_t *out, u
         ctx->next_ticket = t + 1;
         *ticket = t;
         if (b->n_pairs > 0) ctx->cv_work.notify_one();
+        return BSW_OK;
+    });
+}
+
+int bsw_stream_stats(bsw_ctx_t *ctx, bsw_serve_stats_t *out, int32_t reset)
+{
+    if (!ctx || !out) return BSW_EINVAL;
+    return guard([&]() -> int {
+        std::vector<std::pair<float, float>> iv;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            const ServeStats &S = ctx->stats;
+            out->requests = S.requests;
+            out->launches = S.launches;
+            out->merged = S.merged;
+            out->budget_waits = S.budget_waits;
+            iv = S.iv;
+            if (reset) ctx->stats = ServeStats();
+        }
+        // busy: the sum of the launches' intervals; union: the time at least
+        // one launch was on the device; the most launches at one moment
+        std::sort(iv.begin(), iv.end());
+        double busy = 0.0, uni = 0.0, end = -1e30;
+        for (const auto &x : iv) {
+            busy += x.second - x.first;
+            if (x.first > end) { uni += x.second - x.first; end = x.second; }
+            else if (x.second > end) { uni += x.second - end; end = x.second; }
+        }
+        std::vector<std::pair<float, int>> ev;
+        ev.reserve(2 * iv.size());
+        for (const auto &x : iv) { ev.emplace_back(x.first, 1); ev.emplace_back(x.second, -1); }
+        std::sort(ev.begin(), ev.end(), [](const std::pair<float, int> &a, const std::pair<float, int> &b) {
+            return a.first < b.first || (a.first == b.first && a.second < b.second);
+        });
+        int cur = 0, mx = 0;
+        for (const auto &e : ev) { cur += e.second; mx = std::max(mx, cur); }
+        out->busy_ms = busy;
+        out->union_ms = uni;
+        out->max_concurrent = mx;
         return BSW_OK;
     });
 }

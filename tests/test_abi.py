@@ -220,3 +220,48 @@ def test_fault_inject_environment(tmp_path):
         r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
         assert r.returncode == 0, r.stderr
         assert r.stdout.strip() == "[228]"
+
+
+def _band_area(params, q_len, t_len, w_override=None):
+    """Each pair's band area, from the band clip's definition in include/bsw.h."""
+    sc = params.scoring
+    n = np.asarray(q_len, np.int64)
+    m = np.asarray(t_len, np.int64)
+    w = np.full(n.shape, params.w, np.int64) if w_override is None else np.asarray(w_override, np.int64)
+
+    def cap(o, e):
+        return np.maximum((n * sc.match + params.end_bonus - o + e) // e, 1)
+
+    wb = np.minimum(w, np.minimum(cap(sc.o_ins, sc.e_ins), cap(sc.o_del, sc.e_del)))
+    return n * np.minimum(m, 2 * wb + 1)
+
+
+def test_partition_balances_band_area(lib):
+    """bsw_partition: contiguous ranges covering every pair once, each
+    boundary the first pair at which the running band area reaches k/parts of
+    the total (so every part is within one pair of an equal share)."""
+    from paper_1907_12931_gb300 import workload as W
+    for name, n_pairs in (("read151", 50_000), ("long10k", 3000), ("plain10k", 777)):
+        wl = W.make(name, n_pairs=n_pairs)
+        wt = _band_area(wl.params, wl.q_len, wl.t_len).astype(np.float64)
+        run = np.cumsum(wt)
+        for parts in (1, 2, 3, 8, 13):
+            b = lib.bsw_partition(wl.params, wl.q_len, wl.t_len, parts)
+            assert b[0] == 0 and b[-1] == wl.n_pairs and (np.diff(b) >= 0).all()
+            for k in range(1, parts):
+                want = int(np.searchsorted(run * parts >= run[-1] * k, True)) + 1
+                assert b[k] == want, (name, parts, k)
+            shares = np.add.reduceat(wt, b[:-1])[np.diff(b) > 0] if parts > 1 else wt.sum()
+            assert np.all(np.abs(np.atleast_1d(shares) - wt.sum() / parts) <= wt.max() + 1)
+    # per-pair bands, more parts than pairs, an empty batch, bad arguments
+    wl = W.make("plain10k", n_pairs=5)
+    ws = np.array([1, 100, 3, 0, 50], np.int32)
+    b = lib.bsw_partition(wl.params, wl.q_len, wl.t_len, 9, w_override=ws)
+    assert b[0] == 0 and b[-1] == 5 and (np.diff(b) >= 0).all() and b.shape == (10,)
+    e = W.make("plain10k", n_pairs=1)
+    b = lib.bsw_partition(e.params, e.q_len[:0], e.t_len[:0], 4)
+    assert b.tolist() == [0, 0, 0, 0, 0]
+    with pytest.raises(lib.BswError):
+        lib.bsw_partition(wl.params, wl.q_len, wl.t_len, 0)
+    with pytest.raises(lib.BswError):
+        lib.bsw_partition(wl.params, np.array([-1, 3], np.int32), np.array([4, 4], np.int32), 2)

@@ -148,9 +148,35 @@ def test_autotune_with_n(bsw):
     assert gc == cells
 
 
-def test_serving_rejects_n(bsw):
-    wl = hand_cases()
-    with bsw.Context(wl.params) as ctx:
-        with pytest.raises(bsw.BswError) as e:
-            ctx.submit(bsw.HostBatch(wl), np.zeros((wl.n_pairs, 6), np.int32))
-        assert e.value.code == bsw.BSW_EINVAL
+def test_serving_with_n(bsw):
+    """Batches with N bitmaps through the serving loop, merged with N-free
+    batches and with each other (some copied at submit): every request gives
+    the oracle's results, and the same as alone."""
+    hc = hand_cases()
+    r151 = W.make("read151", n_pairs=60_000)
+    nw = W.inject_n(r151, 0.01, 0.002, seed=9)
+    ref_hc, _ = oracle_of(hc)
+    ref_nw, _ = oracle_of(nw)
+    ref_151, _ = oracle_of(r151)
+    rng = np.random.default_rng(31)
+    reqs = [(hc, ref_hc)]
+    for k in range(12):
+        src, ref = ((nw, ref_nw), (r151, ref_151))[k % 2]
+        size = int(rng.integers(1, 9000))
+        start = int(rng.integers(0, src.n_pairs - size))
+        idx = np.arange(start, start + size)
+        reqs.append((src.subset(idx), ref[idx]))
+    with bsw.Context(hc.params, mem_budget_bytes=4 << 30) as ctx:
+        tickets, outs, hbs = [], [], []
+        for k, (sub, _) in enumerate(reqs):
+            hb = bsw.HostBatch(sub)
+            out = np.full((sub.n_pairs, 6), -7, np.int32)
+            tickets.append(ctx.submit(hb, out, bsw.BSW_COPY_INPUTS if k % 3 == 1 else 0))
+            outs.append(out)
+            hbs.append(hb)
+        for t in tickets:
+            assert ctx.poll(t, 60_000_000) == bsw.BSW_OK
+        for (sub, ref), out, hb in zip(reqs, outs, hbs):
+            assert_same(out, ref, "served request with N")
+            alone, _ = ctx.extend_host(hb)
+            np.testing.assert_array_equal(alone, out)

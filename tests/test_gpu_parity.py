@@ -325,6 +325,56 @@ def test_serving_each_request_same_alone_and_mixed(bsw):
             np.testing.assert_array_equal(alone, out)
 
 
+def test_serving_waits_for_memory(bsw):
+    """A budget that holds one launch but not two: while one lane runs, the
+    next admission is put back to wait for its memory (counted in the serving
+    statistics), and every request still comes back with the oracle's results."""
+    wl, ref, _ = workload_and_oracle("read151", 200_000)
+    reqs = [np.arange(k * 40_000, (k + 1) * 40_000) for k in range(5)]
+    with bsw.Context(wl.params, mem_budget_bytes=30 << 20) as ctx:
+        outs, tickets, hbs = [], [], []
+        for idx in reqs:
+            hb = bsw.HostBatch(wl.subset(idx))
+            out = np.full((idx.shape[0], 6), -7, np.int32)
+            tickets.append(ctx.submit(hb, out))
+            outs.append(out)
+            hbs.append(hb)
+        for t in tickets:
+            assert ctx.poll(t, 120_000_000) == bsw.BSW_OK
+        st = ctx.stream_stats()
+        for idx, out in zip(reqs, outs):
+            assert_same(out, ref[idx], "request served under a small budget")
+    assert st["requests"] == len(reqs)
+    assert st["budget_waits"] >= 1
+    assert st["launches"] >= 2
+
+
+def test_serving_launches_overlap(bsw):
+    """Long-query requests larger than one merge run as several launches over
+    the execution lanes; the statistics show their device intervals and that
+    they overlapped, and every result is the oracle's."""
+    wl, ref, _ = workload_and_oracle("long10k")
+    rng = np.random.default_rng(8)
+    with bsw.Context(wl.params, mem_budget_bytes=8 << 30) as ctx:
+        ctx.stream_stats(reset=True)
+        outs, tickets, idxs = [], [], []
+        for _ in range(24):
+            idx = np.sort(rng.choice(wl.n_pairs, 2500, replace=False))
+            out = np.full((idx.shape[0], 6), -7, np.int32)
+            tickets.append(ctx.submit(bsw.HostBatch(wl.subset(idx)), out))
+            outs.append(out)
+            idxs.append(idx)
+        for t in tickets:
+            assert ctx.poll(t, 120_000_000) == bsw.BSW_OK
+        st = ctx.stream_stats(reset=True)
+        assert ctx.stream_stats()["requests"] == 0              # reset
+    for idx, out in zip(idxs, outs):
+        assert_same(out, ref[idx], "long request")
+    assert st["requests"] == 24 and st["launches"] >= 2
+    assert st["union_ms"] > 0 and st["busy_ms"] >= st["union_ms"] * 0.999
+    assert st["max_concurrent"] >= 2, st
+
+
 def test_serving_rejects_and_times_out(bsw):
     wl, _, _ = workload_and_oracle("plain10k")
     with bsw.Context(wl.params, mem_budget_bytes=1 << 16) as ctx:
