@@ -54,6 +54,8 @@ def run_point(ctxs, reqs, rate, verify):
     """Submit reqs (list of (pool_idx, HostBatch, ref, cells)) at Poisson times
     with the given rate (requests/s; None = all at once).  Returns latencies,
     wall time, cells and mismatches."""
+    for c in set(ctxs):
+        c.stream_stats(reset=True)
     n = len(reqs)
     rng = np.random.default_rng(12345)
     gaps = rng.exponential(1.0 / rate, n) if rate else np.zeros(n)
@@ -149,10 +151,21 @@ def sweep(loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0), nreq=1000, c
         rate = load * peak_gcups * 1e9 / mean_cells
         lat, wall, cells, mism = run_point(ctxs, reqs, rate, verify)
         total_mism += mism
+        st = [c.stream_stats() for c in (ctx_short, ctx_long)]
+        busy = sum(x["busy_ms"] for x in st)
         points.append({"offered_load": load, "offered_req_per_s": round(rate, 2),
                        "p50_ms": round(_percentile(lat, 50), 3), "p99_ms": round(_percentile(lat, 99), 3),
                        "throughput_gcups": round(cells / wall / 1e9, 2), "requests": len(reqs),
-                       "mismatches": mism})
+                       "mismatches": mism,
+                       "launches": sum(x["launches"] for x in st),
+                       "merged_requests": sum(x["merged"] for x in st),
+                       "budget_waits": sum(x["budget_waits"] for x in st),
+                       "device_busy_ms_per_context": [round(x["busy_ms"], 2) for x in st],
+                       "overlap_per_context": [round(x["busy_ms"] / x["union_ms"], 3) if x["union_ms"] else None
+                                               for x in st],
+                       "max_concurrent_launches": [x["max_concurrent"] for x in st],
+                       "wall_ms": round(wall * 1e3, 2),
+                       "device_busy_fraction_of_wall": round(busy / (wall * 1e3), 3)})
     ctx_short.close()
     ctx_long.close()
     return {
