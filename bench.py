@@ -42,7 +42,10 @@ METRIC = "BSW GCUPS on 1 GB300 (batched vs plain kernel, bit-exact); p50/p99 ser
 # DRAM bytes read + written per launch of a workload's dominant kernel, from
 # one ncu capture of the current kernel (bytes, source); other kernels and
 # workloads report null.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("read250", "k_inter<192,u8>"): (61_559_552, "ncu dram__bytes_read.sum + dram__bytes_write.sum of the dominant "
+                                                 "launch, profiles/k_inter192_u8_read250.md"),
+}
 
 SECONDARY = ("read151", "long10k")
 

@@ -331,14 +331,10 @@ def test_serving_waits_for_memory(bsw):
     statistics), and every request still comes back with the oracle's results."""
     wl, ref, _ = workload_and_oracle("read151", 200_000)
     reqs = [np.arange(k * 40_000, (k + 1) * 40_000) for k in range(5)]
+    hbs = [bsw.HostBatch(wl.subset(idx)) for idx in reqs]          # packed first: the submits come together
+    outs = [np.full((idx.shape[0], 6), -7, np.int32) for idx in reqs]
     with bsw.Context(wl.params, mem_budget_bytes=30 << 20) as ctx:
-        outs, tickets, hbs = [], [], []
-        for idx in reqs:
-            hb = bsw.HostBatch(wl.subset(idx))
-            out = np.full((idx.shape[0], 6), -7, np.int32)
-            tickets.append(ctx.submit(hb, out))
-            outs.append(out)
-            hbs.append(hb)
+        tickets = [ctx.submit(hb, out) for hb, out in zip(hbs, outs)]
         for t in tickets:
             assert ctx.poll(t, 120_000_000) == bsw.BSW_OK
         st = ctx.stream_stats()
@@ -355,15 +351,12 @@ def test_serving_launches_overlap(bsw):
     they overlapped, and every result is the oracle's."""
     wl, ref, _ = workload_and_oracle("long10k")
     rng = np.random.default_rng(8)
+    idxs = [np.sort(rng.choice(wl.n_pairs, 2500, replace=False)) for _ in range(24)]
+    hbs = [bsw.HostBatch(wl.subset(idx)) for idx in idxs]          # packed first: the submits come together
+    outs = [np.full((idx.shape[0], 6), -7, np.int32) for idx in idxs]
     with bsw.Context(wl.params, mem_budget_bytes=8 << 30) as ctx:
         ctx.stream_stats(reset=True)
-        outs, tickets, idxs = [], [], []
-        for _ in range(24):
-            idx = np.sort(rng.choice(wl.n_pairs, 2500, replace=False))
-            out = np.full((idx.shape[0], 6), -7, np.int32)
-            tickets.append(ctx.submit(bsw.HostBatch(wl.subset(idx)), out))
-            outs.append(out)
-            idxs.append(idx)
+        tickets = [ctx.submit(hb, out) for hb, out in zip(hbs, outs)]
         for t in tickets:
             assert ctx.poll(t, 120_000_000) == bsw.BSW_OK
         st = ctx.stream_stats(reset=True)
