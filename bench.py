@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--no-smem", action="store_true", help="skip the SMEM search leg")
     ap.add_argument("--no-nbases", action="store_true", help="skip the N-bases leg")
     ap.add_argument("--plan", default=None,
-                    help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps[,cta_min] "
+                    help="fixed plan short_max,u8_bounds,i16_bounds,packed,warp_cols,inter_warps[,cta_min[,warp_x2]] "
                          "(no autotune)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="requests per offered-load point (--serve)")
     ap.add_argument("--serve-quick", type=int, default=200,
@@ -218,6 +218,10 @@ def class_of(q_len, t_len, h0, match, plan):
     i16 = _smallest_class(n, I16_NMAX, plan.i16_bounds | 1, 8)
     cta_min = getattr(plan, "cta_min", 0)
     w16 = np.where((cta_min > 0) & (n >= max(cta_min, 1)), 12, 13)
+    if getattr(plan, "warp_x2", 0) and match <= 3:
+        # the two-columns kernel re-runs pairs of bound 2^(15 - z) and above with 32-bit lanes
+        z = int(np.ceil(np.log2(match + 1)))
+        w16 = np.where((w16 == 13) & (bound >= (1 << (15 - z))), 14, w16)
     c = np.where(n > plan.short_max, np.where(bound <= 32767, w16, 14),
                  np.where(bound <= 255, u8, np.where(bound <= 32767, i16, 14)))
     return np.where((n <= 0) | (m <= 0), -1, c)
@@ -236,6 +240,8 @@ def class_kernel(c, plan, scoring):
         return "k_inter<%d,i16>" % I16_NMAX[c - 8]
     if c == 12:
         return "k_cta<8,s16>"
+    if c == 13 and getattr(plan, "warp_x2", 0) and scoring.match <= 3:
+        return "k_warp_x2"
     return "k_warp<%d,s16>" % plan.warp_cols if c == 13 else "k_warp<8,s32>"
 
 
@@ -604,7 +610,7 @@ def plain_leg(bsw, ctx, db, plan, steps, warmup, stream, dist, out_ref, cells_re
     per = {}
     for cols in (4, 8, 16):
         ctx.set_plan(bsw.make_plan(plan.short_max, plan.u8_bounds, plan.i16_bounds, plan.packed, cols,
-                                   plan.inter_warps, plan.cta_min))
+                                   plan.inter_warps, plan.cta_min, 0))
         ms = time_device(ctx, db, bsw.BSW_PLAIN_KERNEL, steps, warmup, stream, dist)
         equal = bool(np.array_equal(db.out.cpu().numpy(), out_ref)) and int(db.cells.item()) == cells_ref
         per[cols] = (ms, equal)

@@ -355,17 +355,25 @@ int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, 
  *                row's band split across the warps (uneven batches: the
  *                longest pairs no longer set the batch's tail); 0: none.  A
  *                multiple of 64 in [128, BSW_MAX_QLEN], or 0.
+ *   warp_x2      1: the 16-bit warp-per-pair class runs the kernel that
+ *                computes two columns per instruction (16-bit halves of one
+ *                register, 8-column granules, 1 to 4 granules per lane chosen
+ *                per row), for pairs whose score bound h0 + match*min(n, m)
+ *                is below 2^(15 - z), 2^z >= match + 1 (16384 for match 1);
+ *                the class's other pairs run with 32-bit lanes.  Applies when
+ *                match <= 3 and o + e <= 8192, e <= 2048 on both sides;
+ *                warp_cols is then unused by that class.  0 or 1.
  *   ms           output of bsw_autotune (the plan's time on its sample, in
  *                milliseconds); ignored by bsw_set_plan.
  */
 typedef struct {
     int32_t short_max;
     uint32_t u8_bounds, i16_bounds;
-    int32_t packed, warp_cols, inter_warps, cta_min;
+    int32_t packed, warp_cols, inter_warps, cta_min, warp_x2;
     float ms;
 } bsw_plan_t;
 
-/* The context's current plan (a new context has {256, 0xff, 0xf, 0, 8, 2, 0}).
+/* The context's current plan (a new context has {256, 0xff, 0xf, 0, 8, 2, 0, 0}).
  * Errors: BSW_EINVAL (null argument). */
 int bsw_get_plan(const bsw_ctx_t *ctx, bsw_plan_t *plan);
 
@@ -379,7 +387,8 @@ int bsw_set_plan(bsw_ctx_t *ctx, const bsw_plan_t *plan);
  * timed with CUDA events as the fastest of `reps` launches (reps <= 0: 3)
  * after one warm-up launch, on the context's stream.  The search is
  * coordinate descent from the default plan: short_max (256, 192, 128, 96,
- * 64), warp_cols (8, 4, 16), cta_min (0, 8192, 4096, 2048, 1024, 512),
+ * 64), warp_x2 (0, 1), warp_cols (8, 4, 16; when warp_x2 stays 0),
+ * cta_min (0, 8192, 4096, 2048, 1024, 512),
  * packed, inter_warps (2, 1, 4), then each class
  * boundary removed in turn (8-bit from 192 down, then 16-bit); a change is
  * kept when it is at least 1% faster than the best so far.  A knob that only

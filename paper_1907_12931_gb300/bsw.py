@@ -75,7 +75,7 @@ class bsw_batch_t(ctypes.Structure):
 class bsw_plan_t(ctypes.Structure):
     _fields_ = [("short_max", ctypes.c_int32), ("u8_bounds", ctypes.c_uint32), ("i16_bounds", ctypes.c_uint32),
                 ("packed", ctypes.c_int32), ("warp_cols", ctypes.c_int32), ("inter_warps", ctypes.c_int32),
-                ("cta_min", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("cta_min", ctypes.c_int32), ("warp_x2", ctypes.c_int32), ("ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -354,8 +354,8 @@ def bsw_sa_build(codes: np.ndarray) -> np.ndarray:
 
 
 def make_plan(short_max=256, u8_bounds=0xff, i16_bounds=0xf, packed=0, warp_cols=8, inter_warps=2,
-              cta_min=0) -> bsw_plan_t:
-    return bsw_plan_t(short_max, u8_bounds, i16_bounds, packed, warp_cols, inter_warps, cta_min, 0.0)
+              cta_min=0, warp_x2=0) -> bsw_plan_t:
+    return bsw_plan_t(short_max, u8_bounds, i16_bounds, packed, warp_cols, inter_warps, cta_min, warp_x2, 0.0)
 
 
 # --------------------------------------------------------------- marshalling

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbsw.so")
-SOURCES = ["bsw_kernels.cu", "bsw_api.cu", "bsw_noalloc.cu", "bsw_driver.cu", "bsw_sal.cu", "bsw_sa.cu", "bsw_fm.cu"]
+SOURCES = ["bsw_kernels.cu", "bsw_warp2.cu", "bsw_api.cu", "bsw_noalloc.cu", "bsw_driver.cu", "bsw_sal.cu", "bsw_sa.cu", "bsw_fm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -201,7 +201,7 @@ WorkLayout work_layout(int64_t n, int64_t slot_bytes, int nwarps)
     L.cursor = take(4 * kNumBins);
     L.cls_start = take(4 * (kNumClass + 1));
     L.cls_count = take(4 * (kNumClass + 1));
-    L.cls_next = take(4 * (kNumClass + 1));
+    L.cls_next = take(4 * kNumCounters);
     L.cells = take(8);
     L.status = take(4);
     L.slots = take((size_t)slot_bytes * (size_t)nwarps);
@@ -427,7 +427,7 @@ struct bsw_ctx {
 
     // execution plan (bsw_set_plan / bsw_autotune) and kernel timing
     Plan plan = default_plan();
-    bsw_plan_t pub_plan{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0, 0.0f};
+    bsw_plan_t pub_plan{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0, 0, 0.0f};
     ClassTimer timer{};
     bool timer_ready = false, timer_valid = false;
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
@@ -1329,9 +1329,10 @@ int bsw_set_plan(bsw_ctx_t *ctx, const bsw_plan_t *plan)
 {
     if (!ctx || !plan) return BSW_EINVAL;
     if (plan->packed != 0 && plan->packed != 1) return BSW_EINVAL;
+    if (plan->warp_x2 != 0 && plan->warp_x2 != 1) return BSW_EINVAL;
     Plan L;
     if (!make_plan(plan->short_max, plan->u8_bounds, plan->i16_bounds, plan->packed != 0, plan->warp_cols,
-                   plan->inter_warps, plan->cta_min, &L))
+                   plan->inter_warps, plan->cta_min, plan->warp_x2 != 0, &L))
         return BSW_EINVAL;
     if (!serving_idle(ctx)) return BSW_ESTATE;
     ctx->plan = L;
@@ -1382,7 +1383,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         auto time_plan = [&](const bsw_plan_t &k, float *ms, int32_t *counts) -> int {
             Plan L;
             if (!make_plan(k.short_max, k.u8_bounds, k.i16_bounds, k.packed != 0, k.warp_cols, k.inter_warps,
-                           k.cta_min, &L))
+                           k.cta_min, k.warp_x2 != 0, &L))
                 return BSW_EINVAL;
             float best = 0.0f;
             for (int r = 0; r <= reps; ++r) {
@@ -1414,7 +1415,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         // empty are not timed (their differences would be noise), and the
         // boundary of a class the sample leaves empty is removed outright (one
         // launch fewer, the same work).
-        bsw_plan_t best{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0, 0.0f};
+        bsw_plan_t best{kShortMax, 0xffu, 0xfu, 0, 8, 2, 0, 0, 0.0f};
         float tbest = 0.0f;
         int32_t cnt[kNumClass + 1], cnt_best[kNumClass + 1];
         if ((rc = time_plan(best, &tbest, cnt_best)) != BSW_OK) return rc;
@@ -1439,7 +1440,13 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
             return false;
         };
         if (any(kClsCTA, kClsW16 + 1)) {
+            if (x2_usable(ctx->P)) {
+                bsw_plan_t k = best;
+                k.warp_x2 = 1;
+                if ((rc = consider(k)) != BSW_OK) return rc;
+            }
             for (int cols : {4, 16}) {
+                if (best.warp_x2) break;
                 bsw_plan_t k = best;
                 k.warp_cols = cols;
                 if ((rc = consider(k)) != BSW_OK) return rc;
@@ -1485,7 +1492,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
         }
         if ((rc = time_plan(best, &tbest, cnt)) != BSW_OK) return rc;
         make_plan(best.short_max, best.u8_bounds, best.i16_bounds, best.packed != 0, best.warp_cols, best.inter_warps,
-                  best.cta_min, &ctx->plan);
+                  best.cta_min, best.warp_x2 != 0, &ctx->plan);
         best.ms = tbest;
         ctx->pub_plan = best;
         clear_graphs(ctx);

@@ -21,6 +21,10 @@ constexpr int kLongMax = BSW_MAX_QLEN;
 constexpr int kNumClass = 15;
 constexpr int kRerun = 15;
 constexpr int kClsCTA = 12, kClsW16 = 13, kClsW32 = 14;
+// Work counters: one per class and the re-run list, then the 64-bit counter
+// (two words, 8-byte aligned) of the two-columns warp kernel's first wave.
+constexpr int kStrata = kNumClass + 1;
+constexpr int kNumCounters = kNumClass + 3;
 
 // Counting-sort bins.  Within a class the bins run from long to short queries,
 // so the persistent kernels take the longest work first.  The 8-bit bins also
@@ -86,12 +90,46 @@ struct Work {
     uint32_t *cursor;          // [kNumBins]
     int32_t *cls_start;        // [kNumClass + 1]
     int32_t *cls_count;        // [kNumClass + 1]
-    uint32_t *cls_next;        // [kNumClass + 1] work counters of the persistent kernels
+    uint32_t *cls_next;        // [kNumCounters] work counters of the persistent kernels
     int32_t *rerun;            // [n] pairs to redo with 32-bit lanes
     unsigned long long *cells; // DP cells computed
     uint32_t *status;          // kSt* bits
     uint8_t *slots;            // warp-per-pair slot scratch
     int64_t slot_bytes_per_warp;
 };
+
+// Device helpers shared by the kernel translation units.
+#ifdef __CUDACC__
+constexpr unsigned kFull = 0xffffffffu;
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Largest gap worth opening: trunc((n*match + end_bonus - o)/e + 1), at least 1.
+__device__ __forceinline__ int gap_cap(int n, int a, int eb, int o, int e)
+{
+    long long x = (long long)n * a + eb - o + e;
+    long long k = x / e;
+    return (int)(k > 1 ? k : 1);
+}
+
+__device__ __forceinline__ int clip_band(const Params &P, int n, int w)
+{
+    int wi = gap_cap(n, P.a, P.end_bonus, P.o_ins, P.e_ins);
+    int wd = gap_cap(n, P.a, P.end_bonus, P.o_del, P.e_del);
+    return min(w, min(wi, wd));
+}
+
+__device__ __forceinline__ void store_result(bsw_result_t *out, int score, int qle, int tle, int gtle,
+                                             int gscore, int moff)
+{
+    bsw_result_t r;
+    r.score = score; r.qle = qle; r.tle = tle; r.gtle = gtle; r.gscore = gscore; r.max_off = moff;
+    *out = r;
+}
+#endif
 
 }  // namespace bsw

@@ -30,38 +30,7 @@
 
 namespace bsw {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kNeg = -(1 << 29);
-
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
-{
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
-// Largest gap worth opening: trunc((n*match + end_bonus - o)/e + 1), at least 1.
-__device__ __forceinline__ int gap_cap(int n, int a, int eb, int o, int e)
-{
-    long long x = (long long)n * a + eb - o + e;
-    long long k = x / e;
-    return (int)(k > 1 ? k : 1);
-}
-
-__device__ __forceinline__ int clip_band(const Params &P, int n, int w)
-{
-    int wi = gap_cap(n, P.a, P.end_bonus, P.o_ins, P.e_ins);
-    int wd = gap_cap(n, P.a, P.end_bonus, P.o_del, P.e_del);
-    return min(w, min(wi, wd));
-}
-
-__device__ __forceinline__ void store_result(bsw_result_t *out, int score, int qle, int tle, int gtle,
-                                             int gscore, int moff)
-{
-    bsw_result_t r;
-    r.score = score; r.qle = qle; r.tle = tle; r.gtle = gtle; r.gscore = gscore; r.max_off = moff;
-    *out = r;
-}
 
 // ------------------------------------------------------------------ bucketing
 
@@ -212,7 +181,7 @@ __global__ void __launch_bounds__(1024) k_scan(Work W, ClassTable T)
         W.cls_count[t] = (int32_t)(pre[T.b[t + 1]] - pre[T.b[t]]);
     }
     if (t == kRerun) { W.cls_start[t] = 0; W.cls_count[t] = 0; }
-    if (t <= kNumClass) W.cls_next[t] = 0;
+    if (t < kNumCounters) W.cls_next[t] = 0;
 }
 
 // Place every pair in its bin.  Each block takes tiles of kScatterTile pairs:
@@ -1743,7 +1712,7 @@ __global__ void __launch_bounds__(256) k_plain_global(Batch B, Params P, Work W)
 // ------------------------------------------------------------------ launcher
 
 bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, int warp_cols, int inter_warps,
-               int cta_min, Plan *out)
+               int cta_min, bool warp_x2, Plan *out)
 {
     if (short_max < 64 || short_max > kShortMax) return false;
     if (cta_min != 0 && (cta_min < 128 || cta_min > kLongMax || (cta_min & 63))) return false;
@@ -1756,6 +1725,7 @@ bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, 
     L.warp_cols = warp_cols;
     L.inter_warps = inter_warps;
     L.cta_min = cta_min;
+    L.warp_x2 = warp_x2;
     int32_t *b = L.cls.b;
     // A disabled class gets an empty range; its queries fall to the next
     // larger enabled class.
@@ -1777,14 +1747,11 @@ bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, 
 Plan default_plan()
 {
     Plan L;
-    make_plan(kShortMax, 0xffu, 0xfu, false, 8, 2, 0, &L);
+    make_plan(kShortMax, 0xffu, 0xfu, false, 8, 2, 0, false, &L);
     return L;
 }
 
 namespace {
-
-// Shared memory a warp-per-pair block may use for its slot rings.
-constexpr size_t kRingSmemMax = 96 * 1024;
 
 // Resident blocks per SM of each k_inter instantiation with 1, 2 and 4 warps
 // per block, set by prepare_kernels.
@@ -1945,9 +1912,10 @@ cudaError_t cls_i16(const Batch &B, const Params &P, const Work &W, int c, cudaS
     return launch_inter<NMAX, false>(B, P, W, c, st, sms, L.inter_warps);
 }
 
-cudaError_t cls_w16(const Batch &B, const Params &P, const Work &W, int c, cudaStream_t st, int, int wblocks,
+cudaError_t cls_w16(const Batch &B, const Params &P, const Work &W, int c, cudaStream_t st, int sms, int wblocks,
                     const Plan &L)
 {
+    if (L.warp_x2 && x2_usable(P) && x2_ring_log2(P) > 0) return launch_x2(B, P, W, c, st, sms);
     if (L.warp_cols == 4) return launch_warp<4, true>(B, P, W, c, st, wblocks);
     if (L.warp_cols == 16) return launch_warp<16, true>(B, P, W, c, st, wblocks);
     return launch_warp<8, true>(B, P, W, c, st, wblocks);
@@ -2065,6 +2033,7 @@ cudaError_t prepare_kernels(int sms)
         return e;
     if ((e = cudaFuncSetAttribute(k_plain<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) != cudaSuccess)
         return e;
+    if ((e = prepare_x2(sms)) != cudaSuccess) return e;
     if ((e = prepare_inter<256, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<192, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<128, true>()) != cudaSuccess) return e;

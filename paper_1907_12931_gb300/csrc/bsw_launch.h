@@ -7,6 +7,9 @@
 
 namespace bsw {
 
+// Shared memory a warp-per-pair block may use for its slot rings.
+constexpr size_t kRingSmemMax = 96 * 1024;
+
 // Warp-per-pair kernels: 8 warps per block, 2 blocks per SM.
 constexpr int kWarpKernelThreads = 256;
 constexpr int kWarpBlocksPerSM = 2;
@@ -35,6 +38,7 @@ struct Plan {
     int32_t warp_cols;     // 4, 8 or 16
     int32_t inter_warps;   // 1, 2 or 4
     int32_t cta_min;       // queries of at least this many bases in the 16-bit range run one pair per block (0: none)
+    bool warp_x2;          // the 16-bit warp class runs the two-columns-per-instruction kernel (where it applies)
 };
 
 // u8_mask bit k enables kU8Nmax[k] as a class (bit 0 is always on), i16_mask
@@ -42,8 +46,18 @@ struct Plan {
 // holds it.  cta_min: 0, or a multiple of 64 in [128, kLongMax].  Returns
 // false for values out of range.
 bool make_plan(int short_max, uint32_t u8_mask, uint32_t i16_mask, bool packed, int warp_cols, int inter_warps,
-               int cta_min, Plan *out);
+               int cta_min, bool warp_x2, Plan *out);
 Plan default_plan();
+
+// The 16-bit warp kernel with two columns per instruction (bsw_warp2.cu):
+// whether the scoring suits it (match <= 3, so scores up to 2^13 fit, and
+// gap costs that fit 16-bit halves), the
+// ring for the context's band (0: too large for shared memory), the
+// per-device set-up, and the launch over one class list.
+bool x2_usable(const Params &P);
+int x2_ring_log2(const Params &P);
+cudaError_t prepare_x2(int sms);
+cudaError_t launch_x2(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms);
 
 // Whether the scoring lets the packed two-pairs-per-thread kernel run.
 bool packed_scoring_ok(const Params &P);

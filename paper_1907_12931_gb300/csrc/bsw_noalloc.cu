@@ -37,7 +37,7 @@ constexpr size_t kOffCursor = kOffHist + al(4 * kNumBins);
 constexpr size_t kOffClsStart = kOffCursor + al(4 * kNumBins);
 constexpr size_t kOffClsCount = kOffClsStart + al(4 * (kNumClass + 1));
 constexpr size_t kOffClsNext = kOffClsCount + al(4 * (kNumClass + 1));
-constexpr size_t kOffCells = kOffClsNext + al(4 * (kNumClass + 1));
+constexpr size_t kOffCells = kOffClsNext + al(4 * kNumCounters);
 constexpr size_t kOffStatus = kOffCells + al(8);
 constexpr size_t kOffSlots = kOffStatus + al(4);
 constexpr size_t kNaBytes = kOffSlots + (size_t)kNaSlotBytes * kNaWarpBlocks * (kWarpKernelThreads / 32);

@@ -26,6 +26,9 @@ PLANS = [
     {"short_max": 64, "cta_min": 128},
     {"short_max": 96, "warp_cols": 16, "cta_min": 1024},
     {"cta_min": 4096, "warp_cols": 4},
+    {"warp_x2": 1},
+    {"short_max": 64, "warp_x2": 1, "u8_bounds": 0x55},
+    {"short_max": 96, "warp_x2": 1, "cta_min": 1024},
 ]
 
 
@@ -91,11 +94,11 @@ def test_set_plan_rejects_bad_fields(bsw):
     wl, _, _ = workload_and_oracle("plain10k")
     bad = [{"short_max": 63}, {"short_max": 257}, {"warp_cols": 5}, {"warp_cols": 32}, {"inter_warps": 3},
            {"packed": 2}, {"u8_bounds": 0x100}, {"i16_bounds": 0x10}, {"cta_min": 64}, {"cta_min": 1000},
-           {"cta_min": 32832}, {"cta_min": -64}]
+           {"cta_min": 32832}, {"cta_min": -64}, {"warp_x2": 2}, {"warp_x2": -1}]
     with bsw.Context(wl.params) as ctx:
         before = ctx.get_plan().as_dict()
         assert before == {"short_max": 256, "u8_bounds": 0xff, "i16_bounds": 0xf, "packed": 0, "warp_cols": 8,
-                          "inter_warps": 2, "cta_min": 0, "ms": 0.0}
+                          "inter_warps": 2, "cta_min": 0, "warp_x2": 0, "ms": 0.0}
         for b in bad:
             with pytest.raises(bsw.BswError) as ei:
                 ctx.set_plan(bsw.make_plan(**b))
