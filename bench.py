@@ -604,13 +604,15 @@ def tune(bsw, ctx, name, n_pairs, seed, args):
 
 
 def plain_leg(bsw, ctx, db, plan, steps, warmup, stream, dist, out_ref, cells_ref):
-    """The plain baselines on the same inputs: the warp-per-pair ring kernel
-    over pairs in input order with 4, 8 and 16 columns per lane (the best is
-    the plain kernel), and the naive global-memory kernel."""
+    """The plain baselines on the same inputs: the warp-per-pair kernels over
+    pairs in input order, the int2 ring kernel with 4, 8 and 16 columns per
+    lane and the two-columns kernel ("x2"; the best of the four is the plain
+    kernel), and the naive global-memory kernel."""
     per = {}
-    for cols in (4, 8, 16):
-        ctx.set_plan(bsw.make_plan(plan.short_max, plan.u8_bounds, plan.i16_bounds, plan.packed, cols,
-                                   plan.inter_warps, plan.cta_min, 0))
+    for cols in (4, 8, 16, "x2"):
+        x2 = cols == "x2"
+        ctx.set_plan(bsw.make_plan(plan.short_max, plan.u8_bounds, plan.i16_bounds, plan.packed, 8 if x2 else cols,
+                                   plan.inter_warps, plan.cta_min, 1 if x2 else 0))
         ms = time_device(ctx, db, bsw.BSW_PLAIN_KERNEL, steps, warmup, stream, dist)
         equal = bool(np.array_equal(db.out.cpu().numpy(), out_ref)) and int(db.cells.item()) == cells_ref
         per[cols] = (ms, equal)
@@ -707,8 +709,13 @@ def measure(bsw, args, name, dist, stream, local, world, rank, headline):
         "cells_per_step": cells, "value": round(gcups, 3), "unit": "GCUPS", "ms_per_step": round(ms, 4),
         "steps": steps,
         "plain": {"value": round(gcups_plain, 3), "unit": "GCUPS", "ms_per_step": round(ms_plain, 4),
-                  "kernel": "k_plain<%d>: the warp-per-pair ring kernel, one pair per warp in input order, no "
-                            "bucketing, classes or re-run list (best of 4, 8, 16 columns per lane)" % best_c,
+                  "kernel": (("k_plain_x2: the two-columns warp-per-pair kernel, one pair per warp in input "
+                              "order, no bucketing or classes (pairs it cannot take run in the 32-bit warp kernel "
+                              "after it)") if best_c == "x2" else
+                             ("k_plain<%d>: the warp-per-pair ring kernel, one pair per warp in input order, no "
+                              "bucketing, classes or re-run list" % best_c))
+                            + "; the best of the ring kernel with 4, 8, 16 columns per lane and the two-columns "
+                              "kernel",
                   "by_columns": {str(c): {"gcups": round(total_cells / (per[c][0] * 1e-3) / 1e9, 3),
                                           "ms_per_step": round(per[c][0], 4), "bit_exact_vs_batched": per[c][1]}
                                  for c in per},

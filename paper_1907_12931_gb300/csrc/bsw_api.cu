@@ -504,7 +504,7 @@ cudaError_t enqueue_launch(bsw_ctx *c, Lane &lane, const Streams &S, const Batch
     Params P = c->P;
     P.flags = flags;
     const bool plain = (flags & (BSW_PLAIN_KERNEL | BSW_PLAIN_GLOBAL)) != 0;
-    c->last_launches = plain ? 1 : batched_launches(L, flags);
+    c->last_launches = plain ? plain_launches(P, L, flags) : batched_launches(L, flags);
     if (lane.work_dirty) {
         if ((e = cudaMemsetAsync(W.hist, 0, 4 * kNumBins, S.main)) != cudaSuccess) return e;
         lane.work_dirty = false;

@@ -130,6 +130,62 @@ __device__ __forceinline__ void store_result(bsw_result_t *out, int score, int q
     r.score = score; r.qle = qle; r.tle = tle; r.gtle = gtle; r.gscore = gscore; r.max_off = moff;
     *out = r;
 }
+
+// Whether bases [off, off + len) of an N bitmap hold an N.
+__device__ __forceinline__ bool range_has_n(const uint8_t *nm, int64_t off, int len)
+{
+    if (!nm || len <= 0) return false;
+    const int64_t a = off, b = off + len;                 // bits [a, b)
+    const int64_t b0 = a >> 3, b1 = (b - 1) >> 3;         // first and last byte
+    auto masked = [&](int64_t byte, uint32_t v) {
+        if (byte == b0) v &= 0xffu << (a & 7);
+        if (byte == b1) v &= 0xffu >> (7 - ((b - 1) & 7));
+        return v;
+    };
+    if (masked(b0, __ldg(nm + b0))) return true;
+    int64_t byte = b0 + 1;
+    for (; byte <= b1 && (reinterpret_cast<uintptr_t>(nm + byte) & 7); ++byte)   // up to an 8-byte boundary
+        if (masked(byte, __ldg(nm + byte))) return true;
+    for (; byte + 8 <= b1; byte += 8)                    // 8 whole bytes strictly between b0 and b1
+        if (__ldg(reinterpret_cast<const unsigned long long *>(nm + byte)) != 0ull) return true;
+    for (; byte <= b1; ++byte)
+        if (masked(byte, __ldg(nm + byte))) return true;
+    return false;
+}
+
+__device__ __forceinline__ bool pair_has_n(const Batch &B, int64_t qo, int n, int64_t to, int m)
+{
+    return range_has_n(B.q_n, qo, n) || range_has_n(B.t_n, to, m);
+}
+
+// Checks of one pair for the plain kernels (the checks k_classify makes);
+// answers pairs with an empty side.  Returns the pair's score bound, or -1
+// when there is nothing to compute.
+__device__ __forceinline__ long long plain_check(const Batch &B, const Params &P, const Work &W, int64_t p,
+                                                 int lane)
+{
+    const int n = B.q_len[p], m = B.t_len[p], h0 = B.h0[p];
+    const int64_t qo = B.q_off[p], to = B.t_off[p];
+    const int w = B.w_override ? B.w_override[p] : P.w;
+    if (n < 0 || m < 0 || h0 < 0 || w < 0 || qo < 0 || to < 0 || (qo & 3) || (to & 3)) {
+        if (lane == 0) atomicOr(W.status, kStInval);
+        return -1;
+    }
+    if (n == 0 || m == 0) {
+        if (lane == 0) store_result(&B.out[p], h0, 0, 0, 0, n == 0 ? h0 : -1, 0);
+        return -1;
+    }
+    const long long bound = (long long)h0 + (long long)P.a * min(n, m);
+    if (bound >= (1ll << 30)) {
+        if (lane == 0) atomicOr(W.status, kStInval);
+        return -1;
+    }
+    if (n > P.max_qlen) {
+        if (lane == 0) atomicOr(W.status, kStTooLong);
+        return -1;
+    }
+    return bound;
+}
 #endif
 
 }  // namespace bsw

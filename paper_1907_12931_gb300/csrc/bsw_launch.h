@@ -58,6 +58,9 @@ bool x2_usable(const Params &P);
 int x2_ring_log2(const Params &P);
 cudaError_t prepare_x2(int sms);
 cudaError_t launch_x2(const Batch &B, const Params &P, const Work &W, int cls, cudaStream_t st, int sms);
+// Its plain baseline over pairs in input order (the pairs it cannot take are
+// left on the re-run list, which the caller runs with the 32-bit kernel).
+cudaError_t launch_plain_x2(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms);
 
 // Whether the scoring lets the packed two-pairs-per-thread kernel run.
 bool packed_scoring_ok(const Params &P);
@@ -92,9 +95,13 @@ cudaError_t launch_batched_serial(const Batch &B, const Params &P, const Work &W
                                   int warp_blocks, const Plan &L);
 
 // Baseline: one pair per warp in input order, the warp kernel with the
-// plan's columns per lane (or, with BSW_PLAIN_GLOBAL in P.flags, the naive
-// one-column-per-lane kernel with its row in global memory).
+// plan's columns per lane, or the two-columns kernel when the plan selects it
+// (then the 32-bit kernel over the pairs it left), or, with BSW_PLAIN_GLOBAL
+// in P.flags, the naive one-column-per-lane kernel with its row in global
+// memory.
 cudaError_t launch_plain(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms, const Plan &L);
+// Kernels launch_plain makes under the plan and flags.
+int plain_launches(const Params &P, const Plan &L, uint32_t flags);
 
 // Per-pair arrays of a host batch already on the device, checked and reduced
 // there: whether any pair is invalid (the checks of bsw_extend_batch) and, over

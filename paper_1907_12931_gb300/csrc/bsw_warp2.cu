@@ -465,6 +465,35 @@ __global__ void __launch_bounds__(kX2Warps * 32, 4) k_warp_x2(Batch B, Params P,
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
 
+// The plain baseline with this kernel: pairs in input order, one per warp
+// (grid stride), no bucketing or classes.  Pairs it cannot take (an N base, a
+// score bound at its limit or above, a band wider than its ring) go to the
+// re-run list, which the 32-bit warp kernel runs afterwards.
+template <bool SYM>
+__global__ void __launch_bounds__(kX2Warps * 32, 4) k_plain_x2(Batch B, Params P, Work W, int ring_log2)
+{
+    extern __shared__ uint4 x2_mem[];
+    const int lane = threadIdx.x & 31;
+    uint2 *ring = reinterpret_cast<uint2 *>(x2_mem) + (threadIdx.x >> 5) * x2_ring_words(ring_log2);
+    const X2K K = x2_consts(P);
+    const long long limit = 1ll << (15 - K.zsh);
+    const int64_t gw = (int64_t)blockIdx.x * kX2Warps + (threadIdx.x >> 5), nw = (int64_t)gridDim.x * kX2Warps;
+    unsigned long long cells = 0;
+    for (int64_t p = gw; p < B.n; p += nw) {
+        const long long bound = plain_check(B, P, W, p, lane);
+        if (bound < 0) continue;
+        const int n = B.q_len[p];
+        const int wb = clip_band(P, n, B.w_override ? B.w_override[p] : P.w);
+        const bool has_n = (B.q_n || B.t_n) && pair_has_n(B, B.q_off[p], n, B.t_off[p], B.t_len[p]);
+        if (!has_n && bound < limit && x2_ring_cols(wb) <= (1 << ring_log2)) {
+            cells += x2_pair<SYM>(B, P, (int)p, ring, x2_ring_cols(wb) - 1, K);
+        } else if (lane == 0) {
+            W.rerun[atomicAdd(&W.cls_count[kRerun], 1)] = (int32_t)p;
+        }
+    }
+    if (lane == 0 && cells) atomicAdd(W.cells, cells);
+}
+
 int g_x2_blocks = 1;   // resident blocks per SM, set by prepare_x2
 
 }  // namespace
@@ -495,6 +524,12 @@ cudaError_t prepare_x2(int sms)
     if ((e = cudaFuncSetAttribute(k_warp_x2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) !=
         cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_plain_x2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_plain_x2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemMax)) !=
+        cudaSuccess)
+        return e;
     // resident blocks for the ring of a w = 500 band (the long-query workload's)
     int nb = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_warp_x2<true>, kX2Warps * 32,
@@ -512,6 +547,20 @@ cudaError_t launch_x2(const Batch &B, const Params &P, const Work &W, int cls, c
     const bool sym = P.o_del == P.o_ins && P.e_del == P.e_ins;
     if (sym) k_warp_x2<true><<<sms * g_x2_blocks, kX2Warps * 32, smem, st>>>(B, P, W, cls, lg);
     else k_warp_x2<false><<<sms * g_x2_blocks, kX2Warps * 32, smem, st>>>(B, P, W, cls, lg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_x2(const Batch &B, const Params &P, const Work &W, cudaStream_t st, int sms)
+{
+    const int lg = x2_ring_log2(P);
+    if (lg == 0) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(W.cls_count + kRerun, 0, 4, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(W.cls_next + kRerun, 0, 4, st)) != cudaSuccess) return e;
+    const size_t smem = (size_t)kX2Warps * x2_ring_words(lg) * 8;
+    const bool sym = P.o_del == P.o_ins && P.e_del == P.e_ins;
+    if (sym) k_plain_x2<true><<<sms * g_x2_blocks, kX2Warps * 32, smem, st>>>(B, P, W, lg);
+    else k_plain_x2<false><<<sms * g_x2_blocks, kX2Warps * 32, smem, st>>>(B, P, W, lg);
     return cudaGetLastError();
 }
 

@@ -6,7 +6,8 @@ register.  It must give the oracle's results bit for bit wherever it runs:
 band widths that give 1 to 4 granules per lane and several chunks per row,
 rows ending on every column of a granule, bands just under the ring size,
 every scoring it accepts, pairs above its score limit (re-run with 32-bit
-lanes), per-pair bands wider than its ring, and the full long-query workload.
+lanes), per-pair bands wider than its ring, and the full long-query workload;
+and as the plain baseline over pairs in input order.
 """
 import numpy as np
 import pytest
@@ -187,3 +188,31 @@ def test_plan_roundtrip_and_bad_values(bsw):
             with pytest.raises(bsw.BswError):
                 ctx.set_plan(bsw.make_plan(warp_x2=bad))
         assert ctx.get_plan().warp_x2 == 1
+
+
+@pytest.mark.parametrize("config", ["long10k", "read250", "plain10k"])
+def test_plain_kernel(bsw, config):
+    """The plain baseline with the two-columns kernel (pairs in input order;
+    pairs it cannot take run in the 32-bit kernel afterwards)."""
+    wl, ref, cells = workload_and_oracle(config)
+    got, gc = run_plan(bsw, wl, {"warp_x2": 1}, flags=bsw.BSW_PLAIN_KERNEL)
+    assert_same(got, ref, config + "/plain x2")
+    assert gc == cells
+
+
+def test_plain_kernel_leftovers(bsw):
+    """Pairs the plain two-columns kernel leaves to the 32-bit kernel: N
+    bases, score bounds at its limit, bands wider than its ring, empty sides
+    (answered in place) and the adversarial set's band widths."""
+    from test_gpu_nbase import hand_cases
+    hc = hand_cases()
+    ref, cells, _ = oracle.extend_batch(hc, nthreads=NTH)
+    got, gc = run_plan(bsw, hc, {"warp_x2": 1}, flags=bsw.BSW_PLAIN_KERNEL)
+    assert_same(got, ref, "plain x2, N hand cases")
+    assert gc == int(cells.sum())
+    wl, ws = adversarial()
+    wl.params = W.Params(W.Scoring(), w=100, zdrop=100, end_bonus=5)
+    ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH, w_override=ws)
+    got, gc = run_plan(bsw, wl, {"warp_x2": 1}, flags=bsw.BSW_PLAIN_KERNEL, w_override=ws)
+    assert_same(got, ref, "plain x2, adversarial")
+    assert gc == int(cells.sum())
