@@ -316,6 +316,7 @@ __device__ unsigned long long x2_pair(const Batch &B, const Params &P, int p, ui
     int hw = -1, lo = 0, hi = n;
     int best = h0, bi = -1, bj = -1, gbest = -1, gi = -1, moff = 0;
     unsigned long long ncell = 0;
+    const int cvis = h0 > P.o_ins ? (h0 - P.o_ins - 1) / e_ins : 0;   // last column with a non-zero boundary
     uint32_t tw = 0;                                           // target bases i..i+15 (i a multiple of 16)
     for (int i = 0; i < m; ++i) {
         if ((i & 15) == 0) {
@@ -330,7 +331,10 @@ __device__ unsigned long long x2_pair(const Batch &B, const Params &P, int p, ui
         for (int c = lo + lane; c < lo_new; c += 32) x2_set(RG, c, mask, 0, 0);   // left the band
         lo = lo_new;
         hi = min(min(hi, i + wb + 1), n);
-        for (int c = hw + 1 + lane; c <= hi - 1; c += 32)     // first visit of columns (hw, hi-1]
+        // First visit of columns (hw, hi-1]: their slots are empty (never
+        // written, or cleared when an alias left the band), so only columns
+        // whose Eq. 3 boundary value is non-zero need a write.
+        for (int c = hw + 1 + lane; c <= min(hi - 1, cvis); c += 32)
             x2_set(RG, c, mask, c == 0 ? h0 : max(0, h0 - P.o_ins - c * e_ins), 0);
         hw = max(hw, hi - 1);
         st_u16_if(lane == 0, x2_half(RG, hi, mask, 0), 0u);   // slot hi: read as empty in this row
