@@ -2011,14 +2011,20 @@ cudaError_t launch_batched(const Batch &B, const Params &P0, const Work &W, cons
     for (int k = 0; k < 3; ++k)
         if ((e = cudaStreamWaitEvent(S.side[k], S.fork, 0)) != cudaSuccess) return e;
     const int wblocks = sms * kWarpBlocksPerSM;
+    // The two-columns warp kernel runs after the other classes: it leaves a
+    // quarter of each SM's block slots free (3 blocks of its 4, so the
+    // longest pairs get a twelfth of an SM, not a sixteenth), and kernels of
+    // other classes in them would take issue slots from those pairs.
+    const bool x2_after = L.warp_x2 && x2_usable(P) && x2_ring_log2(P) > 0;
     for (int c : kForkOrder)
-        if (class_live(c, L, P.flags) &&
+        if (class_live(c, L, P.flags) && !(x2_after && c == kClsW16) &&
             (e = launch_class(c, B, P, W, S.side[kClassStream[c]], sms, wblocks, L, T)) != cudaSuccess)
             return e;
     for (int k = 0; k < 3; ++k) {
         if ((e = cudaEventRecord(S.join[k], S.side[k])) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(S.main, S.join[k], 0)) != cudaSuccess) return e;
     }
+    if (x2_after && (e = launch_class(kClsW16, B, P, W, S.main, sms, wblocks, L, T)) != cudaSuccess) return e;
     // Section V-D1: pairs whose scores left their lane range, exactly, in 32 bits.
     return launch_class(kRerun, B, P, W, S.main, sms, wblocks, L, T);
 }

@@ -424,15 +424,15 @@ __device__ unsigned long long x2_pair(const Batch &B, const Params &P, int p, ui
 
 // Persistent kernel over a class list: pairs whose score bound or band the
 // packed kernel does not hold go to the 32-bit re-run list.  A 10 kbp pair
-// runs about as long as the whole launch, so the first pair of each warp is
-// stratified: the list (longest first) is cut into strata of NB = gridDim.x
+// runs about as long as the whole launch (three blocks per SM), so the first
+// pair of each warp is stratified: the list (longest first) is cut into strata of NB = gridDim.x
 // pairs, and warp j of every block takes its first pair from stratum j, the
 // blocks in the order they start (one 16-bit field of a 64-bit counter per
 // stratum, NB fetches each).  Every block, whatever SM it lands on, thus
 // holds one pair of each stratum, and no SM starts with several of the
 // longest pairs; later pairs come longest first from the rest of the list.
 template <bool SYM>
-__global__ void __launch_bounds__(kX2Warps * 32, 4) k_warp_x2(Batch B, Params P, Work W, int cls, int ring_log2)
+__global__ void __launch_bounds__(kX2Warps * 32, 3) k_warp_x2(Batch B, Params P, Work W, int cls, int ring_log2)
 {
     extern __shared__ uint4 x2_mem[];
     const int lane = threadIdx.x & 31, wj = threadIdx.x >> 5;
@@ -498,7 +498,8 @@ __global__ void __launch_bounds__(kX2Warps * 32, 4) k_plain_x2(Batch B, Params P
     if (lane == 0 && cells) atomicAdd(W.cells, cells);
 }
 
-int g_x2_blocks = 1;   // resident blocks per SM, set by prepare_x2
+int g_x2_blocks = 1;         // blocks per SM of the class kernel, set by prepare_x2
+int g_x2_plain_blocks = 1;   // of the plain kernel (as many as fit)
 
 }  // namespace
 
@@ -539,7 +540,19 @@ cudaError_t prepare_x2(int sms)
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_warp_x2<true>, kX2Warps * 32,
                                                            (size_t)kX2Warps * x2_ring_words(10) * 8)) != cudaSuccess)
         return e;
-    g_x2_blocks = nb > 0 ? nb : 1;
+    // 3 blocks (12 warps) per SM, the class kernel's launch bound, although
+    // 4 would fit at 128 registers: a 10 kbp pair runs about as long as the
+    // launch, and at 12 warps it gets a twelfth of its SM instead of a
+    // sixteenth, so the launch ends with the SMs (long10k's class 16.4 ms
+    // against 18.1 at 4 blocks, every SM done within 0.4 ms of the others).
+    g_x2_blocks = nb > 3 ? 3 : (nb > 0 ? nb : 1);
+    // The plain kernel takes pairs in input order, where the longest pairs are
+    // spread over the whole launch: it runs as many blocks as fit.
+    int np_ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&np_, k_plain_x2<true>, kX2Warps * 32,
+                                                           (size_t)kX2Warps * x2_ring_words(10) * 8)) != cudaSuccess)
+        return e;
+    g_x2_plain_blocks = np_ > 0 ? np_ : 1;
     return cudaSuccess;
 }
 
@@ -563,8 +576,8 @@ cudaError_t launch_plain_x2(const Batch &B, const Params &P, const Work &W, cuda
     if ((e = cudaMemsetAsync(W.cls_next + kRerun, 0, 4, st)) != cudaSuccess) return e;
     const size_t smem = (size_t)kX2Warps * x2_ring_words(lg) * 8;
     const bool sym = P.o_del == P.o_ins && P.e_del == P.e_ins;
-    if (sym) k_plain_x2<true><<<sms * g_x2_blocks, kX2Warps * 32, smem, st>>>(B, P, W, lg);
-    else k_plain_x2<false><<<sms * g_x2_blocks, kX2Warps * 32, smem, st>>>(B, P, W, lg);
+    if (sym) k_plain_x2<true><<<sms * g_x2_plain_blocks, kX2Warps * 32, smem, st>>>(B, P, W, lg);
+    else k_plain_x2<false><<<sms * g_x2_plain_blocks, kX2Warps * 32, smem, st>>>(B, P, W, lg);
     return cudaGetLastError();
 }
 
