@@ -114,7 +114,8 @@ def test_long_with_n(bsw):
     assert gc == cells
 
 
-@pytest.mark.parametrize("plan", [(256, 0xff, 0xf, 0, 8, 2), (64, 0x0, 0x0, 1, 4, 1), (128, 0x55, 0x5, 0, 16, 4)])
+@pytest.mark.parametrize("plan", [(256, 0xff, 0xf, 0, 8, 2), (64, 0x0, 0x0, 1, 4, 1), (128, 0x55, 0x5, 0, 16, 4),
+                                  (96, 0xff, 0xf, 0, 8, 2, 0, 1)])
 def test_plans_with_n(bsw, plan):
     wl, ref, cells = n_workload("read151", 200_000, 0.002, 0.0005)
     with bsw.Context(wl.params, 16 << 30) as ctx:

@@ -46,10 +46,11 @@ def assert_same(got, ref, what):
                              % (what, bad.size, ref.shape[0], k, got[k].tolist(), ref[k].tolist()))
 
 
-def run(bsw, wl, flags=0, device=False, budget=16 << 30, w_override=None, params=None, warp_cols=None, cta_min=0):
+def run(bsw, wl, flags=0, device=False, budget=16 << 30, w_override=None, params=None, warp_cols=None, cta_min=0,
+        warp_x2=0):
     with bsw.Context(params or wl.params, budget) as ctx:
-        if warp_cols is not None or cta_min:
-            ctx.set_plan(bsw.make_plan(warp_cols=warp_cols or 8, cta_min=cta_min))
+        if warp_cols is not None or cta_min or warp_x2:
+            ctx.set_plan(bsw.make_plan(warp_cols=warp_cols or 8, cta_min=cta_min, warp_x2=warp_x2))
         hb = bsw.HostBatch(wl, w_override=w_override)
         if not device:
             return ctx.extend_host(hb, flags)
@@ -388,7 +389,9 @@ def test_serving_rejects_and_times_out(bsw):
 def test_maximum_query_length(bsw):
     """Queries of BSW_MAX_QLEN bases (band 500, the long-read parameters): a
     near-copy, an exact copy whose score leaves the 16-bit range (the 32-bit
-    kernel), and a short pair beside them; one base more is rejected."""
+    kernel), a query of that length against a 9 kbp target (score bound
+    under the two-columns kernel's limit, columns up to the last) and a short
+    pair beside them; one base more is rejected."""
     L = bsw.BSW_MAX_QLEN
     rng = np.random.default_rng(77)
     t = rng.integers(0, 4, L + 500).astype(np.uint8)
@@ -396,7 +399,8 @@ def test_maximum_query_length(bsw):
     flips = rng.random(L) < 0.05
     near[flips] = (near[flips] + 1) % 4
     params = W.Params(W.Scoring(), w=500, zdrop=400, end_bonus=5)
-    wl = W.from_lists([near, t[:L], t[:50]], [t, t, t[:150]], [40, 40, 20], params=params, align=4)
+    wl = W.from_lists([near, t[:L], near, t[:50]], [t, t, t[:9000], t[:150]], [40, 40, 40, 20], params=params,
+                      align=4)
     ref, cells, _ = oracle.extend_batch(wl, nthreads=NTH)
     assert ref[1][0] == 40 + L                        # the exact copy: h0 + L
     for flags in (0, "plain", "i32"):
@@ -406,6 +410,10 @@ def test_maximum_query_length(bsw):
     got, gc = run(bsw, wl, 0, params=params, cta_min=128)             # one pair per block
     assert_same(got, ref, "max qlen/block per pair")
     assert gc == int(cells.sum())
+    for flags in (0, "plain"):                                         # two columns per instruction
+        got, gc = run(bsw, wl, flag_of(bsw, flags), params=params, warp_x2=1)
+        assert_same(got, ref, "max qlen/x2/%s" % flags)
+        assert gc == int(cells.sum())
     too = W.from_lists([t[:L + 1]], [t], [40], params=params, align=4)
     with bsw.Context(params) as ctx:
         with pytest.raises(bsw.BswError) as e:
