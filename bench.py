@@ -52,7 +52,7 @@ MEASURED_TRAFFIC = {
 
 SECONDARY = ("read151", "long10k")
 
-U8_NMAX = (256, 192, 128, 96, 64, 48, 32, 16)
+U8_NMAX = (256, 224, 192, 160, 128, 96, 64, 32)
 I16_NMAX = (256, 128, 64, 32)
 
 WORKLOAD_TEXT = {

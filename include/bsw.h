@@ -340,7 +340,7 @@ int bsw_extend_batch_noalloc(const bsw_scoring_t *sc, int32_t w, int32_t zdrop, 
  *                per-thread length classes); longer ones one pair per warp.
  *                64 <= short_max <= 256.
  *   u8_bounds    bit k (k = 1..7) keeps the 8-bit class boundary at
- *                192, 128, 96, 64, 48, 32, 16 bases; the 256 class (bit 0) is
+ *                224, 192, 160, 128, 96, 64, 32 bases; the 256 class (bit 0) is
  *                always kept.  A query runs in the smallest kept class that
  *                holds it (a class of bound N keeps N + 1 slots per thread).
  *   i16_bounds   the same for the 16-bit classes: bits 1..3 = 128, 64, 32.
@@ -410,7 +410,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *batch, int64_t sample_pairs,
  * Waits for that call's work, then class_ms[c] = the time between the CUDA
  * events recorded on the stream of class c's kernel just before and just
  * after its launch (0 if the class was not launched).  Classes: 0-7 the 8-bit
- * per-thread classes of bound 256, 192, 128, 96, 64, 48, 32, 16; 8-11 the
+ * per-thread classes of bound 256, 224, 192, 160, 128, 96, 64, 32; 8-11 the
  * 16-bit classes of bound 256, 128, 64, 32; 12 the block-per-pair kernel; 13
  * the 16-bit warp-per-pair kernel; 14 the 32-bit one; 15 the 32-bit re-run.
  * launches = the kernels

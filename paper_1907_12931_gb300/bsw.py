@@ -44,7 +44,7 @@ BSW_FAULT_THREAD = 0x08
 BSW_FAULT_HOST = 0x10
 
 # class_ms indices of bsw_timing_t
-CLASS_NAMES = ("u8<256>", "u8<192>", "u8<128>", "u8<96>", "u8<64>", "u8<48>", "u8<32>", "u8<16>",
+CLASS_NAMES = ("u8<256>", "u8<224>", "u8<192>", "u8<160>", "u8<128>", "u8<96>", "u8<64>", "u8<32>",
                "i16<256>", "i16<128>", "i16<64>", "i16<32>", "cta16", "warp16", "warp32", "rerun32")
 
 FIELDS = ("score", "qle", "tle", "gtle", "gscore", "max_off")

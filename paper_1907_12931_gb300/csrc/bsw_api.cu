@@ -1457,7 +1457,7 @@ int bsw_autotune(bsw_ctx_t *ctx, const bsw_batch_t *b, int64_t sample_pairs, int
                 if ((rc = consider(k)) != BSW_OK) return rc;
             }
         }
-        if (can_pack && any(2, 8)) {       // the 8-bit classes of bound 128 and below
+        if (can_pack && any(4, 8)) {       // the 8-bit classes of bound 128 and below
             bsw_plan_t k = best;
             k.packed = 1;
             if ((rc = consider(k)) != BSW_OK) return rc;

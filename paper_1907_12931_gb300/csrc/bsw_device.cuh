@@ -12,8 +12,11 @@ constexpr int kShortMax = 256;
 // Longest query the warp-per-pair kernel's slot scratch is sized for.
 constexpr int kLongMax = BSW_MAX_QLEN;
 
-// Pair classes.  Classes 0-7: 8-bit lanes for query lengths (192,256],
-// (128,192], (96,128], (64,96], (48,64], (32,48], (16,32], [1,16]; 8-11:
+// Pair classes.  Classes 0-7: 8-bit lanes for query lengths (224,256],
+// (192,224], (160,192], (128,160], (96,128], (64,96], (32,64], [1,32] (a
+// class of bound N keeps N + 1 slots per thread, so bounds 32 apart keep the
+// shared memory a warp holds, and thus the warps per SM, close to what its
+// queries need); 8-11:
 // 16-bit lanes for (128,256], (64,128], (32,64], [1,32]; 12: block (several
 // warps) per pair, the longest queries of the 16-bit range; 13: warp per pair
 // with 16-bit-range scores; 14: warp per pair with 32-bit scores; 15: the

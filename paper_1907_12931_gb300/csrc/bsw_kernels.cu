@@ -1707,8 +1707,8 @@ int warps_index(int warps) { return warps <= 1 ? 0 : warps == 2 ? 1 : 2; }
 template <int NMAX, bool U8> size_t inter_smem(int warps) { return (size_t)warps * (NMAX + 1) * 32 * 4; }
 template <int NMAX, bool U8> constexpr int inter_index()
 {
-    return U8 ? (NMAX >= 256 ? 0 : NMAX >= 192 ? 1 : NMAX >= 128 ? 2 : NMAX >= 96 ? 3 : NMAX >= 64 ? 4 : NMAX >= 48 ? 5
-                 : NMAX >= 32 ? 6 : 7)
+    return U8 ? (NMAX >= 256 ? 0 : NMAX >= 224 ? 1 : NMAX >= 192 ? 2 : NMAX >= 160 ? 3 : NMAX >= 128 ? 4 : NMAX >= 96 ? 5
+                 : NMAX >= 64 ? 6 : 7)
               : 8 + (NMAX >= 256 ? 0 : NMAX >= 128 ? 1 : NMAX >= 64 ? 2 : 3);
 }
 
@@ -1878,7 +1878,7 @@ cudaError_t cls_cta(const Batch &B, const Params &P, const Work &W, int c, cudaS
 }
 
 constexpr ClassLaunch kClassLaunch[kNumClass + 1] = {
-    cls_u8<256>, cls_u8<192>, cls_u8<128>, cls_u8<96>, cls_u8<64>, cls_u8<48>, cls_u8<32>, cls_u8<16>,
+    cls_u8<256>, cls_u8<224>, cls_u8<192>, cls_u8<160>, cls_u8<128>, cls_u8<96>, cls_u8<64>, cls_u8<32>,
     cls_i16<256>, cls_i16<128>, cls_i16<64>, cls_i16<32>, cls_cta, cls_w16, cls_w32, cls_w32};
 
 // Launch order of the classes in the forked path and the side stream of each:
@@ -1983,9 +1983,9 @@ cudaError_t prepare_kernels(int sms)
     if ((e = prepare_inter<128, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<96, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<64, true>()) != cudaSuccess) return e;
-    if ((e = prepare_inter<48, true>()) != cudaSuccess) return e;
+    if ((e = prepare_inter<224, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<32, true>()) != cudaSuccess) return e;
-    if ((e = prepare_inter<16, true>()) != cudaSuccess) return e;
+    if ((e = prepare_inter<160, true>()) != cudaSuccess) return e;
     if ((e = prepare_inter<256, false>()) != cudaSuccess) return e;
     if ((e = prepare_inter<128, false>()) != cudaSuccess) return e;
     if ((e = prepare_inter<64, false>()) != cudaSuccess) return e;

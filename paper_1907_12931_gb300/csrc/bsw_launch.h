@@ -16,7 +16,7 @@ constexpr int kWarpBlocksPerSM = 2;
 
 // Query-length upper bounds of the 8-bit (classes 0-7) and 16-bit (classes
 // 8-11) per-thread kernels.
-constexpr int kU8Nmax[8] = {256, 192, 128, 96, 64, 48, 32, 16};
+constexpr int kU8Nmax[8] = {256, 224, 192, 160, 128, 96, 64, 32};
 constexpr int kI16Nmax[4] = {256, 128, 64, 32};
 
 struct Streams {

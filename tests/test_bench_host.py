@@ -50,15 +50,17 @@ def test_class_of_matches_definition():
 
 def test_class_kernel_names():
     sc = W.Scoring()
-    assert bench.class_kernel(3, _Plan(), sc) == "k_inter<96,u8>"
-    assert bench.class_kernel(3, _Plan(packed=1), sc) == "k_inter2<128>"
+    assert bench.class_kernel(5, _Plan(), sc) == "k_inter<96,u8>"
+    assert bench.class_kernel(3, _Plan(), sc) == "k_inter<160,u8>"
+    assert bench.class_kernel(5, _Plan(packed=1), sc) == "k_inter2<128>"
+    assert bench.class_kernel(3, _Plan(packed=1), sc) == "k_inter<160,u8>"   # packed pairs: bounds up to 128
     assert bench.class_kernel(0, _Plan(packed=1), sc) == "k_inter<256,u8>"
     assert bench.class_kernel(9, _Plan(), sc) == "k_inter<128,i16>"
     assert bench.class_kernel(12, _Plan(cta_min=1024), sc) == "k_cta<8,s16>"
     assert bench.class_kernel(13, _Plan(warp_cols=16), sc) == "k_warp<16,s16>"
     assert bench.class_kernel(14, _Plan(), sc) == "k_warp<8,s32>"
     # large gap costs: the packed kernel does not apply
-    assert bench.class_kernel(3, _Plan(packed=1), W.Scoring(1, 200, 100, 1, 100, 1)) == "k_inter<96,u8>"
+    assert bench.class_kernel(5, _Plan(packed=1), W.Scoring(1, 200, 100, 1, 100, 1)) == "k_inter<96,u8>"
 
 
 def test_cpu_baseline_record():

@@ -176,16 +176,17 @@ def test_kernel_times(bsw):
         torch.cuda.synchronize()
         assert_same(db.out.cpu().numpy(), ref, "timed launch")
         assert launches == 18                              # 3 bucketing + 14 classes (no block class) + re-run
-        assert ms[3] > 0 and ms[15] > 0                    # u8<96> carries most cells; re-run always launches
+        assert ms[5] > 0 and ms[15] > 0                    # u8<96> carries most cells; re-run always launches
         assert ms[12] == 0                                 # cta_min 0: no block-per-pair launch
         assert all(t >= 0 for t in ms)
         # a plan with fewer classes launches fewer kernels
         ctx.set_plan(bsw.make_plan(short_max=128, u8_bounds=0x5, i16_bounds=0x1))
         ctx.extend_device(db, bsw.BSW_TIME_KERNELS | bsw.BSW_NO_GRAPH)
         launches2, ms2 = ctx.kernel_times()
-        # u8<256> would hold only queries over 128 bases, which short_max 128
-        # sends to the warp kernel, so it is skipped; live: u8<128>, i16<256>,
-        # the two warp classes and the re-run
+        # bounds kept: 256 and 192.  u8<256> would hold only queries over 192
+        # bases, which short_max 128 sends to the warp kernel, so it is
+        # skipped; live: u8<192> (every query up to 128), i16<256>, the two
+        # warp classes and the re-run
         assert launches2 == 3 + 5
         assert ms2[0] == 0 and ms2[1] == 0 and ms2[3] == 0 and ms2[2] > 0
         ctx.sync()
