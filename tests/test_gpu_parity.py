@@ -144,7 +144,8 @@ def adversarial():
     def add(q, t, h0, w=100):
         qs.append(np.asarray(q, np.uint8)); ts.append(np.asarray(t, np.uint8)); hs.append(h0); ws.append(w)
 
-    lens = [0, 1, 2, 3, 4, 5, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 300, 600]
+    lens = [0, 1, 2, 3, 4, 5, 15, 16, 17, 31, 32, 33, 63, 64, 65, 95, 96, 97, 127, 128, 129, 159, 160, 161, 191, 192,
+            193, 223, 224, 225, 255, 256, 257, 300, 600]
     for n in lens:
         for m in (0, 1, n, n + 100, max(1, n // 2)):
             ref = rng.integers(0, 4, n + m + 8)
