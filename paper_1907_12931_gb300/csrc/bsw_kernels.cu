@@ -434,6 +434,239 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
     return ncell;
 }
 
+// ------------------------------------------ two rows per instruction (8-bit)
+//
+// The 8-bit class pairs without N bases take rows in pairs: rows i and i+1 sit
+// in the low and high halves of s16x2 registers, row i+1 one column behind
+// (step s computes cells (i, s) and (i+1, s-1)), so every DPX instruction of
+// the cell update (Eq. 2, Eq. 3's affine gaps) advances two cells.  Row i+1
+// takes its diagonal H(i, s-2) and its E(i+1, s-1) from row i's registers;
+// only row i+1's results go back to the slot column, slot s-1 <- {H(i+1, s-2),
+// E(i+2, s-1)}, so a pass reads each slot once and writes it once for two
+// rows.  The row selector in bits 0-15 of slot s picks byte q_s of row i's
+// profile for the low half and byte 4 + q_{s-1} (row i+1's profile) for the
+// high half, both sign-extended, so one byte permute gives both scores.
+//
+// Row i+1's band depends on row i's rule-c trims, which are known only after
+// row i ends.  Its left end is found before the packed loop starts: row i
+// runs alone until its first non-zero slot (its trimmed start) is known and
+// the band's lower clip is reached.  Its right end, min(last + 2, n) with
+// `last` row i's last non-zero slot, equals L + 3 for L the last column where
+// H(i, .) > 0 (a slot past L + 1 has H(i, k-1) = 0, and E(i+1, k) > 0 would
+// imply H(i, k) > 0); the packed loop tracks L and runs row i+1 up to row i's
+// end.  Row i+1's cells past L + 2 see a zero diagonal and a zero E, so they
+// hold only F, which is below the in-band row maximum: the row key is
+// unchanged, and after the pass their slots get row i's zeros back (the
+// values a row-by-row pass leaves there).  The last two or three columns of
+// row i+1 run after the loop, once L is known, reading the slot past row i's
+// end as a row-by-row pass does (a stale value, Section V-A's band rule).
+template <int NMAX, bool SYM>
+__device__ __noinline__ unsigned long long inter_pair_rp(const Batch &B, const Params &P, const PairRec &R,
+                                                         bsw_result_t *out, uint32_t *S)
+{
+    const int n = R.n, m = R.m, h0 = R.h0;
+    const int wb = clip_band(P, n, R.w);
+    const int e_del = P.e_del, e_ins = P.e_ins;
+    const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
+    const uint32_t k8 = P.k8, k16 = P.k16;          // 2^8, 2^16 (run-time: multiply-adds, not shifts)
+    int zs = 0;
+    while ((1 << zs) < P.a + 1) ++zs;
+    const uint32_t zmul = 1u << zs;                  // zero-diagonal rule: M = min(D + s, D * 2^z)
+    const uint32_t noe_d2 = (uint32_t)(-oe_del & 0xffff) * 0x10001u, noe_i2 = (uint32_t)(-oe_ins & 0xffff) * 0x10001u;
+    const uint32_t ne_d2 = (uint32_t)(-e_del & 0xffff) * 0x10001u, ne_i2 = (uint32_t)(-e_ins & 0xffff) * 0x10001u;
+
+    // Eq. 3, first row, and the selectors: slot j = q_j * 0x11 + q_{j-1} * 0x1100
+    // + 0xc480 (nibbles q_j, q_j | 8, 4 + q_{j-1}, (4 + q_{j-1}) | 8).
+    const int64_t q_off = R.q_off;
+    const uint8_t *qp = B.q + (q_off >> 2);
+    uint32_t cprev = 0;
+    for (int c = 0; c <= n; c += 4) {
+        const uint32_t byte = c < n ? __ldg(qp + (c >> 2)) : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = c + k;
+            if (j <= n) {
+                const uint32_t cj = j < n ? (byte >> (2 * k)) & 3u : 0u;
+                const int hv = j == 0 ? h0 : max(0, h0 - P.o_ins - j * e_ins);
+                S[j * 32] = cj * 0x11u + cprev * 0x1100u + 0xc480u + ((uint32_t)hv << 24);
+                cprev = cj;
+            }
+        }
+    }
+    const uint8_t *tp = B.t + (R.t_off >> 2);
+    const uint32_t mb8 = (uint32_t)(-P.b) & 0xffu;
+    const uint32_t mis4 = mb8 * 0x01010101u;
+    const uint32_t flip = ((uint32_t)P.a ^ mb8) & 0xffu;
+    const uint8_t *SE8 = reinterpret_cast<const uint8_t *>(S) + 2;                          // E byte of slot 0
+    uint16_t *SEH = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(S) + 2);     // E | H << 8 of slot 0
+
+    int lo = 0, hi = n;
+    int best = h0, bi = -1, bj = -1, gbest = -1, gi = -1, moff = 0;
+    unsigned long long ncell = 0;
+    uint32_t tbyte = 0;
+    for (int i = 0; i < m; i += 2) {
+        if ((i & 3) == 0) tbyte = __ldg(tp + (i >> 2));
+        const int tb0 = (tbyte >> (2 * (i & 3))) & 3, tb1 = (tbyte >> (2 * (i & 3) + 2)) & 3;
+        const uint32_t p0 = mis4 ^ (flip << (8 * tb0));      // row i: byte c = s(t_i, c)
+        const uint32_t p1 = mis4 ^ (flip << (8 * tb1));      // row i+1
+        const bool single = i + 1 == m;
+        lo = max(lo, i - wb);
+        hi = min(min(hi, i + wb + 1), n);
+        const int hl0 = lo == 0 ? max(0, h0 - oe_del - i * e_del) : 0;   // H(i, lo-1), Eq. 3 first column
+
+        // Row i alone from lo until its first non-zero slot and the lower clip
+        // of row i+1's band (c0), or to its end.
+        int f = 0, hprev = hl0, hprev2 = 0, en_last = 0, key_lo = 0, Lp = 0;
+        int lo1 = hi, c0 = -1;
+        bool found = false;
+        for (int s = lo; s < hi; ++s) {
+            const uint32_t wv = S[s * 32];
+            const int d = (int)(wv >> 24), e = (int)((wv >> 16) & 0xffu);
+            const int sc = (int)(short)prmt(p0, p1, wv);
+            const int M = __viaddmin_s32(d, sc, d * (int)zmul);
+            const int h = __vimax3_s32(M, e, f);
+            const int en = __viaddmax_s32_relu(e, -e_del, M - oe_del);
+            f = __viaddmax_s32_relu(f, -e_ins, M - oe_ins);
+            key_lo = max(key_lo, h * 256 + s);
+            if (h > 0) Lp = s + 1;
+            if (!found && (hprev | en)) { found = true; lo1 = s; }
+            hprev2 = hprev; hprev = h; en_last = en;
+            if (!single && found && s >= max(lo1, i + 1 - wb)) { c0 = s; break; }
+        }
+        if (single) {                                        // the last row of an odd count
+            const int rm = key_lo >> 8, rj = key_lo & 255;
+            if (hi > lo) ncell += (unsigned)(hi - lo);
+            if (max(lo, hi) == n) {
+                const int hl = hi > lo ? hprev : hl0;
+                if (hl >= gbest) gi = i;
+                gbest = max(gbest, hl);
+            }
+            if (rm > 0) {
+                if (rm > best) {
+                    best = rm; bi = i; bj = rj;
+                    moff = max(moff, abs(rj - i));
+                }
+            }
+            break;
+        }
+        if (c0 < 0) c0 = max(lo1, i + 1 - wb);
+        const int bnd1 = c0 == 0 ? max(0, h0 - oe_del - (i + 1) * e_del) : 0;   // H(i+1, c0-1)
+
+        // Both rows: step s computes (i, s) low and (i+1, s-1) high.
+        uint32_t hA = (uint32_t)hprev | ((uint32_t)bnd1 << 16);   // h of step s-1
+        uint32_t hB = (uint32_t)hprev2;                            // h of step s-2 (low half used)
+        uint32_t ENp = (uint32_t)en_last;                          // E out of step s-1 (low half used)
+        uint32_t F2 = (uint32_t)f;                                 // F(i, s) | F(i+1, s-1) << 16
+        uint32_t key2 = (uint32_t)key_lo, L2 = (uint32_t)Lp;       // row keys H * 256 + column; L + 1
+        uint32_t j2 = (uint32_t)(c0 + 1) | ((uint32_t)c0 << 16);
+#pragma unroll 4
+        for (int s = c0 + 1; s < hi; ++s) {
+            const uint32_t e = SE8[s * 128];                       // E(i, s): byte load before the word
+            const uint32_t wv = S[s * 32];
+            const uint32_t Hd2 = hB * k16 + __umulhi(wv, k8);      // H(i-1, s-1) | H(i, s-2) << 16
+            const uint32_t Ed2 = ENp * k16 + e;                     // E(i, s) | E(i+1, s-1) << 16
+            const uint32_t M2 = __viaddmin_s16x2(Hd2, prmt(p0, p1, wv), Hd2 * zmul);
+            const uint32_t h2 = __vimax3_s16x2(M2, Ed2, F2);
+            const uint32_t Mi2 = __viaddmax_s16x2_relu(M2, noe_i2, 0u);
+            const uint32_t Md2 = SYM ? Mi2 : __viaddmax_s16x2_relu(M2, noe_d2, 0u);
+            const uint32_t EN2 = __viaddmax_s16x2_relu(Ed2, ne_d2, Md2);
+            F2 = __viaddmax_s16x2_relu(F2, ne_i2, Mi2);
+            const uint32_t h2K = h2 * k8;
+            key2 = __viaddmax_u16x2(h2K, j2, key2);
+            L2 = __viaddmax_u16x2(__viaddmin_u16x2(j2, 0x00010001u, h2K), 0u, L2);   // s + 1 where H(i, s) > 0
+            SEH[(s - 1) * 64] = (uint16_t)prmt(EN2, hA, 0x0062u);             // slot s-1 <- E(i+2, s-1), H(i+1, s-2)
+            j2 += 0x00010001u;
+            hB = hA; hA = h2; ENp = EN2;
+        }
+        int Hi1, Hi2, Ei1, ce, fh, hlh;                            // row i's last values; row i+1's state
+        if (hi > c0 + 1) {
+            Hi1 = (int)(hA & 0xffffu); Hi2 = (int)(hB & 0xffffu); Ei1 = (int)(ENp & 0xffffu);
+            ce = hi - 1; fh = (int)(F2 >> 16); hlh = (int)(hA >> 16);
+        } else {
+            Hi1 = hprev; Hi2 = hprev2; Ei1 = en_last;
+            ce = c0; fh = 0; hlh = bnd1;
+        }
+        key_lo = (int)(key2 & 0xffffu);
+        int key_hi = (int)(key2 >> 16);
+        Lp = (int)(L2 & 0xffffu);
+
+        // Row i: Section V-D's decisions.
+        {
+            const int rm = key_lo >> 8, rj = key_lo & 255;
+            if (hi > lo) ncell += (unsigned)(hi - lo);
+            if (max(lo, hi) == n) {
+                const int hl = hi > lo ? Hi1 : hl0;
+                if (hl >= gbest) gi = i;
+                gbest = max(gbest, hl);
+            }
+            if (rm == 0) break;
+            if (rm > best) {
+                best = rm; bi = i; bj = rj;
+                moff = max(moff, abs(rj - i));
+            } else if (P.zdrop > 0) {
+                const int di = i - bi, dj = rj - bj;
+                const int drop = di > dj ? best - rm - (di - dj) * e_del : best - rm - (dj - di) * e_ins;
+                if (drop > P.zdrop) break;
+            }
+        }
+        // Row i+1's band is [c0, hi1); its columns from ce on run here.
+        const int i1 = i + 1;
+        const int hi1 = min(min(Lp + 2, n), i1 + wb + 1);
+        for (int c = ce; c < hi1; ++c) {
+            const uint32_t wc = S[c * 32];
+            int d, e;
+            if (c == hi - 1) { d = Hi2; e = Ei1; }
+            else if (c == hi) { d = Hi1; e = 0; }
+            else { d = (int)(wc >> 24); e = (int)((wc >> 16) & 0xffu); }   // past row i: the slot as it stands
+            const int sc = (int)(signed char)prmt(p1, 0u, wc);
+            const int M = __viaddmin_s32(d, sc, d * (int)zmul);
+            const int h = __vimax3_s32(M, e, fh);
+            const int en = __viaddmax_s32_relu(e, -e_del, M - oe_del);
+            fh = __viaddmax_s32_relu(fh, -e_ins, M - oe_ins);
+            SEH[c * 64] = (uint16_t)(((uint32_t)hlh << 8) | (uint32_t)en);
+            key_hi = max(key_hi, h * 256 + c);
+            hlh = h;
+        }
+        if (hi1 >= ce && hi1 > c0) SEH[hi1 * 64] = (uint16_t)((uint32_t)hlh << 8);   // row end, E = 0
+        {
+            const int rm = key_hi >> 8, rj = key_hi & 255;
+            if (hi1 > c0) ncell += (unsigned)(hi1 - c0);
+            if (max(c0, hi1) == n) {
+                const int hl = hi1 > c0 ? (int)(S[hi1 * 32] >> 24) : bnd1;
+                if (hl >= gbest) gi = i1;
+                gbest = max(gbest, hl);
+            }
+            if (rm == 0) break;
+            if (rm > best) {
+                best = rm; bi = i1; bj = rj;
+                moff = max(moff, abs(rj - i1));
+            } else if (P.zdrop > 0) {
+                const int di = i1 - bi, dj = rj - bj;
+                const int drop = di > dj ? best - rm - (di - dj) * e_del : best - rm - (dj - di) * e_ins;
+                if (drop > P.zdrop) break;
+            }
+        }
+        for (int k = hi1 + 1; k <= hi; ++k) SEH[k * 64] = 0;       // row i's zeros past row i+1's end
+        int k = c0;                                                // rule c on row i+1
+        while (k < hi1 && !slot_nonzero<true>(S[k * 32])) ++k;
+        lo = k;
+        k = hi1;
+        while (k >= lo && !slot_nonzero<true>(S[k * 32])) --k;
+        hi = min(k + 2, n);
+    }
+    store_result(out, best, bj + 1, bi + 1, gi + 1, gbest, moff);
+    return ncell;
+}
+
+// Whether the row-pair path takes the pair: no N bases (checked by the
+// caller's kernel), scores and gap terms inside the packed 8-bit range.
+__device__ __forceinline__ bool rp_eligible(const Params &P, const PairRec &R, int nmax)
+{
+    return R.n >= 1 && R.m >= 1 && R.n <= nmax && R.h0 >= 0 &&
+           (long long)R.h0 + (long long)P.a * min(R.n, R.m) <= 255 && P.a <= 127 && P.o_del + P.e_del <= 30000 &&
+           P.o_ins + P.e_ins <= 30000 && P.e_del <= 30000 && P.e_ins <= 30000;
+}
+
 template <int NMAX, bool U8, bool NM = false>
 __global__ void __launch_bounds__(256) k_inter(Batch B, Params P, Work W, int cls)
 {
@@ -459,7 +692,12 @@ __global__ void __launch_bounds__(256) k_inter(Batch B, Params P, Work W, int cl
                 R.n = B.q_len[p]; R.m = B.t_len[p]; R.h0 = B.h0[p];
                 R.w = B.w_override ? B.w_override[p] : P.w;
             }
-            cells += inter_pair<NMAX, U8, NM>(B, P, W, p, R, S);
+            if (U8 && !NM && rp_eligible(P, R, NMAX)) {
+                cells += (P.o_del == P.o_ins && P.e_del == P.e_ins) ? inter_pair_rp<NMAX, true>(B, P, R, &B.out[p], S)
+                                                                   : inter_pair_rp<NMAX, false>(B, P, R, &B.out[p], S);
+            } else {
+                cells += inter_pair<NMAX, U8, NM>(B, P, W, p, R, S);
+            }
         }
         __syncwarp();
     }
