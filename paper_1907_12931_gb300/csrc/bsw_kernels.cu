@@ -461,8 +461,8 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
 // row i+1 run after the loop, once L is known, reading the slot past row i's
 // end as a row-by-row pass does (a stale value, Section V-A's band rule).
 template <int NMAX, bool SYM>
-__device__ __noinline__ unsigned long long inter_pair_rp(const Batch &B, const Params &P, const PairRec &R,
-                                                         bsw_result_t *out, uint32_t *S)
+__device__ __forceinline__ unsigned long long inter_pair_rp(const Batch &B, const Params &P, const PairRec &R,
+                                                            bsw_result_t *out, uint32_t *S)
 {
     const int n = R.n, m = R.m, h0 = R.h0;
     const int wb = clip_band(P, n, R.w);
@@ -503,9 +503,12 @@ __device__ __noinline__ unsigned long long inter_pair_rp(const Batch &B, const P
     int lo = 0, hi = n;
     int best = h0, bi = -1, bj = -1, gbest = -1, gi = -1, moff = 0;
     unsigned long long ncell = 0;
-    uint32_t tbyte = 0;
+    uint32_t tbyte = 0, tnext = __ldg(tp);                  // target bases, fetched one byte (4 rows) ahead
     for (int i = 0; i < m; i += 2) {
-        if ((i & 3) == 0) tbyte = __ldg(tp + (i >> 2));
+        if ((i & 3) == 0) {
+            tbyte = tnext;
+            tnext = i + 4 < m ? __ldg(tp + (i >> 2) + 1) : 0u;
+        }
         const int tb0 = (tbyte >> (2 * (i & 3))) & 3, tb1 = (tbyte >> (2 * (i & 3) + 2)) & 3;
         const uint32_t p0 = mis4 ^ (flip << (8 * tb0));      // row i: byte c = s(t_i, c)
         const uint32_t p1 = mis4 ^ (flip << (8 * tb1));      // row i+1
@@ -559,7 +562,7 @@ __device__ __noinline__ unsigned long long inter_pair_rp(const Batch &B, const P
         uint32_t F2 = (uint32_t)f;                                 // F(i, s) | F(i+1, s-1) << 16
         uint32_t key2 = (uint32_t)key_lo, L2 = (uint32_t)Lp;       // row keys H * 256 + column; L + 1
         uint32_t j2 = (uint32_t)(c0 + 1) | ((uint32_t)c0 << 16);
-#pragma unroll 4
+#pragma unroll 8
         for (int s = c0 + 1; s < hi; ++s) {
             const uint32_t e = SE8[s * 128];                       // E(i, s): byte load before the word
             const uint32_t wv = S[s * 32];
@@ -658,8 +661,9 @@ __device__ __noinline__ unsigned long long inter_pair_rp(const Batch &B, const P
     return ncell;
 }
 
-// Whether the row-pair path takes the pair: no N bases (checked by the
-// caller's kernel), scores and gap terms inside the packed 8-bit range.
+// Whether the row-pair path takes the pair: no N bases (the caller's kernel
+// runs it only for batches without N bitmaps), scores and gap terms inside
+// the packed 8-bit range.
 __device__ __forceinline__ bool rp_eligible(const Params &P, const PairRec &R, int nmax)
 {
     return R.n >= 1 && R.m >= 1 && R.n <= nmax && R.h0 >= 0 &&
