@@ -43,11 +43,8 @@ METRIC = "BSW GCUPS on 1 GB300 (batched vs plain kernel, bit-exact); p50/p99 ser
 # one ncu capture of the current kernel (bytes, source); other kernels and
 # workloads report null.
 MEASURED_TRAFFIC = {
-    ("read250", "k_inter<128,u8>"): (49_564_160, "ncu dram__bytes_read.sum + dram__bytes_write.sum of the dominant "
+    ("read250", "k_inter<128,u8>"): (49_626_624, "ncu dram__bytes_read.sum + dram__bytes_write.sum of the dominant "
                                                  "launch, profiles/k_inter128_u8_read250.md"),
-    ("long10k", "k_warp_x2"): (19_968, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch between "
-                                       "launches of the same batch (caches not flushed: the 14 MB of inputs stay "
-                                       "in L2), profiles/k_warp_x2_long10k.md"),
 }
 
 SECONDARY = ("read151", "long10k")

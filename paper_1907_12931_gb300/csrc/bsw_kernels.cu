@@ -469,9 +469,11 @@ __device__ __forceinline__ unsigned long long inter_pair_rp(const Batch &B, cons
     const int e_del = P.e_del, e_ins = P.e_ins;
     const int oe_del = P.o_del + e_del, oe_ins = P.o_ins + e_ins;
     const uint32_t k8 = P.k8, k16 = P.k16;          // 2^8, 2^16 (run-time: multiply-adds, not shifts)
-    int zs = 0;
-    while ((1 << zs) < P.a + 1) ++zs;
-    const uint32_t zmul = 1u << zs;                  // zero-diagonal rule: M = min(D + s, D * 2^z)
+    // Zero-diagonal rule: M = min(D + s, D * 128), D * 128 >= D + s for D >= 1
+    // (match <= 127) and below 2^15 for D <= 255.  The factor comes from a
+    // run-time value so that the product stays a multiply-add (FMA pipe)
+    // instead of becoming a shift (integer pipe).
+    const uint32_t zmul = k8 >> 1;
     const uint32_t noe_d2 = (uint32_t)(-oe_del & 0xffff) * 0x10001u, noe_i2 = (uint32_t)(-oe_ins & 0xffff) * 0x10001u;
     const uint32_t ne_d2 = (uint32_t)(-e_del & 0xffff) * 0x10001u, ne_i2 = (uint32_t)(-e_ins & 0xffff) * 0x10001u;
 

@@ -115,7 +115,7 @@ __device__ __forceinline__ X2K x2_consts(const Params &P)
 #pragma unroll
     for (int k = 0; k < 4; ++k) K.nke2[k] = rep2(-k * P.e_ins);
     K.zsh = x2_zshift(P.a);
-    K.zmul = 1u << K.zsh;
+    K.zmul = P.k16 >> (16 - K.zsh);   // 2^z from a run-time value: the product stays a multiply-add
     return K;
 }
 
