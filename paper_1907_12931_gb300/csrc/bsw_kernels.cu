@@ -459,7 +459,8 @@ __device__ __forceinline__ unsigned long long inter_pair(const Batch &B, const P
 // unchanged, and after the pass their slots get row i's zeros back (the
 // values a row-by-row pass leaves there).  The last two or three columns of
 // row i+1 run after the loop, once L is known, reading the slot past row i's
-// end as a row-by-row pass does (a stale value, Section V-A's band rule).
+// end as a row-by-row pass does (a value an earlier row left there, read when
+// the band grows past the previous row's end).
 template <int NMAX, bool SYM>
 __device__ __forceinline__ unsigned long long inter_pair_rp(const Batch &B, const Params &P, const PairRec &R,
                                                             bsw_result_t *out, uint32_t *S)
