@@ -875,11 +875,13 @@ def run_gb300(args):
             "metric": METRIC, "value": head["value"], "unit": "GCUPS", "n_gpus": world, "steps": head["steps"],
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "u8 storage, int32 arithmetic" if args.config != "long10k"
-                     else "int16 storage, int32 arithmetic",
+            "dtype": "u8 storage, s16x2 arithmetic (two rows per instruction)" if args.config != "long10k"
+                     else "int16 storage, s16x2 arithmetic (two columns per instruction)",
             "dtype_note": "per-pair lane storage by the exact score bound h0 + match*min(n, m) (8-bit when <= 255, "
-                          "16-bit when <= 32767, else 32-bit); every operation runs in 32-bit registers and pairs "
-                          "whose scores leave their lane range are re-run exactly in 32 bits",
+                          "16-bit when <= 32767, else 32-bit); the 8-bit pairs without N bases compute two rows "
+                          "per packed s16x2 DPX instruction and the long queries' warp kernel two columns, the "
+                          "other kernels in 32-bit registers; pairs whose scores leave their lane range are re-run "
+                          "exactly in 32 bits",
             "data": "synthetic",
             "config": {"workload": args.config, "description": head["description"],
                        "pairs_per_gpu": head["pairs"], "cells_per_step": head["cells_per_step"], "l2": head["l2"],
